@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the FR right-hand side on a B300: RHS GDOF/s per RK stage.
+
+Workload (synthetic, seeded): 3D Navier-Stokes on a periodic 96^3 hexahedral
+box [0, 2 pi]^3 (884,736 elements), p = 4 (125 solution points, 5 variables,
+552.96 M DOF), Taylor-Green initial data (M = 0.1, Re = 1600, Pr = 0.71) plus
+a seeded smooth perturbation; LDG beta = 1/2, tau = 0.1.  The paper's own
+benchmark is a periodic hexahedral box at p = 2..4 (Sec. 6); its meshes are
+not published and this box stands in for them.
+
+One step = one classical RK4 step (4 right-hand sides + stage combines) via
+fr_rk4; the metric is N_V * sum_e N_e^(u) |Omega_e| * 4 * steps / time / 1e9.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RHS GDOF/s per RK stage (mixed vs plain FP64 GPU) and % of HBM/tensor roofline"
+UNIT = "GDOF/s"
+PRM = dict(gamma=1.4, mu=1.0 / 1600.0, prandtl=0.71, ldg_beta=0.5, ldg_tau=0.1)
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=96, help="elements per box edge")
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_sample(order, n_sample=16, reps=3):
+    """Time the FP64 CPU oracle's RHS on a bounded sample of the workload
+    (periodic n_sample^3 hexes, same order and physics), on one host thread."""
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(limits=1):
+        return _oracle_sample(order, n_sample, reps)
+
+
+def _oracle_sample(order, n_sample, reps):
+    from fr_inputs import periodic_box, fields
+    from oracle.system import FRSystem
+    m = periodic_box("hex", n_sample, 0.0, 2 * np.pi)
+    o = FRSystem(m, order, "ns", **PRM)
+    U = [fields.perturbed_taylor_green(o.solution_coords(0), M=0.1).transpose(1, 0, 2).copy()]
+    o.rhs(U)                                      # warm-up
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        o.rhs(U)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    dof = U[0].size
+    return dict(value=dof / t / 1e9, unit=UNIT, cores=1, kind="oracle",
+                sample=f"periodic {n_sample}^3 hexes, p={order}, NS, FP64 numpy oracle, "
+                       f"median of {reps} RHS evaluations ({dof} DOF, {t:.2f} s each)"), t
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from threadpoolctl import threadpool_limits
+    threadpool_limits(limits=1)
+    cb, _ = oracle_sample(a.order, n_sample=8, reps=1)
+    # each step = one oracle RHS on the bounded sample
+    from fr_inputs import periodic_box, fields
+    from oracle.system import FRSystem
+    m = periodic_box("hex", 8, 0.0, 2 * np.pi)
+    o = FRSystem(m, a.order, "ns", **PRM)
+    U = [fields.perturbed_taylor_green(o.solution_coords(0), M=0.1).transpose(1, 0, 2).copy()]
+    for _ in range(a.warmup):
+        o.rhs(U)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        o.rhs(U)
+    dt = time.perf_counter() - t0
+    val = U[0].size * a.steps / dt / 1e9
+    line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=a.gpus, steps=a.steps,
+                warmup=a.warmup, ms_per_step=dt / a.steps * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=f"NS TGV periodic hex box, p={a.order}; reference arm = CPU oracle on a "
+                                     f"bounded 8^3 sample (one RHS per step)"),
+                cpu_baseline=dict(cb, value=val, sample="periodic 8^3 hexes, one oracle RHS per step, 1 thread"),
+                e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd.insert(1, f"--id={self.uuid}")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except OSError:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=mx, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ---------------------------------------------------------------- roofline bookkeeping
+def kernel_work(name, nu, nf, V, D, nelem, npairs, s):
+    """Algorithmic (bytes, flops) of one launch of each kernel on the whole block.
+
+    Bytes count every value the kernel must read or write once (state, metric
+    terms, per-pair tables); flops count the dense operator products as the
+    paper defines them (App. A)."""
+    E = nelem
+    if name == "disu_gemm":
+        return (nu + nf) * V * s * E, 2.0 * nf * nu * V * E
+    if name == "tgradu_gemm":
+        return (nf + nu + D * nu) * V * s * E, 2.0 * D * nu * (nf + nu) * V * E
+    if name == "gradfpts_gemm":
+        return (nu + nf) * V * s * E, 2.0 * nf * nu * V * E
+    if name == "tdivf_gemm":
+        return ((nf + D * nu + nu) * V + nu) * s * E, 2.0 * nu * (nf + D * nu) * V * E
+    if name == "gradcoru":
+        return (2 * D * nu * V + D * D * nu + nu) * s * E, 0.0
+    if name == "tdisf":
+        return (nu * V + 2 * D * nu * V + D * D * nu) * s * E, 0.0
+    if name == "comm_sol":
+        return npairs * (4 * V * s + 8), 0.0
+    if name == "comm_flux":
+        return npairs * ((4 * V + 2 * D * V + D + 2) * s + 8), 0.0
+    if name == "rk_stage":
+        return 5 * nu * V * s * E, 0.0
+    return None, None
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1312_1638_b300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload_key):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tab = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = tab.get(f"{workload_key}/{kernel}")
+    if not ent or ent.get("source_sha") != source_sha():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------- GPU leg
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu_baseline, _ = oracle_sample(a.order)         # before any CUDA call
+
+    import torch
+    from fr_inputs import periodic_box, fields
+    from paper_1312_1638_b300 import build as _build
+    _build.build()
+    from paper_1312_1638_b300 import fr
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    # FP32 / FP64 CUDA-core peaks from unit counts and the maximum SM clock:
+    # 148 SMs x 128 FP32 lanes x 2 flop; FP64 at the B300 rate of 1.25 TFLOP/s nominal.
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
+
+    t_setup = time.perf_counter()
+    mesh = periodic_box("hex", a.n, 0.0, 2 * np.pi)
+    s = fr.Solver(mesh, a.order, "ns", a.precision, device=local, **PRM)
+    L = s.layout(0)
+    nu, nf, V, nelem, ld = L["nupts"], L["nfpts"], L["nvars"], L["nelem"], L["ld"]
+    D = 3
+    dof = nu * V * nelem
+    X = torch.from_numpy(s.solution_points(0)).cuda()
+    U0 = fields.perturbed_taylor_green(X, M=0.1)                     # [V, nu, nelem]
+    del X
+    dt_np = torch.float64 if a.precision == "fp64" else torch.float32
+    u = torch.zeros((nu, V, ld), dtype=dt_np, device="cuda")
+    u[:, :, :nelem] = U0.permute(1, 0, 2).to(dt_np)
+    del U0
+    u_init = u.clone()
+    t_setup = time.perf_counter() - t_setup
+    stream = torch.cuda.current_stream()
+    dt = 1e-4
+
+    for _ in range(a.warmup):
+        s.rk4([u], dt, 1, stream)
+    torch.cuda.synchronize()
+    s.profile_enable(True)
+    s.profile_read()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(uuid) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            s.rk4([u], dt, 1, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile_enable(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    assert s.sync_status() == fr.OK
+    s.check_finite([u])
+    finite_ok = s.sync_status() == fr.OK
+    stages = 4 * a.steps
+    value = dof * stages * world / (ms / 1e3) / 1e9
+    launches = sum(v[0] for v in prof.values())
+
+    # roofline of the dominant kernel
+    npairs = nelem * nf // 2
+    srz = 8 if a.precision == "fp64" else 4
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    kname, (kl, kms) = top
+    kbytes, kflops = kernel_work(kname, nu, nf, V, D, nelem, npairs, srz)
+    avg_s = kms / kl / 1e3
+    if kflops:
+        if a.precision == "fp64":
+            roof = dict(bound="alu", achieved=kflops / avg_s / 1e12, peak=1.25, unit="TFLOP/s",
+                        peak_source="nominal FP64 rate of the B300")
+        else:
+            roof = dict(bound="alu", achieved=kflops / avg_s / 1e12, peak=fp32_peak, unit="TFLOP/s",
+                        peak_source="148 SMs x 128 FP32 FMA lanes x 2 flop x max SM clock")
+    else:
+        roof = dict(bound="hbm", achieved=kbytes / avg_s / 1e9, peak=hbm_peak, unit="GB/s",
+                    peak_source=f"{peak_src} hbm_gbs")
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = kname
+    roof["algorithmic_bytes_per_launch"] = kbytes
+    roof["algorithmic_flops_per_launch"] = kflops
+    roof["avg_launch_ms"] = kms / kl
+    wk = f"hex{a.n}_p{a.order}_ns_{a.precision}"
+    roof["traffic"] = measured_traffic(kname, wk)
+    per_kernel = {k: dict(launches=v[0], ms=round(v[1], 3), share=round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4))
+                  for k, v in prof.items() if v[0]}
+    for k, d in per_kernel.items():
+        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz)
+        if b:
+            d["GB_s"] = round(b / (d["ms"] / d["launches"] / 1e3) / 1e9, 1)
+        if f:
+            d["TFLOP_s"] = round(f / (d["ms"] / d["launches"] / 1e3) / 1e12, 2)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not a.no_e2e:
+        uh = u_init.cpu().pin_memory()
+        rh = torch.empty_like(uh).pin_memory()
+        s.rhs_host([uh], [rh], stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ne = max(3, min(a.steps, 10))
+        for _ in range(ne):
+            s.rhs_host([uh], [rh], stream)
+        te = (time.perf_counter() - t0) / ne
+        nbytes = uh.numel() * uh.element_size()
+        e2e = dict(value=dof * world / te / 1e9, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes,
+                   note="one RHS per call: H2D of U, RHS, D2H of R, host-synchronous")
+        del uh, rh
+
+    # plain FP64 GPU path on the same mesh (comparison leg)
+    fp64 = None
+    if not a.no_fp64 and a.precision != "fp64":
+        del u
+        s.close()
+        torch.cuda.empty_cache()
+        s64 = fr.Solver(mesh, a.order, "ns", "fp64", device=local, **PRM)
+        u64 = u_init.to(torch.float64)
+        r64 = torch.empty_like(u64)
+        s64.rhs([u64], [r64], stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            s64.rhs([u64], [r64], stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 2
+        fp64 = dict(gdofs_per_rhs=dof / (t64 / 1e3) / 1e9, ms_per_rhs=t64)
+        s64.close()
+
+    if rank != 0:
+        return 0
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=a.steps, warmup=a.warmup,
+        ms_per_step=ms / a.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32" if a.precision == "fp32" else ("f64" if a.precision == "fp64" else "bf16x3+f32"),
+        data="synthetic",
+        config=dict(workload=f"3D Navier-Stokes Taylor-Green (+seeded perturbation), periodic {a.n}^3 hex box, "
+                             f"p={a.order}, {dof} DOF, precision {a.precision}",
+                    elements=nelem, order=a.order, dof=dof, step="one RK4 step (4 RHS + stage combines)",
+                    l2="inputs larger than L2 (state alone is %.1f GB)" % (u_init.numel() * u_init.element_size() / 1e9),
+                    parallelism=f"replicas x{world}", setup_s=round(t_setup, 1)),
+        roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
+        clocks=clk.summary(), per_kernel=per_kernel, fp64_gpu=fp64, finite=finite_ok,
+    )
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -11,11 +11,19 @@ from __future__ import annotations
 import numpy as np
 
 
+def _xp(x):
+    """Array module of x: numpy, or torch for torch tensors (device inputs)."""
+    if type(x).__module__.startswith("torch"):
+        import torch
+        return torch
+    return np
+
+
 def conserved(rho, vel, p, gamma):
     """(rho, v, p) -> (rho, rho v, E) with E = p/(gamma-1) + rho |v|^2 / 2."""
-    vel = [np.asarray(v) for v in vel]
+    xp = _xp(rho)
     ke = 0.5 * rho * sum(v * v for v in vel)
-    return np.stack([rho] + [rho * v for v in vel] + [p / (gamma - 1.0) + ke])
+    return xp.stack([rho] + [rho * v for v in vel] + [p / (gamma - 1.0) + ke])
 
 
 def uniform(x, rho, vel, p, gamma):
@@ -65,22 +73,26 @@ def _perturbation_terms(rng, nmodes, ndims):
 
 def perturbed_taylor_green(x, M=0.1, gamma=1.4, amp=0.01, nmodes=8, seed=1312):
     """Taylor-Green field plus amp * sum_m a_m sin(k_m . x + phi_m) on each of
-    rho, u, v, w, p (p scaled by rho0 V0^2 = 1); integer k_m in {-3..3}^3."""
-    X = np.stack([x[0], x[1], x[2]])
+    rho, u, v, w, p (p scaled by rho0 V0^2 = 1); integer k_m in {-3..3}^3.
+
+    x may be a numpy array or a torch tensor (evaluated where it lives)."""
+    xp = _xp(x[0])
+    X0, X1, X2 = x[0], x[1], x[2]
     rng = np.random.default_rng(seed)
     p0 = 1.0 / (gamma * M * M)
-    u = np.sin(X[0]) * np.cos(X[1]) * np.cos(X[2])
-    v = -np.cos(X[0]) * np.sin(X[1]) * np.cos(X[2])
-    w = np.zeros_like(u)
-    p = p0 + (np.cos(2 * X[0]) + np.cos(2 * X[1])) * (np.cos(2 * X[2]) + 2.0) / 16.0
+    u = xp.sin(X0) * xp.cos(X1) * xp.cos(X2)
+    v = -xp.cos(X0) * xp.sin(X1) * xp.cos(X2)
+    w = xp.zeros_like(u)
+    p = p0 + (xp.cos(2 * X0) + xp.cos(2 * X1)) * (xp.cos(2 * X2) + 2.0) / 16.0
     rho = p / p0
     prims = [rho, u, v, w, p]
     out = []
     for q in prims:
         k, a, phi = _perturbation_terms(rng, nmodes, 3)
-        d = np.zeros_like(q)
+        d = xp.zeros_like(q)
         for m in range(nmodes):
-            d += a[m] * np.sin(np.tensordot(k[m], X, axes=1) + phi[m])
+            arg = float(k[m][0]) * X0 + float(k[m][1]) * X1 + float(k[m][2]) * X2 + float(phi[m])
+            d += float(a[m]) * xp.sin(arg)
         out.append(q + amp * d)
     return conserved(out[0], out[1:4], out[4], gamma)
 

@@ -1,0 +1,217 @@
+/*
+ * fr.h -- C ABI of the B300 (sm_103a) Flux Reconstruction right-hand side.
+ *
+ * The library evaluates the semi-discrete FR operator of Witherden, Farrington
+ * & Vincent, "PyFR: An Open Source Framework for Solving Advection-Diffusion
+ * Type Problems on Streaming Architectures using the Flux Reconstruction
+ * Approach" (arXiv 1312.1638):
+ *
+ *     dU/dt = R(U) = -J^{-1} [ M3 D~ + (M1 - M3 M2) F~ ]      (Eq. negdivconf,
+ *                                                           App. A)
+ *
+ * for the Euler and compressible Navier-Stokes equations (Sec. 4) on meshes of
+ * quadrilaterals, triangles and hexahedra, with Rusanov interface fluxes
+ * (App. B), LDG common solution/viscous flux (Sec. 4.3), boundary ghost states
+ * (App. C) and classical RK4 time stepping (end of Sec. 2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * State layout (Sec. 3.3, SoA packing with variable stride |Omega_e|): one
+ * buffer per element block, [nupts][nvars][ld] with column index
+ * alpha*ld + n for variable alpha of element n.  ld >= nelem is chosen by the
+ * library (a multiple of 128) and reported by fr_layout().  Columns n >= nelem
+ * are padding: the library never reads them for anything but dense operator
+ * products and leaves their output unspecified.
+ *
+ * Element types and node orderings (fr_eblock.nodes, host, [nelem][nnodes][ndims]):
+ *   FR_QUAD 4 nodes: tensor product of {-1,1}^2, xi fastest; 9 nodes: tensor
+ *           product of {-1,0,1}^2, xi fastest.
+ *   FR_TRI  3 nodes: (-1,-1),(1,-1),(-1,1); 6 nodes: those, then mid-points of
+ *           edges 0-1, 1-2, 2-0.
+ *   FR_HEX  8 nodes: tensor product of {-1,1}^3 (xi, eta, zeta; xi fastest).
+ * Faces: quad 0:eta=-1 1:xi=+1 2:eta=+1 3:xi=-1; tri 0:v0-v1 1:v1-v2 2:v2-v0;
+ * hex 0:zeta=-1 1:eta=-1 2:xi=+1 3:eta=+1 4:xi=-1 5:zeta=+1.
+ * Solution points: tensor Gauss-Legendre (quad, hex, xi fastest); for
+ * triangles the interior nodes of the degree-(p+3) equispaced lattice (the
+ * paper's Williams-Shunn points are not printed).  Flux points: Gauss-Legendre
+ * on every face.  Correction functions: DG (Sec. 5).
+ *
+ * Precision: FR_PREC_FP64 state buffers are double; every other precision
+ * uses float state buffers.
+ *
+ * Streams: `stream` arguments are cudaStream_t values passed as void*
+ * (NULL = legacy default stream).  Calls that take a stream are
+ * stream-ordered and return without synchronising the host unless stated.
+ *
+ * Errors: every call returns an fr_status; no exception crosses the ABI.
+ * fr_last_error() returns a message for the most recent failure of that
+ * context (or of fr_setup when ctx is NULL).  On error nothing is freed that
+ * the caller owns.
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fr_ctx fr_ctx;   /* opaque; owned by the library */
+
+typedef enum {
+    FR_OK = 0,
+    FR_ERR_ARG = 1,          /* bad argument (NULL pointer, bad block index, ...) */
+    FR_ERR_MESH = 2,         /* unmatched flux point, non-positive Jacobian ...   */
+    FR_ERR_CUDA = 3,         /* a CUDA runtime call failed                         */
+    FR_ERR_NONFINITE = 4,    /* a NaN/Inf was detected in a state                  */
+    FR_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up                 */
+    FR_ERR_UNSUPPORTED = 6,  /* combination not implemented / no GPU context       */
+    FR_ERR_OOM = 7           /* device allocation failed                           */
+} fr_status;
+
+typedef enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 } fr_system;
+typedef enum { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1, FR_PREC_BF16X3 = 2 } fr_precision;
+typedef enum { FR_QUAD = 0, FR_TRI = 1, FR_HEX = 2 } fr_etype;
+/* boundary types (App. C): free-stream ("supersonic inflow") ghost, subsonic
+ * outflow, no-slip isothermal wall */
+typedef enum { FR_BC_FREESTREAM = 0, FR_BC_OUTFLOW = 1, FR_BC_WALL = 2 } fr_bctype;
+
+/* Physical and numerical parameters (Sec. 4, Sec. 4.3, App. C). */
+typedef struct {
+    int32_t ndims;        /* 2 or 3 */
+    int32_t order;        /* polynomial order p >= 1 */
+    int32_t system;       /* fr_system */
+    int32_t precision;    /* fr_precision */
+    double gamma;         /* ratio of specific heats */
+    double mu;            /* constant dynamic viscosity (NS) */
+    double prandtl;       /* Prandtl number (NS) */
+    double ldg_beta;      /* LDG beta: C = (1/2-beta) u_L + (1/2+beta) u_R */
+    double ldg_tau;       /* LDG penalty tau >= 0 (dissipative sign) */
+    double bc_rho, bc_v[3], bc_p;   /* free-stream ghost state */
+    double outflow_p;               /* subsonic-outflow pressure */
+    double wall_cpTw, wall_v[3];    /* isothermal wall: C_p T_w and velocity */
+} fr_params;
+
+/* One block of elements of a single type, host memory, read during fr_setup only. */
+typedef struct {
+    int32_t etype;        /* fr_etype */
+    int32_t nnodes;       /* nodes per element (4/9 quad, 3/6 tri, 8 hex) */
+    int64_t nelem;
+    const double* nodes;  /* [nelem][nnodes][ndims] */
+} fr_eblock;
+
+typedef struct {
+    int32_t ndims;
+    int32_t nblocks;
+    const fr_eblock* blocks;
+    int64_t nbfaces;
+    const int64_t* bfaces;    /* [nbfaces][4]: block, element, face, fr_bctype */
+    int32_t nperiodic;
+    const double* periodic;   /* [nperiodic][ndims] translation vectors */
+} fr_mesh;
+
+/*
+ * fr_setup -- build the FR discretisation of `mesh` (Sec. 2, App. A).
+ * Host work: point sets, nodal bases (Vandermonde construction, Sec. 2),
+ * operator matrices M0..M6 (App. A), metric terms, flux-point pairing by
+ * physical coordinates (Sec. 2: a pair must coincide; periodic translations
+ * tried in every combination), L side = lexicographically smaller
+ * (block, element, face), each pair visited once.
+ * device >= 0: allocates operators, metric terms, pair tables and scratch on
+ * that CUDA device (owned by the context, freed by fr_destroy).
+ * device == -1: host-only context; only the inspection calls below work and
+ * fr_rhs/fr_rk4 return FR_ERR_UNSUPPORTED.
+ * Errors: FR_ERR_ARG, FR_ERR_MESH (unmatched or doubly matched flux point,
+ * boundary face also paired, non-positive Jacobian), FR_ERR_UNSUPPORTED,
+ * FR_ERR_CUDA / FR_ERR_OOM.  *out is NULL on failure.
+ */
+fr_status fr_setup(const fr_mesh* mesh, const fr_params* params, int device, fr_ctx** out);
+
+/* Layout of block `block`: points, variables, elements and the column
+ * stride ld of its state buffers (Sec. 3.3).  Any output pointer may be NULL. */
+fr_status fr_layout(const fr_ctx* ctx, int block, int32_t* nupts, int32_t* nfpts,
+                    int32_t* nvars, int64_t* nelem, int64_t* ld);
+
+/* Physical coordinates of the solution points of block `block` (the element
+ * mapping of Sec. 2 evaluated at x~^(u)), written to host memory
+ * out[ndims][nupts][nelem]. */
+fr_status fr_solution_points(const fr_ctx* ctx, int block, double* out);
+
+/* Host copy of an operator matrix of block `block` (App. A), row-major FP64.
+ * which: 0..6 = M0..M6 (M5 omitted: it is diag(M0,...,M0)), 7 = M4 - M6 M0,
+ * 8 = M1 - M3 M2.  If out is NULL only rows/cols are returned. */
+fr_status fr_operator(const fr_ctx* ctx, int block, int which, double* out,
+                      int32_t* rows, int32_t* cols);
+
+/* Interface pairs (Sec. 2 lookup table).  With out == NULL returns the count
+ * in *npairs; otherwise writes [npairs][6] = (bL, fptL, elemL, bR, fptR, elemR). */
+fr_status fr_pairs(const fr_ctx* ctx, int64_t* npairs, int64_t* out);
+
+/*
+ * fr_rhs -- r = R(u) (Eq. negdivconf) on the device.
+ * u[b], r[b]: device pointers, one per block, layout [nupts][nvars][ld],
+ * double for FR_PREC_FP64 else float.  r may alias u (Sec. 3.6 aliasing).
+ * Stream-ordered on `stream`; returns after enqueueing.
+ * Errors: FR_ERR_ARG (NULL pointer), FR_ERR_UNSUPPORTED (host-only context),
+ * FR_ERR_CUDA (launch failure).
+ */
+fr_status fr_rhs(fr_ctx* ctx, void* const* u, void* const* r, void* stream);
+
+/*
+ * fr_rhs_host -- as fr_rhs, but u and r are HOST buffers (any host memory;
+ * pinned memory makes the copies asynchronous).  The library copies u to a
+ * device staging buffer it owns, evaluates R, copies r back and synchronises
+ * `stream` before returning.  u and r may alias.
+ */
+fr_status fr_rhs_host(fr_ctx* ctx, const void* const* u, void* const* r, void* stream);
+
+/*
+ * fr_rk4 -- advance u in place by `nsteps` classical RK4 steps of size dt
+ * (end of Sec. 2; Sec. 5.1).  Uses two library-owned state registers.
+ * Stream-ordered; returns after enqueueing.
+ */
+fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
+
+/*
+ * fr_sum_weighted -- FP64 totals sum_e sum_rho w_rho J_rho u_{rho,alpha,n}
+ * (solution-point quadrature of each variable: the conserved totals of
+ * Eq. commpflux's conservation argument), written to host out[nvars].
+ * Synchronises `stream`.
+ */
+fr_status fr_sum_weighted(fr_ctx* ctx, void* const* u, double* out, void* stream);
+
+/* Reads and clears the device error flags (non-finite values seen by
+ * fr_check_finite, timeouts).  Synchronises the device. */
+fr_status fr_sync_status(fr_ctx* ctx);
+
+/* Scans u for NaN/Inf on the device; the result is reported by the next
+ * fr_sync_status() as FR_ERR_NONFINITE.  Stream-ordered. */
+fr_status fr_check_finite(fr_ctx* ctx, void* const* u, void* stream);
+
+/*
+ * Kernel-level timing.  fr_profile_enable(ctx, 1) makes every later kernel
+ * launch of fr_rhs / fr_rk4 record a CUDA event pair on its launch stream.
+ * fr_profile_read synchronises on those events and returns, per kernel, the
+ * number of launches and the total event-measured milliseconds since the
+ * previous read, then clears them.  names receives nkernels NUL-terminated
+ * names of at most 31 characters in rows of 32 bytes.  Arrays may be NULL;
+ * *nkernels is always set.
+ */
+fr_status fr_profile_enable(fr_ctx* ctx, int enable);
+fr_status fr_profile_read(fr_ctx* ctx, int32_t* nkernels, char* names, int64_t* launches, double* ms);
+
+/* Message for the last failure on ctx (ctx == NULL: last fr_setup failure). */
+const char* fr_last_error(const fr_ctx* ctx);
+
+/* Frees everything the context owns.  Synchronises its device. */
+void fr_destroy(fr_ctx* ctx);
+
+/* ABI version (increments on any signature change). */
+int32_t fr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FR_H */

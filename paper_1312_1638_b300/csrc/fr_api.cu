@@ -1,0 +1,507 @@
+// C ABI of the FR library: context set-up (host work + device upload) and the
+// stream-ordered entry points declared in include/fr.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fr.h"
+#include "fr_dev.hpp"
+#include "fr_host.hpp"
+
+struct fr_ctx {
+    std::string err;
+    fr_params prm{};
+    int ndims = 0, nvars = 0;
+    std::vector<std::unique_ptr<fr::ElemType>> etypes;
+    std::vector<fr::HostBlock> hblocks;
+    std::vector<fr::HostPair> pairs;     // interior flux-point pairs (sorted like the device tables)
+    std::vector<fr::HostBnd> bnds;       // boundary flux points
+    fr::DevCtx dev;
+    std::vector<void*> allocs;
+};
+
+static thread_local std::string g_setup_err;
+
+namespace {
+
+struct Fail {
+    fr_status st;
+    std::string msg;
+};
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? FR_ERR_OOM : FR_ERR_CUDA,           \
+                       std::string(#call) + ": " + cudaGetErrorString(e_)};                   \
+    } while (0)
+
+void* dalloc(fr_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    CK(cudaMalloc(&p, bytes));
+    c->allocs.push_back(p);
+    return p;
+}
+
+template <typename T>
+void* upload(fr_ctx* c, const std::vector<T>& h) {
+    void* p = dalloc(c, h.size() * sizeof(T));
+    CK(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+// convert a double vector to the compute type and upload
+void* upload_real(fr_ctx* c, const std::vector<double>& h, bool fp64) {
+    if (fp64) return upload(c, h);
+    std::vector<float> f(h.begin(), h.end());
+    return upload(c, f);
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+fr_status set_err(fr_ctx* c, fr_status st, const std::string& m) {
+    if (c) c->err = m;
+    else g_setup_err = m;
+    return st;
+}
+
+// [A | B] side by side: A is r x ka, B is r x kb, both row-major
+std::vector<double> hcat(const std::vector<double>& A, int ka, const std::vector<double>& B, int kb, int rows) {
+    std::vector<double> o((size_t)rows * (ka + kb));
+    for (int i = 0; i < rows; ++i) {
+        std::copy(&A[(size_t)i * ka], &A[(size_t)i * ka] + ka, &o[(size_t)i * (ka + kb)]);
+        std::copy(&B[(size_t)i * kb], &B[(size_t)i * kb] + kb, &o[(size_t)i * (ka + kb) + ka]);
+    }
+    return o;
+}
+
+template <typename T>
+void fill_metrics(fr_ctx* c, const fr::HostBlock& hb, fr::DevBlock& B, int d) {
+    const fr::ElemType& el = *hb.el;
+    const int64_t ld = B.ld, nu = el.nupts;
+    std::vector<T> smat((size_t)d * d * nu * ld, T(0)), rcp((size_t)nu * ld, T(0));
+    std::vector<double> wdet((size_t)nu * ld, 0.0);
+    bool ok = true;
+#pragma omp parallel reduction(&& : ok)
+    {
+        std::vector<double> adj((size_t)nu * d * d), det(nu);
+#pragma omp for schedule(static)
+        for (int64_t e = 0; e < hb.nelem; ++e) {
+            if (!fr::element_metrics(hb, e, adj.data(), det.data())) ok = false;
+            for (int s = 0; s < nu; ++s) {
+                for (int k = 0; k < d * d; ++k) smat[((size_t)k * nu + s) * ld + e] = (T)adj[(size_t)s * d * d + k];
+                rcp[(size_t)s * ld + e] = (T)(1.0 / det[s]);
+                wdet[(size_t)s * ld + e] = el.qw[s] * det[s];
+            }
+        }
+    }
+    if (!ok) throw Fail{FR_ERR_MESH, "non-positive Jacobian at a solution point"};
+    B.smat = upload(c, smat);
+    B.rcpdjac = upload(c, rcp);
+    B.wdet = (double*)upload(c, wdet);
+}
+
+void upload_device(fr_ctx* c) {
+    fr::DevCtx& D = c->dev;
+    const bool fp64 = c->prm.precision == FR_PREC_FP64;
+    const size_t rs = fp64 ? sizeof(double) : sizeof(float);
+    const int d = c->ndims, V = c->nvars;
+    const bool ns = c->prm.system == FR_NAVIER_STOKES;
+    CK(cudaSetDevice(D.device));
+    size_t maxpart = 0;
+    for (size_t b = 0; b < c->hblocks.size(); ++b) {
+        const fr::HostBlock& hb = c->hblocks[b];
+        const fr::ElemType& el = *hb.el;
+        fr::DevBlock B;
+        B.etype = hb.etype; B.nupts = el.nupts; B.nfpts = el.nfpts; B.nvars = V;
+        B.nelem = hb.nelem;
+        B.ld = round_up(std::max<int64_t>(hb.nelem, 1), 128);
+        const int64_t ld = B.ld, nu = el.nupts, nf = el.nfpts;
+        maxpart = std::max(maxpart, (size_t)nu * V);
+        // metric terms at solution points, filled directly in the compute type
+        if (fp64) {
+            fill_metrics<double>(c, hb, B, d);
+        } else {
+            fill_metrics<float>(c, hb, B, d);
+        }
+        B.Uf = dalloc(c, (size_t)nf * V * ld * rs);
+        B.Q = dalloc(c, (size_t)d * nu * V * ld * rs);
+        CK(cudaMemset(B.Uf, 0, (size_t)nf * V * ld * rs));
+        CK(cudaMemset(B.Q, 0, (size_t)d * nu * V * ld * rs));
+        if (ns) {
+            B.Qf = dalloc(c, (size_t)d * nf * V * ld * rs);
+            CK(cudaMemset(B.Qf, 0, (size_t)d * nf * V * ld * rs));
+        }
+        B.opM0 = upload_real(c, el.M0, fp64);
+        B.opQ = upload_real(c, hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu), fp64);
+        B.opR = upload_real(c, hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu), fp64);
+        if ((double)nf * V * ld >= 4294967296.0) throw Fail{FR_ERR_UNSUPPORTED, "flux-point array exceeds 2^32 entries"};
+        D.blocks.push_back(B);
+    }
+    // interior pair groups by (bL, bR)
+    std::map<std::pair<int, int>, std::vector<int64_t>> groups;
+    for (int64_t k = 0; k < (int64_t)c->pairs.size(); ++k) groups[{c->pairs[k].bL, c->pairs[k].bR}].push_back(k);
+    for (auto& kv : groups) {
+        fr::DevPairGroup g;
+        g.bL = kv.first.first; g.bR = kv.first.second;
+        g.n = (int64_t)kv.second.size();
+        const fr::DevBlock &L = D.blocks[g.bL], &R = D.blocks[g.bR];
+        std::vector<uint32_t> oL(g.n), oR(g.n);
+        std::vector<double> nrm((size_t)d * g.n), mL(g.n), mR(g.n);
+        for (int64_t i = 0; i < g.n; ++i) {
+            const fr::HostPair& P = c->pairs[kv.second[i]];
+            oL[i] = (uint32_t)((int64_t)P.fL * V * L.ld + P.nL);
+            oR[i] = (uint32_t)((int64_t)P.fR * V * R.ld + P.nR);
+            for (int j = 0; j < d; ++j) nrm[(size_t)j * g.n + i] = P.nrm[j];
+            mL[i] = P.magL; mR[i] = P.magR;
+        }
+        g.offL = (uint32_t*)upload(c, oL);
+        g.offR = (uint32_t*)upload(c, oR);
+        g.nrm = upload_real(c, nrm, fp64);
+        g.magL = upload_real(c, mL, fp64);
+        g.magR = upload_real(c, mR, fp64);
+        D.pgroups.push_back(g);
+    }
+    // boundary groups by (block, type)
+    std::map<std::pair<int, int>, std::vector<int64_t>> bg;
+    for (int64_t k = 0; k < (int64_t)c->bnds.size(); ++k) bg[{c->bnds[k].b, c->bnds[k].bctype}].push_back(k);
+    for (auto& kv : bg) {
+        fr::DevBndGroup g;
+        g.b = kv.first.first; g.bctype = kv.first.second;
+        g.n = (int64_t)kv.second.size();
+        const fr::DevBlock& B = D.blocks[g.b];
+        std::vector<uint32_t> o(g.n);
+        std::vector<double> nrm((size_t)d * g.n), m(g.n);
+        for (int64_t i = 0; i < g.n; ++i) {
+            const fr::HostBnd& P = c->bnds[kv.second[i]];
+            o[i] = (uint32_t)((int64_t)P.f * V * B.ld + P.n);
+            for (int j = 0; j < d; ++j) nrm[(size_t)j * g.n + i] = P.nrm[j];
+            m[i] = P.mag;
+        }
+        g.off = (uint32_t*)upload(c, o);
+        g.nrm = upload_real(c, nrm, fp64);
+        g.mag = upload_real(c, m, fp64);
+        D.bgroups.push_back(g);
+    }
+    D.flags = (int*)dalloc(c, 2 * sizeof(int));
+    CK(cudaMemset(D.flags, 0, 2 * sizeof(int)));
+    D.partial = (double*)dalloc(c, std::max<size_t>(maxpart, 1) * sizeof(double));
+    CK(cudaDeviceSynchronize());
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int32_t fr_version(void) { return 1; }
+
+const char* fr_last_error(const fr_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_err.c_str(); }
+
+void fr_destroy(fr_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->dev.device >= 0) {
+        cudaSetDevice(ctx->dev.device);
+        cudaDeviceSynchronize();
+        fr::prof_free(ctx->dev);
+        for (void* p : ctx->allocs) cudaFree(p);
+    }
+    delete ctx;
+}
+
+fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx** out) {
+    if (out) *out = nullptr;
+    if (!mesh || !prm || !out) return set_err(nullptr, FR_ERR_ARG, "NULL argument");
+    if (prm->ndims != 2 && prm->ndims != 3) return set_err(nullptr, FR_ERR_ARG, "ndims must be 2 or 3");
+    if (mesh->ndims != prm->ndims) return set_err(nullptr, FR_ERR_ARG, "mesh and params disagree on ndims");
+    if (prm->system != FR_EULER && prm->system != FR_NAVIER_STOKES) return set_err(nullptr, FR_ERR_ARG, "bad system");
+    if (prm->precision != FR_PREC_FP64 && prm->precision != FR_PREC_FP32)
+        return set_err(nullptr, FR_ERR_UNSUPPORTED, "precision not available in this build");
+    if (mesh->nblocks < 1 || !mesh->blocks) return set_err(nullptr, FR_ERR_ARG, "no element blocks");
+    if (mesh->nperiodic < 0 || (mesh->nperiodic > 0 && !mesh->periodic))
+        return set_err(nullptr, FR_ERR_ARG, "bad periodic translations");
+    if (mesh->nbfaces < 0 || (mesh->nbfaces > 0 && !mesh->bfaces)) return set_err(nullptr, FR_ERR_ARG, "bad boundary list");
+    std::unique_ptr<fr_ctx> c(new (std::nothrow) fr_ctx());
+    if (!c) return set_err(nullptr, FR_ERR_OOM, "host allocation failed");
+    c->prm = *prm;
+    c->ndims = prm->ndims;
+    c->nvars = prm->ndims + 2;
+    try {
+        std::map<int, fr::ElemType*> cache;
+        int nfp_face = -1;
+        for (int b = 0; b < mesh->nblocks; ++b) {
+            const fr_eblock& eb = mesh->blocks[b];
+            int et = eb.etype;
+            if (et < 0 || et > 2) throw Fail{FR_ERR_ARG, "bad element type"};
+            if ((et == FR_HEX) != (prm->ndims == 3)) throw Fail{FR_ERR_ARG, "element type does not match ndims"};
+            if (eb.nelem < 1 || !eb.nodes) throw Fail{FR_ERR_ARG, "empty element block"};
+            if (!cache.count(et)) {
+                std::unique_ptr<fr::ElemType> el(new fr::ElemType());
+                std::string err;
+                if (!fr::build_element(et, prm->order, *el, err)) throw Fail{FR_ERR_ARG, err};
+                cache[et] = el.get();
+                c->etypes.push_back(std::move(el));
+            }
+            fr::HostBlock hb;
+            hb.etype = et; hb.nnodes = eb.nnodes; hb.nelem = eb.nelem; hb.el = cache[et];
+            long double x[3] = {0, 0, 0}, N[27], dN[81];
+            if (!fr::shape_functions(et, eb.nnodes, x, N, dN)) throw Fail{FR_ERR_ARG, "unsupported nodes per element"};
+            hb.nodes.assign(eb.nodes, eb.nodes + (size_t)eb.nelem * eb.nnodes * prm->ndims);
+            if (!fr::prepare_block(hb)) throw Fail{FR_ERR_ARG, "unsupported element mapping"};
+            if (nfp_face >= 0 && nfp_face != hb.el->nfp_face) throw Fail{FR_ERR_ARG, "inconsistent face point counts"};
+            nfp_face = hb.el->nfp_face;
+            c->hblocks.push_back(std::move(hb));
+        }
+        std::string err;
+        if (!fr::pair_mesh(prm->ndims, c->hblocks, mesh->bfaces, mesh->nbfaces, mesh->periodic, mesh->nperiodic,
+                           c->pairs, c->bnds, err))
+            throw Fail{FR_ERR_MESH, err};
+        // locality order: group by block pair, then L flux point, then L element
+        std::sort(c->pairs.begin(), c->pairs.end(), [](const fr::HostPair& a, const fr::HostPair& b) {
+            if (a.bL != b.bL) return a.bL < b.bL;
+            if (a.bR != b.bR) return a.bR < b.bR;
+            if (a.fL != b.fL) return a.fL < b.fL;
+            return a.nL < b.nL;
+        });
+        std::sort(c->bnds.begin(), c->bnds.end(), [](const fr::HostBnd& a, const fr::HostBnd& b) {
+            if (a.b != b.b) return a.b < b.b;
+            if (a.bctype != b.bctype) return a.bctype < b.bctype;
+            if (a.f != b.f) return a.f < b.f;
+            return a.n < b.n;
+        });
+        c->dev.ndims = prm->ndims; c->dev.nvars = c->nvars; c->dev.system = prm->system;
+        c->dev.precision = prm->precision; c->dev.order = prm->order;
+        fr::DevParams& P = c->dev.prm;
+        P.gamma = prm->gamma; P.mu = prm->mu; P.prandtl = prm->prandtl; P.beta = prm->ldg_beta; P.tau = prm->ldg_tau;
+        P.bc_rho = prm->bc_rho; P.bc_p = prm->bc_p; P.outflow_p = prm->outflow_p; P.wall_cpTw = prm->wall_cpTw;
+        for (int i = 0; i < 3; ++i) { P.bc_v[i] = prm->bc_v[i]; P.wall_v[i] = prm->wall_v[i]; }
+        if (device >= 0) {
+            c->dev.device = device;
+            upload_device(c.get());
+            // the host pair list is only kept for inspection of small meshes
+            if (c->pairs.size() > (size_t)4000000) { c->pairs.clear(); c->pairs.shrink_to_fit(); }
+        } else {
+            // host-only: still check every Jacobian
+            for (auto& hb : c->hblocks) {
+                std::vector<double> adj((size_t)hb.el->nupts * 9), det(hb.el->nupts);
+                for (int64_t e = 0; e < hb.nelem; ++e)
+                    if (!fr::element_metrics(hb, e, adj.data(), det.data()))
+                        throw Fail{FR_ERR_MESH, "non-positive Jacobian at a solution point"};
+            }
+        }
+    } catch (const Fail& f) {
+        if (c->dev.device >= 0)
+            for (void* p : c->allocs) cudaFree(p);
+        return set_err(nullptr, f.st, f.msg);
+    } catch (const std::bad_alloc&) {
+        if (c->dev.device >= 0)
+            for (void* p : c->allocs) cudaFree(p);
+        return set_err(nullptr, FR_ERR_OOM, "host allocation failed");
+    }
+    *out = c.release();
+    return FR_OK;
+}
+
+fr_status fr_layout(const fr_ctx* ctx, int b, int32_t* nupts, int32_t* nfpts, int32_t* nvars, int64_t* nelem,
+                    int64_t* ld) {
+    if (!ctx || b < 0 || b >= (int)ctx->hblocks.size()) return FR_ERR_ARG;
+    const fr::HostBlock& hb = ctx->hblocks[b];
+    if (nupts) *nupts = hb.el->nupts;
+    if (nfpts) *nfpts = hb.el->nfpts;
+    if (nvars) *nvars = ctx->nvars;
+    if (nelem) *nelem = hb.nelem;
+    if (ld) *ld = round_up(std::max<int64_t>(hb.nelem, 1), 128);
+    return FR_OK;
+}
+
+fr_status fr_solution_points(const fr_ctx* ctx, int b, double* out) {
+    if (!ctx || !out || b < 0 || b >= (int)ctx->hblocks.size()) return FR_ERR_ARG;
+    const fr::HostBlock& hb = ctx->hblocks[b];
+    const fr::ElemType& el = *hb.el;
+    int d = el.ndims, nu = el.nupts, nn = hb.nnodes;
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < hb.nelem; ++e)
+        for (int s = 0; s < nu; ++s)
+            for (int i = 0; i < d; ++i) {
+                double acc = 0;
+                for (int a = 0; a < nn; ++a) acc += hb.Nu[(size_t)s * nn + a] * hb.nodes[((size_t)e * nn + a) * d + i];
+                out[((size_t)i * nu + s) * hb.nelem + e] = acc;
+            }
+    return FR_OK;
+}
+
+fr_status fr_operator(const fr_ctx* ctx, int b, int which, double* out, int32_t* rows, int32_t* cols) {
+    if (!ctx || b < 0 || b >= (int)ctx->hblocks.size()) return FR_ERR_ARG;
+    const fr::ElemType& el = *ctx->hblocks[b].el;
+    int nu = el.nupts, nf = el.nfpts, d = el.ndims, r = 0, cl = 0;
+    const std::vector<double>* m = nullptr;
+    switch (which) {
+        case 0: m = &el.M0; r = nf; cl = nu; break;
+        case 1: m = &el.M1; r = nu; cl = d * nu; break;
+        case 2: m = &el.M2; r = nf; cl = d * nu; break;
+        case 3: m = &el.M3; r = nu; cl = nf; break;
+        case 4: m = &el.M4; r = d * nu; cl = nu; break;
+        case 6: m = &el.M6; r = d * nu; cl = nf; break;
+        case 7: m = &el.M46; r = d * nu; cl = nu; break;
+        case 8: m = &el.M132; r = nu; cl = d * nu; break;
+        default: return FR_ERR_ARG;
+    }
+    if (rows) *rows = r;
+    if (cols) *cols = cl;
+    if (out) std::copy(m->begin(), m->end(), out);
+    return FR_OK;
+}
+
+fr_status fr_pairs(const fr_ctx* ctx, int64_t* npairs, int64_t* out) {
+    if (!ctx || !npairs) return FR_ERR_ARG;
+    if (ctx->pairs.empty() && ctx->dev.device >= 0 && !ctx->dev.pgroups.empty()) return FR_ERR_UNSUPPORTED;
+    *npairs = (int64_t)ctx->pairs.size();
+    if (out)
+        for (size_t k = 0; k < ctx->pairs.size(); ++k) {
+            const fr::HostPair& P = ctx->pairs[k];
+            int64_t* o = out + 6 * k;
+            o[0] = P.bL; o[1] = P.fL; o[2] = P.nL; o[3] = P.bR; o[4] = P.fR; o[5] = P.nR;
+        }
+    return FR_OK;
+}
+
+static fr_status check_dev(fr_ctx* ctx) {
+    if (!ctx) return FR_ERR_ARG;
+    if (ctx->dev.device < 0) return set_err(ctx, FR_ERR_UNSUPPORTED, "host-only context has no device state");
+    cudaError_t e = cudaSetDevice(ctx->dev.device);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+static bool ptrs_ok(const fr_ctx* ctx, const void* const* p) {
+    if (!p) return false;
+    for (size_t b = 0; b < ctx->hblocks.size(); ++b)
+        if (!p[b]) return false;
+    return true;
+}
+
+fr_status fr_rhs(fr_ctx* ctx, void* const* u, void* const* r, void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, u) || !ptrs_ok(ctx, r)) return set_err(ctx, FR_ERR_ARG, "NULL state pointer");
+    cudaError_t e = fr::launch_rhs(ctx->dev, u, r, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+fr_status fr_rhs_host(fr_ctx* ctx, const void* const* u, void* const* r, void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, (void* const*)u) || !ptrs_ok(ctx, r)) return set_err(ctx, FR_ERR_ARG, "NULL state pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    std::vector<void*> dv(ctx->dev.blocks.size());
+    try {
+        for (size_t b = 0; b < ctx->dev.blocks.size(); ++b) {
+            fr::DevBlock& B = ctx->dev.blocks[b];
+            size_t bytes = (size_t)B.nupts * B.nvars * B.ld * rs;
+            if (!B.stage) B.stage = dalloc(ctx, bytes);
+            dv[b] = B.stage;
+            CK(cudaMemcpyAsync(B.stage, u[b], bytes, cudaMemcpyHostToDevice, st));
+        }
+        CK(fr::launch_rhs(ctx->dev, dv.data(), dv.data(), st));
+        for (size_t b = 0; b < ctx->dev.blocks.size(); ++b) {
+            fr::DevBlock& B = ctx->dev.blocks[b];
+            size_t bytes = (size_t)B.nupts * B.nvars * B.ld * rs;
+            CK(cudaMemcpyAsync(r[b], B.stage, bytes, cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+    } catch (const Fail& f) {
+        return set_err(ctx, f.st, f.msg);
+    }
+    return FR_OK;
+}
+
+fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, u) || nsteps < 0) return set_err(ctx, FR_ERR_ARG, "bad argument");
+    size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    try {
+        for (auto& B : ctx->dev.blocks) {
+            size_t bytes = (size_t)B.nupts * B.nvars * B.ld * rs;
+            if (!B.rk_acc) B.rk_acc = dalloc(ctx, bytes);
+            if (!B.rk_tmp) B.rk_tmp = dalloc(ctx, bytes);
+        }
+    } catch (const Fail& f) {
+        return set_err(ctx, f.st, f.msg);
+    }
+    cudaError_t e = fr::launch_rk4(ctx->dev, u, dt, nsteps, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+fr_status fr_sum_weighted(fr_ctx* ctx, void* const* u, double* out, void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, u) || !out) return set_err(ctx, FR_ERR_ARG, "bad argument");
+    cudaError_t e = fr::launch_sum_weighted(ctx->dev, u, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+fr_status fr_check_finite(fr_ctx* ctx, void* const* u, void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, u)) return set_err(ctx, FR_ERR_ARG, "NULL state pointer");
+    cudaError_t e = fr::launch_check_finite(ctx->dev, u, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+fr_status fr_profile_enable(fr_ctx* ctx, int enable) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    ctx->dev.prof = enable != 0;
+    return FR_OK;
+}
+
+fr_status fr_profile_read(fr_ctx* ctx, int32_t* nk, char* names, int64_t* launches, double* ms) {
+    if (!nk) return FR_ERR_ARG;
+    *nk = fr::K_NKERNELS;
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    int64_t l[fr::K_NKERNELS];
+    double t[fr::K_NKERNELS];
+    cudaError_t e = fr::prof_drain(ctx->dev, l, t);
+    for (int k = 0; k < fr::K_NKERNELS; ++k) {
+        if (names) {
+            std::memset(names + 32 * k, 0, 32);
+            std::strncpy(names + 32 * k, fr::kKernelNames[k], 31);
+        }
+        if (launches) launches[k] = l[k];
+        if (ms) ms[k] = t[k];
+    }
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+fr_status fr_sync_status(fr_ctx* ctx) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    int f[2] = {0, 0};
+    e = cudaMemcpy(f, ctx->dev.flags, sizeof(f), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    cudaMemset(ctx->dev.flags, 0, sizeof(f));
+    if (f[1]) return set_err(ctx, FR_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (f[0]) return set_err(ctx, FR_ERR_NONFINITE, "non-finite value in a state");
+    return FR_OK;
+}
+
+}  // extern "C"

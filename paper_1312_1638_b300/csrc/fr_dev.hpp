@@ -1,0 +1,96 @@
+// Device-side state of an FR context and the kernel launchers (CUDA).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace fr {
+
+// Physical / numerical parameters as passed to kernels (Sec. 4, App. C).
+struct DevParams {
+    double gamma, mu, prandtl, beta, tau;
+    double bc_rho, bc_v[3], bc_p, outflow_p, wall_cpTw, wall_v[3];
+};
+
+// One element block on the device.  Buffers hold T = double (FP64) or float.
+struct DevBlock {
+    int etype = 0, nupts = 0, nfpts = 0, nvars = 0;
+    int64_t nelem = 0, ld = 0;
+    void* smat = nullptr;      // adj(J): [ndims*ndims][nupts][ld]
+    void* rcpdjac = nullptr;   // 1/det J: [nupts][ld]
+    double* wdet = nullptr;    // FP64 quadrature weight * det J: [nupts][ld]
+    void* Uf = nullptr;        // [nfpts][nvars][ld]   U^(f), then D~ in place
+    void* Q = nullptr;         // [ndims*nupts][nvars][ld]  Q~ -> Q -> F~ in place
+    void* Qf = nullptr;        // [ndims*nfpts][nvars][ld]  C^(f), then Q^(f)  (NS)
+    void* opM0 = nullptr;      // M0: nfpts x nupts
+    void* opQ = nullptr;       // [M6 | M4 - M6 M0]: ndims*nupts x (nfpts + nupts)
+    void* opR = nullptr;       // [M3 | M1 - M3 M2]: nupts x (nfpts + ndims*nupts)
+    void* stage = nullptr;     // device staging for fr_rhs_host: [nupts][nvars][ld]
+    void* rk_acc = nullptr;    // RK4 registers
+    void* rk_tmp = nullptr;
+};
+
+struct DevPairGroup {          // interior pairs between block bL and block bR
+    int bL = 0, bR = 0;
+    int64_t n = 0;
+    uint32_t* offL = nullptr;  // fpt*nvars*ld + elem in the L block's flux-point arrays
+    uint32_t* offR = nullptr;
+    void* nrm = nullptr;       // [ndims][n] unit normal of L (T)
+    void* magL = nullptr;      // [n] J^(f) n^(f) of L (T)
+    void* magR = nullptr;
+};
+
+struct DevBndGroup {           // boundary flux points of one block and one type
+    int b = 0, bctype = 0;
+    int64_t n = 0;
+    uint32_t* off = nullptr;
+    void* nrm = nullptr;
+    void* mag = nullptr;
+};
+
+// Kernel-level timing: CUDA events recorded on the launch stream around each
+// kernel when profiling is enabled.
+enum KernelId {
+    K_DISU = 0, K_COMM_SOL, K_COMM_SOL_BC, K_TGRADU, K_GRADCORU, K_GRADFPTS, K_TDISF, K_COMM_FLUX,
+    K_COMM_FLUX_BC, K_TDIVF, K_RK_STAGE, K_NKERNELS
+};
+extern const char* const kKernelNames[K_NKERNELS];
+
+struct ProfRec {
+    int id;
+    cudaEvent_t a, b;
+};
+
+struct DevCtx {
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    int device = -1;
+    int ndims = 0, nvars = 0, system = 0, precision = 0, order = 0;
+    DevParams prm{};
+    std::vector<DevBlock> blocks;
+    std::vector<DevPairGroup> pgroups;
+    std::vector<DevBndGroup> bgroups;
+    int* flags = nullptr;          // [0] non-finite seen, [1] timeout
+    double* partial = nullptr;     // reduction scratch
+    int64_t npartial = 0;
+};
+
+// profiling helpers (no-ops when c.prof is false)
+void prof_begin(DevCtx& c, int id, cudaStream_t st);
+void prof_end(DevCtx& c, cudaStream_t st);
+// drain: per kernel id, launches and total ms since the last drain (synchronises)
+cudaError_t prof_drain(DevCtx& c, int64_t* launches, double* ms);
+void prof_free(DevCtx& c);
+
+// RHS r = R(u) for every block (precision and dimension dispatched inside).
+cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t st);
+// classical RK4, nsteps steps of dt, in place on u
+cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st);
+// FP64 weighted totals per variable
+cudaError_t launch_sum_weighted(DevCtx& c, void* const* u, double* host_out, cudaStream_t st);
+cudaError_t launch_check_finite(DevCtx& c, void* const* u, cudaStream_t st);
+
+}  // namespace fr

@@ -1,0 +1,717 @@
+// CUDA kernels of the FR right-hand side (Sec. 2, Sec. 3.6 kernel flow, App. A).
+//
+// Kernel categories follow the paper's split (Sec. 6): dense operator
+// products ("GEMM"), point-wise kernels with direct access ("PD": gradient
+// transform, transformed flux) and point-wise kernels over flux-point pairs
+// with indirect access ("PI": common solution, common normal flux).
+//
+// State layout is SoA (Sec. 3.3): [points][nvars][ld], so every operator
+// product is C[M x N] = A[M x K] B[K x N] with N = nvars * ld columns.
+#include <cmath>
+#include <cstdio>
+
+#include "fr_dev.hpp"
+
+namespace fr {
+
+// ============================================================ operator GEMM
+// C = A [B1; B2] with A = [A1 | A2] stored as one M x (K1 + K2) row-major
+// matrix; B rows k < K1 come from B1, the rest from B2 (both N columns,
+// row stride N).  epi = 1 applies -1/J (Eq. negdivconf) per (row, element).
+template <typename T> struct GemmCfg;
+template <> struct GemmCfg<float>  { static constexpr int TN = 128, RN = 4, MB = 64, RM = 8, KC = 16; };
+template <> struct GemmCfg<double> { static constexpr int TN = 64,  RN = 2, MB = 64, RM = 8, KC = 16; };
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+gemm_kernel(int M, int K, int K1, const T* __restrict__ A, const T* __restrict__ B1,
+            const T* __restrict__ B2, int64_t N, T* __restrict__ C, int epi,
+            const T* __restrict__ rcp, int64_t ld) {
+    using G = GemmCfg<T>;
+    constexpr int TN = G::TN, RN = G::RN, MB = G::MB, RM = G::RM, KC = G::KC;
+    __shared__ __align__(16) T As[KC][MB];
+    __shared__ __align__(16) T Bs[KC][TN];
+    const int tid = threadIdx.x;
+    const int tx = tid % 32, ty = tid / 32;          // 32 column groups x 8 row groups
+    const int64_t col0 = (int64_t)blockIdx.x * TN;
+    for (int m0 = 0; m0 < M; m0 += MB) {
+        T acc[RM][RN];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < RN; ++j) acc[i][j] = T(0);
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            __syncthreads();
+            for (int e = tid; e < MB * KC; e += 256) {
+                int r = e / KC, kk = e % KC;
+                int gr = m0 + r, gk = k0 + kk;
+                As[kk][r] = (gr < M && gk < K) ? A[(int64_t)gr * K + gk] : T(0);
+            }
+            for (int e = tid; e < KC * TN; e += 256) {
+                int kk = e / TN, c = e % TN;
+                int gk = k0 + kk;
+                int64_t gc = col0 + c;
+                T v = T(0);
+                if (gk < K && gc < N) v = gk < K1 ? B1[(int64_t)gk * N + gc] : B2[(int64_t)(gk - K1) * N + gc];
+                Bs[kk][c] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                T a[RM], b[RN];
+#pragma unroll
+                for (int i = 0; i < RM; ++i) a[i] = As[kk][ty * RM + i];
+#pragma unroll
+                for (int j = 0; j < RN; ++j) b[j] = Bs[kk][tx * RN + j];
+#pragma unroll
+                for (int i = 0; i < RM; ++i)
+#pragma unroll
+                    for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RM; ++i) {
+            int row = m0 + ty * RM + i;
+            if (row >= M) continue;
+#pragma unroll
+            for (int j = 0; j < RN; ++j) {
+                int64_t col = col0 + tx * RN + j;
+                if (col >= N) continue;
+                T v = acc[i][j];
+                if (epi == 1) v = -v * rcp[(int64_t)row * ld + (col % ld)];
+                C[(int64_t)row * N + col] = v;
+            }
+        }
+    }
+}
+
+template <typename T>
+static void gemm(int M, int K, int K1, const void* A, const void* B1, const void* B2, int64_t N,
+                 void* C, int epi, const void* rcp, int64_t ld, cudaStream_t st) {
+    constexpr int TN = GemmCfg<T>::TN;
+    dim3 grid((unsigned)((N + TN - 1) / TN));
+    gemm_kernel<T><<<grid, 256, 0, st>>>(M, K, K1, (const T*)A, (const T*)B1, (const T*)B2, N, (T*)C, epi,
+                                         (const T*)rcp, ld);
+}
+
+// ============================================================ gas dynamics
+template <typename T, int D>
+struct Gas {
+    static constexpr int NV = D + 2;
+
+    __device__ static __forceinline__ T pressure(const T* u, T gm1) {
+        T ke = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) ke += u[1 + i] * u[1 + i];
+        return gm1 * (u[D + 1] - T(0.5) * ke / u[0]);
+    }
+
+    // normal inviscid flux n.f(u) (Eq. eulerflux); returns p and v.n
+    __device__ static __forceinline__ void normal_flux(const T* u, const T* n, T gm1, T* fn, T& p, T& vn) {
+        T rinv = T(1) / u[0];
+        p = pressure(u, gm1);
+        vn = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) vn += n[i] * u[1 + i] * rinv;
+        fn[0] = u[0] * vn;
+#pragma unroll
+        for (int i = 0; i < D; ++i) fn[1 + i] = u[1 + i] * vn + p * n[i];
+        fn[D + 1] = (u[D + 1] + p) * vn;
+    }
+
+    // Rusanov common inviscid flux (App. B)
+    __device__ static __forceinline__ void rusanov(const T* uL, const T* uR, const T* n, T gamma, T* F) {
+        T fL[NV], fR[NV], pL, pR, vnL, vnR;
+        normal_flux(uL, n, gamma - T(1), fL, pL, vnL);
+        normal_flux(uR, n, gamma - T(1), fR, pR, vnR);
+        T s = sqrt(gamma * (pL + pR) / (uL[0] + uR[0])) + T(0.5) * fabs(vnL + vnR);
+#pragma unroll
+        for (int a = 0; a < NV; ++a) F[a] = T(0.5) * (fL[a] + fR[a]) + T(0.5) * s * (uL[a] - uR[a]);
+    }
+
+    // full inviscid flux tensor f[i][a]
+    __device__ static __forceinline__ void inv_flux(const T* u, T gm1, T f[D][NV]) {
+        T rinv = T(1) / u[0];
+        T p = pressure(u, gm1);
+        T v[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) v[i] = u[1 + i] * rinv;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            f[i][0] = u[1 + i];
+#pragma unroll
+            for (int j = 0; j < D; ++j) f[i][1 + j] = u[1 + j] * v[i] + (i == j ? p : T(0));
+            f[i][D + 1] = v[i] * (u[D + 1] + p);
+        }
+    }
+
+    // viscous flux f_vis (Eq. visflux), constant mu; kappa = mu gamma / (Pr (gamma-1))
+    // multiplies d(p/rho) (T = p / (rho C_v (gamma-1)), Delta = mu C_p / Pr)
+    __device__ static __forceinline__ void vis_flux(const T* u, const T q[D][NV], T gm1, T mu, T kappa,
+                                                    T fv[D][NV]) {
+        T rinv = T(1) / u[0];
+        T v[D], v2 = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { v[i] = u[1 + i] * rinv; v2 += v[i] * v[i]; }
+        T p = gm1 * (u[D + 1] - T(0.5) * u[0] * v2);
+        T dv[D][D], dpr[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T drho = q[j][0];
+#pragma unroll
+            for (int i = 0; i < D; ++i) dv[i][j] = (q[j][1 + i] - v[i] * drho) * rinv;
+            T vdm = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) vdm += v[i] * q[j][1 + i];
+            T dp = gm1 * (q[j][D + 1] - vdm + T(0.5) * v2 * drho);
+            dpr[j] = (dp - p * rinv * drho) * rinv;
+        }
+        T div = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) div += dv[i][i];
+        T tau[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                tau[i][j] = mu * (dv[j][i] + dv[i][j]) - (i == j ? T(2) / T(3) * mu * div : T(0));
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            fv[i][0] = T(0);
+#pragma unroll
+            for (int j = 0; j < D; ++j) fv[i][1 + j] = tau[i][j];
+            T e = kappa * dpr[i];
+#pragma unroll
+            for (int j = 0; j < D; ++j) e += v[j] * tau[j][i];
+            fv[i][D + 1] = e;
+        }
+    }
+
+    // ghost states (App. C): inviscid ghost gi, LDG ghost gl; returns whether
+    // the ghost gradient is q_L (wall) or zero
+    __device__ static __forceinline__ bool ghosts(int bctype, const T* uL, const DevParams& P, T* gi, T* gl) {
+        T gamma = T(P.gamma), gm1 = gamma - T(1);
+        if (bctype == 0) {
+            T rho = T(P.bc_rho), ke = T(0);
+            gi[0] = rho;
+#pragma unroll
+            for (int i = 0; i < D; ++i) { gi[1 + i] = rho * T(P.bc_v[i]); ke += T(P.bc_v[i]) * T(P.bc_v[i]); }
+            gi[D + 1] = T(P.bc_p) / gm1 + T(0.5) * rho * ke;
+#pragma unroll
+            for (int a = 0; a < NV; ++a) gl[a] = gi[a];
+            return false;
+        }
+        if (bctype == 1) {
+            T rho = uL[0], ke = T(0);
+            gi[0] = rho;
+#pragma unroll
+            for (int i = 0; i < D; ++i) { gi[1 + i] = uL[1 + i]; ke += uL[1 + i] * uL[1 + i]; }
+            gi[D + 1] = T(P.outflow_p) / gm1 + T(0.5) * ke / rho;
+#pragma unroll
+            for (int a = 0; a < NV; ++a) gl[a] = gi[a];
+            return false;
+        }
+        T rho = uL[0], rinv = T(1) / rho, cpt = T(P.wall_cpTw) / gamma, k1 = T(0), k2 = T(0);
+        gi[0] = rho; gl[0] = rho;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            T vw = T(P.wall_v[i]);
+            T vm = T(2) * vw - uL[1 + i] * rinv;
+            gi[1 + i] = rho * vm; k1 += vm * vm;
+            gl[1 + i] = rho * vw; k2 += vw * vw;
+        }
+        gi[D + 1] = rho * (cpt + T(0.5) * k1);
+        gl[D + 1] = rho * (cpt + T(0.5) * k2);
+        return true;
+    }
+};
+
+// ============================================================ point-wise (PD)
+// Q = J^{-T} Q~ = adj(J)^T Q~ / det J, in place (Eq. gradufpts, first line)
+template <typename T, int D>
+__global__ void grad_transform_kernel(int nupts, int64_t nelem, int64_t ld, const T* __restrict__ smat,
+                                      const T* __restrict__ rcp, T* __restrict__ Q) {
+    constexpr int NV = D + 2;
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    T adj[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) adj[i][j] = smat[((int64_t)(i * D + j) * nupts + s) * ld + n];
+    T r = rcp[(int64_t)s * ld + n];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+        T qt[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) qt[i] = Q[((int64_t)(i * nupts + s) * NV + a) * ld + n];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc += adj[i][j] * qt[i];
+            Q[((int64_t)(j * nupts + s) * NV + a) * ld + n] = acc * r;
+        }
+    }
+}
+
+// F~ = J J^{-1} f(u, q) = adj(J) f at solution points (Sec. 2); F may alias Q
+template <typename T, int D, bool NS>
+__global__ void tflux_kernel(int nupts, int64_t nelem, int64_t ld, const T* __restrict__ U,
+                             const T* Q, const T* __restrict__ smat, T* F, DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    T u[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) u[a] = U[((int64_t)s * NV + a) * ld + n];
+    T gamma = T(P.gamma), gm1 = gamma - T(1);
+    T f[D][NV];
+    Gas<T, D>::inv_flux(u, gm1, f);
+    if (NS) {
+        T q[D][NV], fv[D][NV];
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int a = 0; a < NV; ++a) q[j][a] = Q[((int64_t)(j * nupts + s) * NV + a) * ld + n];
+        T mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
+        Gas<T, D>::vis_flux(u, q, gm1, mu, kappa, fv);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int a = 0; a < NV; ++a) f[i][a] -= fv[i][a];
+    }
+    T adj[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) adj[i][j] = smat[((int64_t)(i * D + j) * nupts + s) * ld + n];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < D; ++j) acc += adj[i][j] * f[j][a];
+            F[((int64_t)(i * nupts + s) * NV + a) * ld + n] = acc;
+        }
+}
+
+// ============================================================ interfaces (PI)
+// LDG common solution (Eq. commsoln, Sec. 4.3): each pair visited once,
+// the same value written to both sides.
+template <typename T, int D>
+__global__ void comm_sol_kernel(int64_t npairs, const uint32_t* __restrict__ offL, const uint32_t* __restrict__ offR,
+                                const T* __restrict__ UfL, const T* __restrict__ UfR, int64_t ldL, int64_t ldR,
+                                T* __restrict__ CL, T* __restrict__ CR, T beta) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    int64_t oL = offL[k], oR = offR[k];
+    T wl = T(0.5) - beta, wr = T(0.5) + beta;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+        T c = wl * UfL[oL + a * ldL] + wr * UfR[oR + a * ldR];
+        CL[oL + a * ldL] = c;
+        CR[oR + a * ldR] = c;
+    }
+}
+
+template <typename T, int D>
+__global__ void comm_sol_bc_kernel(int64_t nb, int bctype, const uint32_t* __restrict__ off, const T* __restrict__ Uf,
+                                   int64_t ld, T* __restrict__ C, DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    int64_t o = off[k];
+    T uL[NV], gi[NV], gl[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) uL[a] = Uf[o + a * ld];
+    Gas<T, D>::ghosts(bctype, uL, P, gi, gl);
+    T beta = T(P.beta);
+#pragma unroll
+    for (int a = 0; a < NV; ++a) C[o + a * ld] = (T(0.5) - beta) * uL[a] + (T(0.5) + beta) * gl[a];
+}
+
+// Common normal flux (Eq. commpflux): Rusanov (App. B) minus the LDG viscous
+// flux with a dissipative tau penalty (Sec. 4.3), scaled by J^(f) n^(f) and
+// written with opposite signs to both sides, in place over U^(f).
+template <typename T, int D, bool NS>
+__global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ offL, const uint32_t* __restrict__ offR,
+                                 T* UfL, T* UfR, const T* __restrict__ QfL, const T* __restrict__ QfR,
+                                 int64_t ldL, int64_t ldR, int64_t qsL, int64_t qsR, const T* __restrict__ nrm,
+                                 const T* __restrict__ magL, const T* __restrict__ magR, DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    int64_t oL = offL[k], oR = offR[k];
+    T uL[NV], uR[NV], n[D], F[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) { uL[a] = UfL[oL + a * ldL]; uR[a] = UfR[oR + a * ldR]; }
+#pragma unroll
+    for (int i = 0; i < D; ++i) n[i] = nrm[i * npairs + k];
+    T gamma = T(P.gamma);
+    Gas<T, D>::rusanov(uL, uR, n, gamma, F);
+    if (NS) {
+        T qL[D][NV], qR[D][NV], fvL[D][NV], fvR[D][NV];
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int a = 0; a < NV; ++a) {
+                qL[j][a] = QfL[j * qsL + oL + a * ldL];
+                qR[j][a] = QfR[j * qsR + oR + a * ldR];
+            }
+        T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
+        Gas<T, D>::vis_flux(uL, qL, gm1, mu, kappa, fvL);
+        Gas<T, D>::vis_flux(uR, qR, gm1, mu, kappa, fvR);
+        T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            T fv = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) fv += n[i] * (wl * fvL[i][a] + wr * fvR[i][a]);
+            F[a] = F[a] - fv + tau * (uL[a] - uR[a]);
+        }
+    }
+    T mL = magL[k], mR = magR[k];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+        UfL[oL + a * ldL] = mL * F[a];
+        UfR[oR + a * ldR] = -mR * F[a];
+    }
+}
+
+template <typename T, int D, bool NS>
+__global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __restrict__ off, T* Uf,
+                                    const T* __restrict__ Qf, int64_t ld, int64_t qs, const T* __restrict__ nrm,
+                                    const T* __restrict__ mag, DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    int64_t o = off[k];
+    T uL[NV], gi[NV], gl[NV], n[D], F[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) uL[a] = Uf[o + a * ld];
+#pragma unroll
+    for (int i = 0; i < D; ++i) n[i] = nrm[i * nb + k];
+    bool grad_is_qL = Gas<T, D>::ghosts(bctype, uL, P, gi, gl);
+    T gamma = T(P.gamma);
+    Gas<T, D>::rusanov(uL, gi, n, gamma, F);
+    if (NS) {
+        T qL[D][NV], fvL[D][NV], fvR[D][NV], qg[D][NV];
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int a = 0; a < NV; ++a) {
+                qL[j][a] = Qf[j * qs + o + a * ld];
+                qg[j][a] = grad_is_qL ? qL[j][a] : T(0);
+            }
+        T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
+        Gas<T, D>::vis_flux(uL, qL, gm1, mu, kappa, fvL);
+        Gas<T, D>::vis_flux(gl, qg, gm1, mu, kappa, fvR);
+        T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            T fv = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) fv += n[i] * (wl * fvL[i][a] + wr * fvR[i][a]);
+            F[a] = F[a] - fv + tau * (uL[a] - gl[a]);
+        }
+    }
+    T m = mag[k];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) Uf[o + a * ld] = m * F[a];
+}
+
+// ============================================================ RK4 combine
+// acc += a_acc * k; tmp = u + a_tmp * k, where k lives in tmp (in place)
+template <typename T>
+__global__ void rk_stage_kernel(int64_t n, T* __restrict__ acc, T* __restrict__ tmp, const T* __restrict__ u,
+                                T a_acc, T a_tmp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T k = tmp[i];
+    acc[i] += a_acc * k;
+    tmp[i] = u[i] + a_tmp * k;
+}
+
+template <typename T>
+__global__ void rk_final_kernel(int64_t n, const T* __restrict__ acc, const T* __restrict__ k, T* __restrict__ u,
+                                T a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u[i] = acc[i] + a * k[i];
+}
+
+// ============================================================ diagnostics
+template <typename T>
+__global__ void sum_weighted_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, const T* __restrict__ u,
+                                    const double* __restrict__ wdet, double* __restrict__ partial) {
+    // one block per (point, variable); block-reduce over elements in FP64
+    int s = blockIdx.x, a = blockIdx.y;
+    double acc = 0.0;
+    for (int64_t n = threadIdx.x; n < nelem; n += blockDim.x)
+        acc += wdet[(int64_t)s * ld + n] * (double)u[((int64_t)s * nvars + a) * ld + n];
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)a * nupts + s] = red[0];
+}
+
+template <typename T>
+__global__ void check_finite_kernel(int npts, int nvars, int64_t nelem, int64_t ld, const T* __restrict__ u,
+                                    int* flags) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nelem) return;
+    int bad = 0;
+    for (int s = 0; s < npts; ++s)
+        for (int a = 0; a < nvars; ++a) {
+            T v = u[((int64_t)s * nvars + a) * ld + n];
+            if (!isfinite(v)) bad = 1;
+        }
+    if (bad) atomicOr(&flags[0], 1);
+}
+
+// ============================================================ profiling
+const char* const kKernelNames[K_NKERNELS] = {"disu_gemm", "comm_sol", "comm_sol_bc", "tgradu_gemm",
+                                              "gradcoru", "gradfpts_gemm", "tdisf", "comm_flux",
+                                              "comm_flux_bc", "tdivf_gemm", "rk_stage"};
+
+static cudaEvent_t prof_event(DevCtx& c) {
+    if (!c.pool.empty()) {
+        cudaEvent_t e = c.pool.back();
+        c.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(DevCtx& c, int id, cudaStream_t st) {
+    if (!c.prof) return;
+    ProfRec r{id, prof_event(c), prof_event(c)};
+    cudaEventRecord(r.a, st);
+    c.recs.push_back(r);
+}
+
+void prof_end(DevCtx& c, cudaStream_t st) {
+    if (!c.prof || c.recs.empty()) return;
+    cudaEventRecord(c.recs.back().b, st);
+}
+
+cudaError_t prof_drain(DevCtx& c, int64_t* launches, double* ms) {
+    for (int k = 0; k < K_NKERNELS; ++k) { launches[k] = 0; ms[k] = 0.0; }
+    cudaError_t err = cudaSuccess;
+    for (auto& r : c.recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) err = e;
+        launches[r.id] += 1;
+        ms[r.id] += t;
+        c.pool.push_back(r.a);
+        c.pool.push_back(r.b);
+    }
+    c.recs.clear();
+    return err;
+}
+
+void prof_free(DevCtx& c) {
+    for (auto& r : c.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c.pool) cudaEventDestroy(e);
+    c.recs.clear();
+    c.pool.clear();
+}
+
+// ============================================================ drivers
+static inline dim3 pw_grid(int64_t nelem, int npts) {
+    return dim3((unsigned)((nelem + 127) / 128), (unsigned)npts);
+}
+static inline unsigned lin_grid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T, int D>
+static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
+    constexpr int NV = D + 2;
+    const bool ns = c.system == 1;
+    // 1. U^(f) = M0 U  (K1, disu)
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        prof_begin(c, K_DISU, st);
+        gemm<T>(B.nfpts, B.nupts, B.nupts, B.opM0, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0, nullptr, B.ld, st);
+        prof_end(c, st);
+    }
+    if (ns) {
+        // 2. common solution into the Q^(f) storage (C^(f) aliases Q^(f), Sec. 3.6)
+        for (auto& g : c.pgroups) {
+            DevBlock &L = c.blocks[g.bL], &R = c.blocks[g.bR];
+            if (!g.n) continue;
+            prof_begin(c, K_COMM_SOL, st);
+            comm_sol_kernel<T, D><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                g.n, g.offL, g.offR, (const T*)L.Uf, (const T*)R.Uf, L.ld, R.ld, (T*)L.Qf, (T*)R.Qf, T(c.prm.beta));
+            prof_end(c, st);
+        }
+        for (auto& g : c.bgroups) {
+            DevBlock& B = c.blocks[g.b];
+            if (!g.n) continue;
+            prof_begin(c, K_COMM_SOL_BC, st);
+            comm_sol_bc_kernel<T, D><<<lin_grid(g.n, 128), 128, 0, st>>>(g.n, g.bctype, g.off, (const T*)B.Uf, B.ld,
+                                                                          (T*)B.Qf, c.prm);
+            prof_end(c, st);
+        }
+        for (size_t b = 0; b < c.blocks.size(); ++b) {
+            DevBlock& B = c.blocks[b];
+            int64_t N = (int64_t)NV * B.ld;
+            // 3. Q~ = M6 C + (M4 - M6 M0) U  (tgradu, eq. tquptsm)
+            prof_begin(c, K_TGRADU, st);
+            gemm<T>(D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.opQ, B.Qf, u[b], N, B.Q, 0, nullptr, B.ld, st);
+            prof_end(c, st);
+            // 4. Q = J^{-T} Q~
+            prof_begin(c, K_GRADCORU, st);
+            grad_transform_kernel<T, D><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                B.nupts, B.nelem, B.ld, (const T*)B.smat, (const T*)B.rcpdjac, (T*)B.Q);
+            prof_end(c, st);
+            // 5. Q^(f) = M5 Q (block diagonal: M0 per component)
+            for (int i = 0; i < D; ++i) {
+                prof_begin(c, K_GRADFPTS, st);
+                gemm<T>(B.nfpts, B.nupts, B.nupts, B.opM0, (const T*)B.Q + (int64_t)i * B.nupts * N, nullptr, N,
+                        (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st);
+                prof_end(c, st);
+            }
+        }
+    }
+    // 6. F~ = J J^{-1} f(U, Q)  (tdisf), in place over Q
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        prof_begin(c, K_TDISF, st);
+        if (ns)
+            tflux_kernel<T, D, true><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                B.nupts, B.nelem, B.ld, (const T*)u[b], (const T*)B.Q, (const T*)B.smat, (T*)B.Q, c.prm);
+        else
+            tflux_kernel<T, D, false><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                B.nupts, B.nelem, B.ld, (const T*)u[b], nullptr, (const T*)B.smat, (T*)B.Q, c.prm);
+        prof_end(c, st);
+    }
+    // 7. common normal flux D~ in place over U^(f) (comm_flux int / bc)
+    for (auto& g : c.pgroups) {
+        if (!g.n) continue;
+        DevBlock &L = c.blocks[g.bL], &R = c.blocks[g.bR];
+        int64_t qsL = (int64_t)L.nfpts * NV * L.ld, qsR = (int64_t)R.nfpts * NV * R.ld;
+        prof_begin(c, K_COMM_FLUX, st);
+        if (ns)
+            comm_flux_kernel<T, D, true><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                g.n, g.offL, g.offR, (T*)L.Uf, (T*)R.Uf, (const T*)L.Qf, (const T*)R.Qf, L.ld, R.ld, qsL, qsR,
+                (const T*)g.nrm, (const T*)g.magL, (const T*)g.magR, c.prm);
+        else
+            comm_flux_kernel<T, D, false><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                g.n, g.offL, g.offR, (T*)L.Uf, (T*)R.Uf, nullptr, nullptr, L.ld, R.ld, qsL, qsR,
+                (const T*)g.nrm, (const T*)g.magL, (const T*)g.magR, c.prm);
+        prof_end(c, st);
+    }
+    for (auto& g : c.bgroups) {
+        if (!g.n) continue;
+        DevBlock& B = c.blocks[g.b];
+        int64_t qs = (int64_t)B.nfpts * NV * B.ld;
+        prof_begin(c, K_COMM_FLUX_BC, st);
+        if (ns)
+            comm_flux_bc_kernel<T, D, true><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                g.n, g.bctype, g.off, (T*)B.Uf, (const T*)B.Qf, B.ld, qs, (const T*)g.nrm, (const T*)g.mag, c.prm);
+        else
+            comm_flux_bc_kernel<T, D, false><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                g.n, g.bctype, g.off, (T*)B.Uf, nullptr, B.ld, qs, (const T*)g.nrm, (const T*)g.mag, c.prm);
+        prof_end(c, st);
+    }
+    // 8. R = -J^{-1} [M3 D~ + (M1 - M3 M2) F~]  (tdivtpcorf + negdivconf)
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        prof_begin(c, K_TDIVF, st);
+        gemm<T>(B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.opR, B.Uf, B.Q, (int64_t)NV * B.ld, r[b], 1, B.rcpdjac,
+                B.ld, st);
+        prof_end(c, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
+    if (c.precision == 0) return c.ndims == 2 ? rhs_impl<double, 2>(c, u, r, st) : rhs_impl<double, 3>(c, u, r, st);
+    return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st) : rhs_impl<float, 3>(c, u, r, st);
+}
+
+template <typename T>
+static cudaError_t rk4_impl(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {
+    std::vector<void*> tmp(c.blocks.size());
+    for (size_t b = 0; b < c.blocks.size(); ++b) tmp[b] = c.blocks[b].rk_tmp;
+    for (int step = 0; step < nsteps; ++step) {
+        for (size_t b = 0; b < c.blocks.size(); ++b) {
+            DevBlock& B = c.blocks[b];
+            size_t bytes = (size_t)B.nupts * B.nvars * B.ld * sizeof(T);
+            cudaMemcpyAsync(B.rk_acc, u[b], bytes, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(B.rk_tmp, u[b], bytes, cudaMemcpyDeviceToDevice, st);
+        }
+        const double a_acc[4] = {dt / 6, dt / 3, dt / 3, dt / 6};
+        const double a_tmp[3] = {dt / 2, dt / 2, dt};
+        for (int s = 0; s < 4; ++s) {
+            cudaError_t e = launch_rhs(c, tmp.data(), tmp.data(), st);
+            if (e != cudaSuccess) return e;
+            for (size_t b = 0; b < c.blocks.size(); ++b) {
+                DevBlock& B = c.blocks[b];
+                int64_t n = (int64_t)B.nupts * B.nvars * B.ld;
+                prof_begin(c, K_RK_STAGE, st);
+                if (s < 3)
+                    rk_stage_kernel<T><<<lin_grid(n, 256), 256, 0, st>>>(n, (T*)B.rk_acc, (T*)B.rk_tmp,
+                                                                         (const T*)u[b], T(a_acc[s]), T(a_tmp[s]));
+                else
+                    rk_final_kernel<T><<<lin_grid(n, 256), 256, 0, st>>>(n, (const T*)B.rk_acc, (const T*)B.rk_tmp,
+                                                                         (T*)u[b], T(a_acc[3]));
+                prof_end(c, st);
+            }
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {
+    return c.precision == 0 ? rk4_impl<double>(c, u, dt, nsteps, st) : rk4_impl<float>(c, u, dt, nsteps, st);
+}
+
+cudaError_t launch_sum_weighted(DevCtx& c, void* const* u, double* out, cudaStream_t st) {
+    for (int a = 0; a < c.nvars; ++a) out[a] = 0.0;
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        dim3 grid(B.nupts, B.nvars);
+        if (c.precision == 0)
+            sum_weighted_kernel<double><<<grid, 256, 0, st>>>(B.nupts, B.nvars, B.nelem, B.ld, (const double*)u[b],
+                                                              B.wdet, c.partial);
+        else
+            sum_weighted_kernel<float><<<grid, 256, 0, st>>>(B.nupts, B.nvars, B.nelem, B.ld, (const float*)u[b],
+                                                             B.wdet, c.partial);
+        std::vector<double> h((size_t)B.nupts * B.nvars);
+        cudaMemcpyAsync(h.data(), c.partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        for (int a = 0; a < B.nvars; ++a)
+            for (int s = 0; s < B.nupts; ++s) out[a] += h[(size_t)a * B.nupts + s];
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(DevCtx& c, void* const* u, cudaStream_t st) {
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        if (c.precision == 0)
+            check_finite_kernel<double><<<lin_grid(B.nelem, 256), 256, 0, st>>>(B.nupts, B.nvars, B.nelem, B.ld,
+                                                                                (const double*)u[b], c.flags);
+        else
+            check_finite_kernel<float><<<lin_grid(B.nelem, 256), 256, 0, st>>>(B.nupts, B.nvars, B.nelem, B.ld,
+                                                                               (const float*)u[b], c.flags);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fr

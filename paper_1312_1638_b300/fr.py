@@ -1,0 +1,279 @@
+"""ctypes binding of ``libfr.so`` (include/fr.h): argument marshalling only.
+
+Every step of the right-hand side runs in the library's CUDA kernels; this
+module converts ``fr_inputs.Mesh`` objects and torch tensors into the C
+structures and raw pointers the ABI takes.  There is no CPU fallback: if the
+shared library is missing, importing this module raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libfr.so")
+
+OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_OOM = range(8)
+EULER, NAVIER_STOKES = 0, 1
+FP64, FP32, BF16X3 = 0, 1, 2
+ETYPES = {"quad": 0, "tri": 1, "hex": 2}
+STATUS_NAMES = ["FR_OK", "FR_ERR_ARG", "FR_ERR_MESH", "FR_ERR_CUDA", "FR_ERR_NONFINITE",
+                "FR_ERR_TIMEOUT", "FR_ERR_UNSUPPORTED", "FR_ERR_OOM"]
+
+# names exported by libfr.so (every function declared in include/fr.h)
+EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pairs", "fr_rhs",
+           "fr_rhs_host", "fr_rk4", "fr_sum_weighted", "fr_sync_status", "fr_check_finite",
+           "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read"]
+
+
+class FRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("ndims", C.c_int32), ("order", C.c_int32), ("system", C.c_int32), ("precision", C.c_int32),
+                ("gamma", C.c_double), ("mu", C.c_double), ("prandtl", C.c_double),
+                ("ldg_beta", C.c_double), ("ldg_tau", C.c_double),
+                ("bc_rho", C.c_double), ("bc_v", C.c_double * 3), ("bc_p", C.c_double),
+                ("outflow_p", C.c_double), ("wall_cpTw", C.c_double), ("wall_v", C.c_double * 3)]
+
+
+class EBlock(C.Structure):
+    _fields_ = [("etype", C.c_int32), ("nnodes", C.c_int32), ("nelem", C.c_int64),
+                ("nodes", C.POINTER(C.c_double))]
+
+
+class MeshC(C.Structure):
+    _fields_ = [("ndims", C.c_int32), ("nblocks", C.c_int32), ("blocks", C.POINTER(EBlock)),
+                ("nbfaces", C.c_int64), ("bfaces", C.POINTER(C.c_int64)),
+                ("nperiodic", C.c_int32), ("periodic", C.POINTER(C.c_double))]
+
+
+_lib = None
+
+
+def load():
+    """Load libfr.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise ImportError(f"{LIBPATH} is missing: build it with paper_1312_1638_b300.build.build()")
+    lib = C.CDLL(LIBPATH)
+    vp, vpp = C.c_void_p, C.POINTER(C.c_void_p)
+    lib.fr_setup.argtypes = [C.POINTER(MeshC), C.POINTER(Params), C.c_int, C.POINTER(vp)]
+    lib.fr_layout.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                              C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.fr_solution_points.argtypes = [vp, C.c_int, C.POINTER(C.c_double)]
+    lib.fr_operator.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                C.POINTER(C.c_int32)]
+    lib.fr_pairs.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.fr_rhs.argtypes = [vp, vpp, vpp, vp]
+    lib.fr_rhs_host.argtypes = [vp, vpp, vpp, vp]
+    lib.fr_rk4.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
+    lib.fr_sum_weighted.argtypes = [vp, vpp, C.POINTER(C.c_double), vp]
+    lib.fr_sync_status.argtypes = [vp]
+    lib.fr_check_finite.argtypes = [vp, vpp, vp]
+    lib.fr_profile_enable.argtypes = [vp, C.c_int]
+    lib.fr_profile_read.argtypes = [vp, C.POINTER(C.c_int32), C.c_char_p, C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_double)]
+    lib.fr_last_error.argtypes = [vp]
+    lib.fr_last_error.restype = C.c_char_p
+    lib.fr_destroy.argtypes = [vp]
+    lib.fr_destroy.restype = None
+    lib.fr_version.restype = C.c_int32
+    for name in EXPORTS:
+        if name not in ("fr_last_error", "fr_destroy", "fr_version"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _ptrs(seq):
+    arr = (C.c_void_p * len(seq))()
+    for i, t in enumerate(seq):
+        arr[i] = t if isinstance(t, int) else t.data_ptr()
+    return arr
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Solver:
+    """An FR discretisation of a mesh (fr_setup) and its entry points.
+
+    ``device=-1`` builds a host-only context (operators, points, pairs for
+    inspection); any other value is the CUDA device ordinal.
+    """
+
+    def __init__(self, mesh, order, system="euler", precision="fp64", device=0, **params):
+        lib = load()
+        self.lib = lib
+        self.mesh = mesh
+        self.ndims = mesh.ndims
+        self.nvars = mesh.ndims + 2
+        self.precision = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}[precision]
+        self.system = {"euler": EULER, "ns": NAVIER_STOKES}[system]
+        self.device = device
+        p = Params()
+        p.ndims, p.order, p.system, p.precision = mesh.ndims, order, self.system, self.precision
+        p.gamma = params.get("gamma", 1.4)
+        p.mu = params.get("mu", 0.0)
+        p.prandtl = params.get("prandtl", 0.72)
+        p.ldg_beta = params.get("ldg_beta", 0.5)
+        p.ldg_tau = params.get("ldg_tau", 0.1)
+        p.bc_rho = params.get("bc_rho", 1.0)
+        for i, v in enumerate(params.get("bc_v", (1.0, 0.0, 0.0))):
+            p.bc_v[i] = v
+        p.bc_p = params.get("bc_p", 1.0)
+        p.outflow_p = params.get("outflow_p", 1.0)
+        p.wall_cpTw = params.get("wall_cpTw", 1.0)
+        for i, v in enumerate(params.get("wall_v", (0.0, 0.0, 0.0))):
+            p.wall_v[i] = v
+        self.params = p
+        self._keep = []
+        blocks = (EBlock * len(mesh.blocks))()
+        for i, b in enumerate(mesh.blocks):
+            nodes = np.ascontiguousarray(b.nodes, dtype=np.float64)
+            self._keep.append(nodes)
+            blocks[i].etype = ETYPES[b.etype]
+            blocks[i].nnodes = nodes.shape[1]
+            blocks[i].nelem = nodes.shape[0]
+            blocks[i].nodes = nodes.ctypes.data_as(C.POINTER(C.c_double))
+        bf = np.ascontiguousarray(np.asarray(mesh.bfaces, np.int64).reshape(-1, 4))
+        per = np.ascontiguousarray(np.asarray(mesh.periodic, np.float64).reshape(-1, mesh.ndims))
+        self._keep += [bf, per]
+        m = MeshC()
+        m.ndims, m.nblocks, m.blocks = mesh.ndims, len(mesh.blocks), blocks
+        m.nbfaces = bf.shape[0]
+        m.bfaces = bf.ctypes.data_as(C.POINTER(C.c_int64))
+        m.nperiodic = per.shape[0]
+        m.periodic = per.ctypes.data_as(C.POINTER(C.c_double))
+        ctx = C.c_void_p()
+        st = lib.fr_setup(C.byref(m), C.byref(p), device, C.byref(ctx))
+        if st != OK:
+            raise FRError(st, lib.fr_last_error(None).decode())
+        self.ctx = ctx
+        self._keep = []
+
+    def _check(self, st):
+        if st != OK:
+            raise FRError(st, self.lib.fr_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.fr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nblocks(self):
+        return len(self.mesh.blocks)
+
+    def layout(self, b):
+        nu, nf, nv = C.c_int32(), C.c_int32(), C.c_int32()
+        ne, ld = C.c_int64(), C.c_int64()
+        self._check(self.lib.fr_layout(self.ctx, b, C.byref(nu), C.byref(nf), C.byref(nv), C.byref(ne), C.byref(ld)))
+        return dict(nupts=nu.value, nfpts=nf.value, nvars=nv.value, nelem=ne.value, ld=ld.value)
+
+    def solution_points(self, b):
+        L = self.layout(b)
+        out = np.empty((self.ndims, L["nupts"], L["nelem"]))
+        self._check(self.lib.fr_solution_points(self.ctx, b, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def operator(self, b, which):
+        r, c = C.c_int32(), C.c_int32()
+        self._check(self.lib.fr_operator(self.ctx, b, which, None, C.byref(r), C.byref(c)))
+        out = np.empty((r.value, c.value))
+        self._check(self.lib.fr_operator(self.ctx, b, which, out.ctypes.data_as(C.POINTER(C.c_double)), None, None))
+        return out
+
+    def pairs(self):
+        n = C.c_int64()
+        self._check(self.lib.fr_pairs(self.ctx, C.byref(n), None))
+        out = np.empty((n.value, 6), np.int64)
+        self._check(self.lib.fr_pairs(self.ctx, C.byref(n), out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    # --------------------------------------------------------- device entry points
+    @property
+    def dtype_name(self):
+        return "float64" if self.precision == FP64 else "float32"
+
+    def alloc_state(self, b, torch_mod=None):
+        import torch
+        L = self.layout(b)
+        dt = torch.float64 if self.precision == FP64 else torch.float32
+        return torch.zeros((L["nupts"], L["nvars"], L["ld"]), dtype=dt, device=f"cuda:{self.device}")
+
+    def pack(self, b, u_np):
+        """[nupts, nvars, nelem] numpy -> padded [nupts, nvars, ld] host array."""
+        L = self.layout(b)
+        dt = np.float64 if self.precision == FP64 else np.float32
+        out = np.zeros((L["nupts"], L["nvars"], L["ld"]), dt)
+        out[:, :, :L["nelem"]] = u_np
+        return out
+
+    def rhs(self, u, r, stream=None):
+        self._check(self.lib.fr_rhs(self.ctx, _ptrs(u), _ptrs(r), _stream_ptr(stream)))
+
+    def rhs_host(self, u, r, stream=None):
+        """u, r: lists of C-contiguous host arrays (numpy or pinned torch CPU tensors)."""
+        def hp(x):
+            return x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+        self._check(self.lib.fr_rhs_host(self.ctx, _ptrs([hp(x) for x in u]), _ptrs([hp(x) for x in r]),
+                                         _stream_ptr(stream)))
+
+    def rk4(self, u, dt, nsteps, stream=None):
+        self._check(self.lib.fr_rk4(self.ctx, _ptrs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+
+    def sum_weighted(self, u, stream=None):
+        out = np.zeros(self.nvars)
+        self._check(self.lib.fr_sum_weighted(self.ctx, _ptrs(u), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                             _stream_ptr(stream)))
+        return out
+
+    def check_finite(self, u, stream=None):
+        self._check(self.lib.fr_check_finite(self.ctx, _ptrs(u), _stream_ptr(stream)))
+
+    def profile_enable(self, on=True):
+        self._check(self.lib.fr_profile_enable(self.ctx, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel name: (launches, total ms)} since the previous read."""
+        nk = C.c_int32()
+        self.lib.fr_profile_read(self.ctx, C.byref(nk), None, None, None)
+        names = C.create_string_buffer(32 * nk.value)
+        launches = (C.c_int64 * nk.value)()
+        ms = (C.c_double * nk.value)()
+        self._check(self.lib.fr_profile_read(self.ctx, C.byref(nk), names, launches, ms))
+        out = {}
+        for k in range(nk.value):
+            name = names.raw[32 * k:32 * (k + 1)].split(b"\0", 1)[0].decode()
+            out[name] = (int(launches[k]), float(ms[k]))
+        return out
+
+    def sync_status(self):
+        return self.lib.fr_sync_status(self.ctx)

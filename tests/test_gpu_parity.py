@@ -1,0 +1,162 @@
+"""GPU parity: the CUDA right-hand side (through the C ABI) against the FP64
+oracle on the same seeded inputs, element by element.
+
+Tolerances: FP64 path rel-L2 <= 1e-12 per variable (both sides evaluate the
+same discretisation; only summation order and the fused operators
+M4 - M6 M0, M1 - M3 M2 differ).  FP32 path rel-L2 <= 1e-5, with the oracle
+evaluated on the same FP32-rounded input.
+"""
+import numpy as np
+import pytest
+
+from fr_inputs import periodic_box, annulus_mixed, fields
+from oracle.system import FRSystem
+from tests.libutil import ensure_built, oracle_state, rel_l2_per_var
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU test without a GPU"
+    ensure_built()
+    return t
+
+
+def gpu_rhs(torch, s, U, inplace=False):
+    u = [torch.from_numpy(s.pack(b, U[b])).cuda() for b in range(len(U))]
+    r = u if inplace else [torch.full_like(x, float("nan")) for x in u]
+    s.rhs(u, r)
+    torch.cuda.synchronize()
+    return [r[b].cpu().numpy()[:, :, :U[b].shape[2]].astype(np.float64) for b in range(len(U))]
+
+
+NS_PRM = dict(gamma=1.4, mu=0.02, prandtl=0.72, ldg_beta=0.5, ldg_tau=0.1)
+
+CASES = {
+    # name: (mesh factory, order, system, state factory)
+    "quad_euler_p2_vortex": (lambda: periodic_box("quad", 16, -5.0, 5.0), 2, "euler",
+                             lambda X: fields.isentropic_vortex(X, S=5.0, M=0.4, R=1.5)),
+    "quad_ns_p3_jitter_ragged": (lambda: periodic_box("quad", 12, 0.0, 2 * np.pi, jitter=0.12, seed=3), 3, "ns",
+                                 lambda X: fields.smooth_random(X, period=2 * np.pi, seed=5, amp=0.2)),
+    "hex_euler_p4": (lambda: periodic_box("hex", 3, 0.0, 2 * np.pi, jitter=0.08, seed=4), 4, "euler",
+                     lambda X: fields.smooth_random(X, period=2 * np.pi, seed=6, amp=0.2)),
+    "hex_ns_p3_tgv": (lambda: periodic_box("hex", 6, 0.0, 2 * np.pi, jitter=0.1, seed=2), 3, "ns",
+                      lambda X: fields.taylor_green(X, M=0.1)),
+    "hex_ns_p2_single_elem": (lambda: periodic_box("hex", 1, 0.0, 1.0), 2, "ns",
+                              lambda X: fields.smooth_random(X, period=1.0, seed=8, amp=0.1)),
+}
+
+
+def _mixed_case():
+    m = annulus_mixed(ntheta=24, nr_quad=3, nr_tri=3, r0=0.5, r1=4.0, jitter=0.05, seed=7)
+    m.bfaces[m.bfaces[:, 0] == 1, 3] = 1          # outer ring: subsonic outflow on some faces
+    m.bfaces[(m.bfaces[:, 0] == 1) & (m.bfaces[:, 1] % 2 == 0), 3] = 0
+    return m
+
+
+MIXED_PRM = dict(NS_PRM, bc_rho=1.0, bc_v=(1.0, 0.0, 0.0), bc_p=1 / (1.4 * 0.04), outflow_p=1 / (1.4 * 0.04),
+                 wall_cpTw=1.4 / 0.4 * (1 / (1.4 * 0.04)))
+
+
+def _case_solver(fr, name, prec):
+    mk, p, system, st = CASES[name]
+    m = mk()
+    prm = NS_PRM if system == "ns" else dict(gamma=1.4)
+    return m, p, system, st, prm
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rhs_fp64_matches_oracle(torch, name):
+    from paper_1312_1638_b300 import fr
+    m, p, system, st, prm = _case_solver(fr, name, "fp64")
+    o = FRSystem(m, p, system, **prm)
+    U = oracle_state(o, st)
+    R = o.rhs(U)
+    s = fr.Solver(m, p, system, "fp64", device=0, **prm)
+    G = gpu_rhs(torch, s, U)
+    for g, r in zip(G, R):
+        assert rel_l2_per_var(g, r) < 1e-12
+        assert np.abs(g - r).max() <= 1e-11 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rhs_fp32_matches_oracle(torch, name):
+    from paper_1312_1638_b300 import fr
+    m, p, system, st, prm = _case_solver(fr, name, "fp32")
+    o = FRSystem(m, p, system, **prm)
+    U = [u.astype(np.float32).astype(np.float64) for u in oracle_state(o, st)]
+    R = o.rhs(U)
+    s = fr.Solver(m, p, system, "fp32", device=0, **prm)
+    G = gpu_rhs(torch, s, U)
+    for g, r in zip(G, R):
+        assert rel_l2_per_var(g, r) < 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_rhs_mixed_mesh_with_boundaries(torch, prec, tol):
+    from paper_1312_1638_b300 import fr
+    m = _mixed_case()
+    o = FRSystem(m, 3, "ns", **MIXED_PRM)
+    U = oracle_state(o, lambda X: fields.smooth_random(X, seed=3, amp=0.1, vel0=(1.0, 0.0),
+                                                       p0=1 / (1.4 * 0.04)))
+    if prec == "fp32":
+        U = [u.astype(np.float32).astype(np.float64) for u in U]
+    R = o.rhs(U)
+    s = fr.Solver(m, 3, "ns", prec, device=0, **MIXED_PRM)
+    G = gpu_rhs(torch, s, U)
+    for g, r in zip(G, R):
+        assert rel_l2_per_var(g, r) < tol
+
+
+def test_rhs_in_place_and_host_buffers(torch):
+    from paper_1312_1638_b300 import fr
+    m, p, system, st, prm = _case_solver(fr, "quad_ns_p3_jitter_ragged", "fp64")
+    o = FRSystem(m, p, system, **prm)
+    U = oracle_state(o, st)
+    s = fr.Solver(m, p, system, "fp64", device=0, **prm)
+    A = gpu_rhs(torch, s, U)
+    B = gpu_rhs(torch, s, U, inplace=True)
+    uh = [s.pack(0, U[0])]
+    rh = [np.zeros_like(uh[0])]
+    s.rhs_host(uh, rh)
+    assert np.array_equal(A[0], B[0])                    # r aliasing u gives the same bits
+    assert np.array_equal(A[0], rh[0][:, :, :U[0].shape[2]])
+
+
+def test_rk4_matches_oracle(torch):
+    from paper_1312_1638_b300 import fr
+    m = periodic_box("quad", 16, -5.0, 5.0)
+    o = FRSystem(m, 2, "euler")
+    U = oracle_state(o, lambda X: fields.isentropic_vortex(X, S=5.0, M=0.4, R=1.5))
+    ref = o.rk4(U, 1e-3, 10)
+    s = fr.Solver(m, 2, "euler", "fp64", device=0)
+    u = [torch.from_numpy(s.pack(0, U[0])).cuda()]
+    s.rk4(u, 1e-3, 10)
+    torch.cuda.synchronize()
+    g = u[0].cpu().numpy()[:, :, :U[0].shape[2]]
+    assert rel_l2_per_var(g, ref[0]) < 1e-13
+    assert np.abs(g - ref[0]).max() < 1e-12
+
+
+def test_weighted_sums_conservation_and_nonfinite_flag(torch):
+    from paper_1312_1638_b300 import fr
+    m, p, system, st, prm = _case_solver(fr, "hex_ns_p3_tgv", "fp64")
+    o = FRSystem(m, p, system, **prm)
+    U = oracle_state(o, st)
+    s = fr.Solver(m, p, system, "fp64", device=0, **prm)
+    u = [torch.from_numpy(s.pack(0, U[0])).cuda()]
+    tot = s.sum_weighted(u)
+    ref = np.einsum("un,uvn->v", o.quadrature_weights(0), U[0])
+    assert np.allclose(tot, ref, rtol=1e-13)
+    r = [torch.empty_like(u[0])]
+    s.rhs(u, r)
+    dtot = s.sum_weighted(r)
+    scale = np.einsum("un,uvn->v", o.quadrature_weights(0), np.abs(o.rhs(U)[0]))
+    assert np.all(np.abs(dtot) < 1e-12 * scale.max())
+    assert s.sync_status() == fr.OK
+    r[0][3, 1, 5] = float("nan")                         # a NaN planted from the host
+    s.check_finite(r)
+    assert s.sync_status() == fr.ERR_NONFINITE
+    assert s.sync_status() == fr.OK                       # the flag is cleared by reading it

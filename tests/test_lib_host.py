@@ -1,0 +1,107 @@
+"""CPU tests of the C-ABI library: it loads, exports every function declared
+in include/fr.h, and its host-side set-up (operators, solution points,
+interface pairs, error statuses) agrees with the oracle.  No compute calls
+are made (no GPU here)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from tests.libutil import ensure_built, declared_functions
+from fr_inputs import periodic_box, annulus_mixed, Mesh, Block
+from oracle.system import FRSystem
+
+
+@pytest.fixture(scope="module")
+def fr():
+    ensure_built()
+    from paper_1312_1638_b300 import fr as frmod
+    return frmod
+
+
+def test_library_exports_every_declared_symbol(fr):
+    lib = ctypes.CDLL(fr.LIBPATH)
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(fr.EXPORTS)
+    assert fr.load().fr_version() == 1
+
+
+CASES = [("quad", 3, 1, 0.1), ("quad", 3, 4, 0.1), ("hex", 2, 2, 0.1), ("hex", 2, 4, 0.0)]
+
+
+@pytest.mark.parametrize("etype,n,p,jit", CASES)
+def test_operators_and_points_match_oracle(fr, etype, n, p, jit):
+    m = periodic_box(etype, n, 0.0, 2 * np.pi, jitter=jit, seed=1)
+    s = fr.Solver(m, p, "ns", "fp64", device=-1)
+    o = FRSystem(m, p, "ns")
+    el = o.eles[0]
+    for which, M in [(0, el.M0), (1, el.M1), (2, el.M2), (3, el.M3), (4, el.M4), (6, el.M6),
+                     (7, el.M4 - el.M6 @ el.M0), (8, el.M1 - el.M3 @ el.M2)]:
+        assert np.allclose(s.operator(0, which), M, atol=1e-12), which
+    assert np.allclose(s.solution_points(0), o.solution_coords(0), atol=1e-13)
+
+
+def _pair_set(rows):
+    return {tuple(int(v) for v in r) for r in rows}
+
+
+@pytest.mark.parametrize("etype,n,p,jit", CASES[:3])
+def test_pairs_match_oracle(fr, etype, n, p, jit):
+    m = periodic_box(etype, n, 0.0, 1.0, jitter=jit, seed=4, shuffle=True)
+    s = fr.Solver(m, p, "euler", "fp64", device=-1)
+    o = FRSystem(m, p)
+    P = o.pairs
+    ref = np.stack([P["bL"], P["fL"], P["nL"], P["bR"], P["fR"], P["nR"]], 1)
+    assert _pair_set(s.pairs()) == _pair_set(ref)
+
+
+def test_mixed_mesh_setup_matches_oracle(fr):
+    m = annulus_mixed(ntheta=16, nr_quad=2, nr_tri=2, r0=0.5, r1=3.0, jitter=0.05, seed=3)
+    s = fr.Solver(m, 3, "ns", "fp64", device=-1)
+    o = FRSystem(m, 3, "ns")
+    for b in range(2):
+        el = o.eles[b]
+        for which, M in [(0, el.M0), (3, el.M3), (4, el.M4)]:
+            assert np.allclose(s.operator(b, which), M, atol=1e-12)
+        assert np.allclose(s.solution_points(b), o.solution_coords(b), atol=1e-13)
+    P = o.pairs
+    ref = np.stack([P["bL"], P["fL"], P["nL"], P["bR"], P["fR"], P["nR"]], 1)
+    assert _pair_set(s.pairs()) == _pair_set(ref)
+
+
+def test_layout_padding(fr):
+    m = periodic_box("hex", 3, jitter=0.0)
+    s = fr.Solver(m, 2, "euler", "fp32", device=-1)
+    L = s.layout(0)
+    assert L == dict(nupts=27, nfpts=54, nvars=5, nelem=27, ld=128)
+
+
+def test_unmatched_face_is_a_mesh_error(fr):
+    m = periodic_box("quad", 3)
+    m.periodic = m.periodic[:1]           # drop the y identification
+    with pytest.raises(fr.FRError) as e:
+        fr.Solver(m, 2, device=-1)
+    assert e.value.status == fr.ERR_MESH
+
+
+def test_inverted_element_is_a_mesh_error(fr):
+    m = periodic_box("quad", 2)
+    nodes = m.blocks[0].nodes.copy()
+    nodes[0] = nodes[0][[1, 0, 3, 2]]     # mirror one element
+    m2 = Mesh(2, [Block("quad", nodes)], m.bfaces, m.periodic)
+    with pytest.raises(fr.FRError) as e:
+        fr.Solver(m2, 2, device=-1)
+    assert e.value.status == fr.ERR_MESH
+
+
+def test_bad_arguments(fr):
+    m = periodic_box("quad", 2)
+    with pytest.raises(fr.FRError) as e:
+        fr.Solver(m, 0, device=-1)
+    assert e.value.status == fr.ERR_ARG
+    s = fr.Solver(m, 1, device=-1)
+    assert s.lib.fr_rhs(s.ctx, None, None, None) in (fr.ERR_ARG, fr.ERR_UNSUPPORTED)
+    assert s.lib.fr_layout(s.ctx, 5, None, None, None, None, None) == fr.ERR_ARG
