@@ -91,6 +91,20 @@ typedef struct {
     double bc_rho, bc_v[3], bc_p;   /* free-stream ghost state */
     double outflow_p;               /* subsonic-outflow pressure */
     double wall_cpTw, wall_v[3];    /* isothermal wall: C_p T_w and velocity */
+    /* Perturbation form (ref_rho = 0: the plain form).  The kernels carry
+     * u' = u - u_ref about the state at rest u_ref = (ref_rho, 0, E_ref) with
+     * E_ref = ref_p / (gamma - 1): interpolation and gradients act on u' (exact:
+     * rows of M0 sum to one, rows of M4 to zero), pressure is formed as
+     * p' = (gamma-1)(E' - rho|v|^2/2), the momentum flux carries p' and the
+     * energy flux is v (E' + p' - h_ref rho') with h_ref = gamma E_ref / ref_rho,
+     * and the result is finished with R_E += h_ref R_rho.  The energy split is
+     * exact by linearity of R in the fluxes; dropping the constant pressure
+     * flux is exact wherever the mesh preserves a free stream (affine
+     * elements, quadratic 2D and trilinear 3D elements at p >= 2).  Choosing
+     * the mean density and pressure keeps FP32 / split-precision results
+     * accurate at low Mach number, where u and the fluxes are dominated by
+     * constants whose divergence vanishes. */
+    double ref_rho, ref_p;
 } fr_params;
 
 /* One block of elements of a single type, host memory, read during fr_setup only. */
@@ -208,7 +222,7 @@ const char* fr_last_error(const fr_ctx* ctx);
 void fr_destroy(fr_ctx* ctx);
 
 /* ABI version (increments on any signature change). */
-int32_t fr_version(void);
+int32_t fr_version(void);   /* 2 */
 
 #ifdef __cplusplus
 }

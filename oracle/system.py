@@ -162,8 +162,15 @@ class FRSystem:
             arrs[bb][f[m], :, n[m]] = vals[:, m].T
 
     # ------------------------------------------------------------ RHS
-    def rhs(self, U):
-        """R(U) for a list of per-block states U_b[nupts, nvars, nelem]."""
+    def rhs(self, U, scale=False):
+        """R(U) for a list of per-block states U_b[nupts, nvars, nelem].
+
+        With scale=True also returns, per block, the magnitude
+        S = |J^{-1}| (|M3| |D~| + |M3| |M2| |F~| + |M1| |F~|) of the terms whose
+        sum is R (step 5 below): the componentwise forward-error scale of the
+        final contraction, |R_computed - R| <= c eps S for a computation with
+        unit round-off eps in its last stages.
+        """
         prm = self.prm
         gamma, beta, tau = prm["gamma"], prm["ldg_beta"], prm["ldg_tau"]
         mu, pr = prm["mu"], prm["prandtl"]
@@ -236,12 +243,18 @@ class FRSystem:
                 Fb[:, m] = Fm
             self._scatter(D, B["b"], B["f"], B["n"], B["mag"] * Fb)
         # 5./6. corrected divergence and negation
-        R = []
+        R, S = [], []
         for el, g, dd, ft in zip(self.eles, self.geo, D, Ft):
             rt = (np.einsum("uf,fvn->uvn", el.M3, dd - np.einsum("fa,avn->fvn", el.M2, ft))
                   + np.einsum("ua,avn->uvn", el.M1, ft))
             R.append(-rt / g["det"].T[:, None, :])
-        return R
+            if scale:
+                aM3, aM2, aM1 = np.abs(el.M3), np.abs(el.M2), np.abs(el.M1)
+                aD, aF = np.abs(dd), np.abs(ft)
+                st = (np.einsum("uf,fvn->uvn", aM3, aD + np.einsum("fa,avn->fvn", aM2, aF))
+                      + np.einsum("ua,avn->uvn", aM1, aF))
+                S.append(st / np.abs(g["det"]).T[:, None, :])
+        return (R, S) if scale else R
 
     # ------------------------------------------------------------ time stepping
     def rk4(self, U, dt, nsteps=1):

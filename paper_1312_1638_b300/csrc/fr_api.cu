@@ -203,7 +203,7 @@ void upload_device(fr_ctx* c) {
 // ====================================================================== ABI
 extern "C" {
 
-int32_t fr_version(void) { return 1; }
+int32_t fr_version(void) { return 2; }
 
 const char* fr_last_error(const fr_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_err.c_str(); }
 
@@ -282,6 +282,12 @@ fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx
         c->dev.precision = prm->precision; c->dev.order = prm->order;
         fr::DevParams& P = c->dev.prm;
         P.gamma = prm->gamma; P.mu = prm->mu; P.prandtl = prm->prandtl; P.beta = prm->ldg_beta; P.tau = prm->ldg_tau;
+        if (prm->ref_rho < 0 || (prm->ref_rho == 0 && prm->ref_p != 0))
+            throw Fail{FR_ERR_ARG, "perturbation form needs ref_rho > 0 (or ref_rho = ref_p = 0)"};
+        P.ref_rho = prm->ref_rho;
+        P.ref_p = prm->ref_rho > 0 ? prm->ref_p : 0.0;
+        P.ref_E = P.ref_p / (prm->gamma - 1.0);
+        P.ref_h = prm->ref_rho > 0 ? prm->gamma * P.ref_E / prm->ref_rho : 0.0;
         P.bc_rho = prm->bc_rho; P.bc_p = prm->bc_p; P.outflow_p = prm->outflow_p; P.wall_cpTw = prm->wall_cpTw;
         for (int i = 0; i < 3; ++i) { P.bc_v[i] = prm->bc_v[i]; P.wall_v[i] = prm->wall_v[i]; }
         if (device >= 0) {

@@ -12,6 +12,8 @@ namespace fr {
 struct DevParams {
     double gamma, mu, prandtl, beta, tau;
     double bc_rho, bc_v[3], bc_p, outflow_p, wall_cpTw, wall_v[3];
+    // perturbation form: reference state at rest (all zero = plain form)
+    double ref_rho, ref_E, ref_p, ref_h;
 };
 
 // One element block on the device.  Buffers hold T = double (FP64) or float.
@@ -54,7 +56,7 @@ struct DevBndGroup {           // boundary flux points of one block and one type
 // kernel when profiling is enabled.
 enum KernelId {
     K_DISU = 0, K_COMM_SOL, K_COMM_SOL_BC, K_TGRADU, K_GRADCORU, K_GRADFPTS, K_TDISF, K_COMM_FLUX,
-    K_COMM_FLUX_BC, K_TDIVF, K_RK_STAGE, K_NKERNELS
+    K_COMM_FLUX_BC, K_TDIVF, K_RK_STAGE, K_ENERGY_FIX, K_NKERNELS
 };
 extern const char* const kKernelNames[K_NKERNELS];
 

@@ -18,6 +18,13 @@ namespace fr {
 // C = A [B1; B2] with A = [A1 | A2] stored as one M x (K1 + K2) row-major
 // matrix; B rows k < K1 come from B1, the rest from B2 (both N columns,
 // row stride N).  epi = 1 applies -1/J (Eq. negdivconf) per (row, element).
+// B rows in [ks0, ks1) are solution states: the reference state of the
+// perturbation form, sub.v[alpha] for column alpha*ld + n, is subtracted as
+// they are loaded.
+template <typename T>
+struct Sub {
+    T v[5];
+};
 template <typename T> struct GemmCfg;
 template <> struct GemmCfg<float>  { static constexpr int TN = 128, RN = 4, MB = 64, RM = 8, KC = 16; };
 template <> struct GemmCfg<double> { static constexpr int TN = 64,  RN = 2, MB = 64, RM = 8, KC = 16; };
@@ -26,7 +33,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int K, int K1, const T* __restrict__ A, const T* __restrict__ B1,
             const T* __restrict__ B2, int64_t N, T* __restrict__ C, int epi,
-            const T* __restrict__ rcp, int64_t ld) {
+            const T* __restrict__ rcp, int64_t ld, int ks0, int ks1, Sub<T> sub) {
     using G = GemmCfg<T>;
     constexpr int TN = G::TN, RN = G::RN, MB = G::MB, RM = G::RM, KC = G::KC;
     __shared__ __align__(16) T As[KC][MB];
@@ -52,7 +59,10 @@ gemm_kernel(int M, int K, int K1, const T* __restrict__ A, const T* __restrict__
                 int gk = k0 + kk;
                 int64_t gc = col0 + c;
                 T v = T(0);
-                if (gk < K && gc < N) v = gk < K1 ? B1[(int64_t)gk * N + gc] : B2[(int64_t)(gk - K1) * N + gc];
+                if (gk < K && gc < N) {
+                    v = gk < K1 ? B1[(int64_t)gk * N + gc] : B2[(int64_t)(gk - K1) * N + gc];
+                    if (gk >= ks0 && gk < ks1) v -= sub.v[gc / ld];
+                }
                 Bs[kk][c] = v;
             }
             __syncthreads();
@@ -87,73 +97,105 @@ gemm_kernel(int M, int K, int K1, const T* __restrict__ A, const T* __restrict__
 
 template <typename T>
 static void gemm(int M, int K, int K1, const void* A, const void* B1, const void* B2, int64_t N,
-                 void* C, int epi, const void* rcp, int64_t ld, cudaStream_t st) {
+                 void* C, int epi, const void* rcp, int64_t ld, cudaStream_t st, int ks0 = 0, int ks1 = 0,
+                 Sub<T> sub = Sub<T>{}) {
     constexpr int TN = GemmCfg<T>::TN;
     dim3 grid((unsigned)((N + TN - 1) / TN));
     gemm_kernel<T><<<grid, 256, 0, st>>>(M, K, K1, (const T*)A, (const T*)B1, (const T*)B2, N, (T*)C, epi,
-                                         (const T*)rcp, ld);
+                                         (const T*)rcp, ld, ks0, ks1, sub);
 }
 
 // ============================================================ gas dynamics
+// Every routine takes the perturbation state u' = u - u_ref about the
+// reference state at rest u_ref = (rho_ref, 0, E_ref), p_ref = (gamma-1) E_ref,
+// h_ref = gamma E_ref / rho_ref.  With u_ref = 0 (Ref all zero) these are the
+// plain Euler / NS expressions of Sec. 4 (Eq. eulerflux, idealgas, visflux).
+template <typename T>
+struct Ref {
+    T rho, E, p, h;
+};
+
+template <typename T>
+__device__ __forceinline__ Ref<T> make_ref(const DevParams& P) {
+    return Ref<T>{T(P.ref_rho), T(P.ref_E), T(P.ref_p), T(P.ref_h)};
+}
+
 template <typename T, int D>
 struct Gas {
     static constexpr int NV = D + 2;
 
-    __device__ static __forceinline__ T pressure(const T* u, T gm1) {
-        T ke = T(0);
+    // full density, velocity, pressure perturbation p' and full pressure
+    __device__ static __forceinline__ void prim(const T* u, const Ref<T>& r, T gm1, T& rho, T* v, T& pp, T& p) {
+        rho = r.rho + u[0];
+        T rinv = T(1) / rho, ke = T(0);
 #pragma unroll
-        for (int i = 0; i < D; ++i) ke += u[1 + i] * u[1 + i];
-        return gm1 * (u[D + 1] - T(0.5) * ke / u[0]);
+        for (int i = 0; i < D; ++i) { v[i] = u[1 + i] * rinv; ke += u[1 + i] * v[i]; }
+        pp = gm1 * (u[D + 1] - T(0.5) * ke);
+        p = r.p + pp;
     }
 
-    // normal inviscid flux n.f(u) (Eq. eulerflux); returns p and v.n
-    __device__ static __forceinline__ void normal_flux(const T* u, const T* n, T gm1, T* fn, T& p, T& vn) {
-        T rinv = T(1) / u[0];
-        p = pressure(u, gm1);
+    // normal inviscid flux n.f in perturbation form; returns full p, rho and v.n
+    __device__ static __forceinline__ void normal_flux(const T* u, const T* n, const Ref<T>& r, T gm1, T* fn, T& p,
+                                                       T& rho, T& vn) {
+        T v[D], pp;
+        prim(u, r, gm1, rho, v, pp, p);
         vn = T(0);
 #pragma unroll
-        for (int i = 0; i < D; ++i) vn += n[i] * u[1 + i] * rinv;
-        fn[0] = u[0] * vn;
+        for (int i = 0; i < D; ++i) vn += n[i] * v[i];
+        T mn = T(0);
 #pragma unroll
-        for (int i = 0; i < D; ++i) fn[1 + i] = u[1 + i] * vn + p * n[i];
-        fn[D + 1] = (u[D + 1] + p) * vn;
+        for (int i = 0; i < D; ++i) mn += n[i] * u[1 + i];
+        fn[0] = mn;
+#pragma unroll
+        for (int i = 0; i < D; ++i) fn[1 + i] = u[1 + i] * vn + pp * n[i];
+        fn[D + 1] = vn * (u[D + 1] + pp - r.h * u[0]);
     }
 
-    // Rusanov common inviscid flux (App. B)
-    __device__ static __forceinline__ void rusanov(const T* uL, const T* uR, const T* n, T gamma, T* F) {
-        T fL[NV], fR[NV], pL, pR, vnL, vnR;
-        normal_flux(uL, n, gamma - T(1), fL, pL, vnL);
-        normal_flux(uR, n, gamma - T(1), fR, pR, vnR);
-        T s = sqrt(gamma * (pL + pR) / (uL[0] + uR[0])) + T(0.5) * fabs(vnL + vnR);
+    // Rusanov common inviscid flux (App. B) in perturbation form
+    __device__ static __forceinline__ void rusanov(const T* uL, const T* uR, const T* n, const Ref<T>& r, T gamma,
+                                                   T* F) {
+        T fL[NV], fR[NV], pL, pR, rL, rR, vnL, vnR;
+        normal_flux(uL, n, r, gamma - T(1), fL, pL, rL, vnL);
+        normal_flux(uR, n, r, gamma - T(1), fR, pR, rR, vnR);
+        T s = sqrt(gamma * (pL + pR) / (rL + rR)) + T(0.5) * fabs(vnL + vnR);
+        T du[NV];
+        jump(uL, uR, r, du);
 #pragma unroll
-        for (int a = 0; a < NV; ++a) F[a] = T(0.5) * (fL[a] + fR[a]) + T(0.5) * s * (uL[a] - uR[a]);
+        for (int a = 0; a < NV; ++a) F[a] = T(0.5) * (fL[a] + fR[a]) + T(0.5) * s * du[a];
     }
 
-    // full inviscid flux tensor f[i][a]
-    __device__ static __forceinline__ void inv_flux(const T* u, T gm1, T f[D][NV]) {
-        T rinv = T(1) / u[0];
-        T p = pressure(u, gm1);
-        T v[D];
+    // u_L - u_R in the variables of the split: the energy equation carries
+    // E - h_ref rho, so its jump is dE - h_ref drho
+    __device__ static __forceinline__ void jump(const T* uL, const T* uR, const Ref<T>& r, T* du) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) v[i] = u[1 + i] * rinv;
+        for (int a = 0; a < NV; ++a) du[a] = uL[a] - uR[a];
+        du[D + 1] -= r.h * du[0];
+    }
+
+    // full inviscid flux tensor f[i][a] in perturbation form
+    __device__ static __forceinline__ void inv_flux(const T* u, const Ref<T>& r, T gm1, T f[D][NV]) {
+        T rho, v[D], pp, p;
+        prim(u, r, gm1, rho, v, pp, p);
+        T e = u[D + 1] + pp - r.h * u[0];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             f[i][0] = u[1 + i];
 #pragma unroll
-            for (int j = 0; j < D; ++j) f[i][1 + j] = u[1 + j] * v[i] + (i == j ? p : T(0));
-            f[i][D + 1] = v[i] * (u[D + 1] + p);
+            for (int j = 0; j < D; ++j) f[i][1 + j] = u[1 + j] * v[i] + (i == j ? pp : T(0));
+            f[i][D + 1] = v[i] * e;
         }
     }
 
     // viscous flux f_vis (Eq. visflux), constant mu; kappa = mu gamma / (Pr (gamma-1))
-    // multiplies d(p/rho) (T = p / (rho C_v (gamma-1)), Delta = mu C_p / Pr)
-    __device__ static __forceinline__ void vis_flux(const T* u, const T q[D][NV], T gm1, T mu, T kappa,
-                                                    T fv[D][NV]) {
-        T rinv = T(1) / u[0];
-        T v[D], v2 = T(0);
+    // multiplies d(p/rho) (T = p / (rho C_v (gamma-1)), Delta = mu C_p / Pr).
+    // Gradients are unaffected by the reference shift.
+    __device__ static __forceinline__ void vis_flux(const T* u, const T q[D][NV], const Ref<T>& r, T gm1, T mu,
+                                                    T kappa, T fv[D][NV]) {
+        T rho, v[D], pp, p;
+        prim(u, r, gm1, rho, v, pp, p);
+        T rinv = T(1) / rho, v2 = T(0);
 #pragma unroll
-        for (int i = 0; i < D; ++i) { v[i] = u[1 + i] * rinv; v2 += v[i] * v[i]; }
-        T p = gm1 * (u[D + 1] - T(0.5) * u[0] * v2);
+        for (int i = 0; i < D; ++i) v2 += v[i] * v[i];
         T dv[D][D], dpr[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
@@ -187,32 +229,36 @@ struct Gas {
         }
     }
 
-    // ghost states (App. C): inviscid ghost gi, LDG ghost gl; returns whether
-    // the ghost gradient is q_L (wall) or zero
-    __device__ static __forceinline__ bool ghosts(int bctype, const T* uL, const DevParams& P, T* gi, T* gl) {
+    // ghost states (App. C) as perturbations: inviscid ghost gi, LDG ghost gl;
+    // returns whether the ghost gradient is q_L (wall) or zero.  Constant parts
+    // (p_f - p_ref, rho_ref C_pT_w / gamma - E_ref) are formed in FP64.
+    __device__ static __forceinline__ bool ghosts(int bctype, const T* uL, const DevParams& P, const Ref<T>& r,
+                                                  T* gi, T* gl) {
         T gamma = T(P.gamma), gm1 = gamma - T(1);
         if (bctype == 0) {
             T rho = T(P.bc_rho), ke = T(0);
-            gi[0] = rho;
+            gi[0] = T(P.bc_rho - P.ref_rho);
 #pragma unroll
             for (int i = 0; i < D; ++i) { gi[1 + i] = rho * T(P.bc_v[i]); ke += T(P.bc_v[i]) * T(P.bc_v[i]); }
-            gi[D + 1] = T(P.bc_p) / gm1 + T(0.5) * rho * ke;
+            gi[D + 1] = T((P.bc_p - P.ref_p) / (P.gamma - 1.0)) + T(0.5) * rho * ke;
 #pragma unroll
             for (int a = 0; a < NV; ++a) gl[a] = gi[a];
             return false;
         }
+        T rho = r.rho + uL[0];
         if (bctype == 1) {
-            T rho = uL[0], ke = T(0);
-            gi[0] = rho;
+            T ke = T(0);
+            gi[0] = uL[0];
 #pragma unroll
             for (int i = 0; i < D; ++i) { gi[1 + i] = uL[1 + i]; ke += uL[1 + i] * uL[1 + i]; }
-            gi[D + 1] = T(P.outflow_p) / gm1 + T(0.5) * ke / rho;
+            gi[D + 1] = T((P.outflow_p - P.ref_p) / (P.gamma - 1.0)) + T(0.5) * ke / rho;
 #pragma unroll
             for (int a = 0; a < NV; ++a) gl[a] = gi[a];
             return false;
         }
-        T rho = uL[0], rinv = T(1) / rho, cpt = T(P.wall_cpTw) / gamma, k1 = T(0), k2 = T(0);
-        gi[0] = rho; gl[0] = rho;
+        T rinv = T(1) / rho, cpt = T(P.wall_cpTw / P.gamma), k1 = T(0), k2 = T(0);
+        T e0 = T(P.ref_rho * P.wall_cpTw / P.gamma - P.ref_E);
+        gi[0] = uL[0]; gl[0] = uL[0];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             T vw = T(P.wall_v[i]);
@@ -220,8 +266,10 @@ struct Gas {
             gi[1 + i] = rho * vm; k1 += vm * vm;
             gl[1 + i] = rho * vw; k2 += vw * vw;
         }
-        gi[D + 1] = rho * (cpt + T(0.5) * k1);
-        gl[D + 1] = rho * (cpt + T(0.5) * k2);
+        // rho (C_pT_w/gamma + |v|^2/2) - E_ref = rho' C_pT_w/gamma + e0 + rho |v|^2/2
+        gi[D + 1] = uL[0] * cpt + e0 + T(0.5) * rho * k1;
+        gl[D + 1] = uL[0] * cpt + e0 + T(0.5) * rho * k2;
+        (void)gm1;
         return true;
     }
 };
@@ -264,12 +312,15 @@ __global__ void tflux_kernel(int nupts, int64_t nelem, int64_t ld, const T* __re
     int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s = blockIdx.y;
     if (n >= nelem) return;
+    const Ref<T> rf = make_ref<T>(P);
     T u[NV];
 #pragma unroll
     for (int a = 0; a < NV; ++a) u[a] = U[((int64_t)s * NV + a) * ld + n];
+    u[0] -= rf.rho;
+    u[D + 1] -= rf.E;
     T gamma = T(P.gamma), gm1 = gamma - T(1);
     T f[D][NV];
-    Gas<T, D>::inv_flux(u, gm1, f);
+    Gas<T, D>::inv_flux(u, rf, gm1, f);
     if (NS) {
         T q[D][NV], fv[D][NV];
 #pragma unroll
@@ -277,7 +328,7 @@ __global__ void tflux_kernel(int nupts, int64_t nelem, int64_t ld, const T* __re
 #pragma unroll
             for (int a = 0; a < NV; ++a) q[j][a] = Q[((int64_t)(j * nupts + s) * NV + a) * ld + n];
         T mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
-        Gas<T, D>::vis_flux(u, q, gm1, mu, kappa, fv);
+        Gas<T, D>::vis_flux(u, q, rf, gm1, mu, kappa, fv);
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -329,7 +380,7 @@ __global__ void comm_sol_bc_kernel(int64_t nb, int bctype, const uint32_t* __res
     T uL[NV], gi[NV], gl[NV];
 #pragma unroll
     for (int a = 0; a < NV; ++a) uL[a] = Uf[o + a * ld];
-    Gas<T, D>::ghosts(bctype, uL, P, gi, gl);
+    Gas<T, D>::ghosts(bctype, uL, P, make_ref<T>(P), gi, gl);
     T beta = T(P.beta);
 #pragma unroll
     for (int a = 0; a < NV; ++a) C[o + a * ld] = (T(0.5) - beta) * uL[a] + (T(0.5) + beta) * gl[a];
@@ -353,7 +404,8 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
 #pragma unroll
     for (int i = 0; i < D; ++i) n[i] = nrm[i * npairs + k];
     T gamma = T(P.gamma);
-    Gas<T, D>::rusanov(uL, uR, n, gamma, F);
+    const Ref<T> rf = make_ref<T>(P);
+    Gas<T, D>::rusanov(uL, uR, n, rf, gamma, F);
     if (NS) {
         T qL[D][NV], qR[D][NV], fvL[D][NV], fvR[D][NV];
 #pragma unroll
@@ -364,15 +416,17 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
                 qR[j][a] = QfR[j * qsR + oR + a * ldR];
             }
         T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
-        Gas<T, D>::vis_flux(uL, qL, gm1, mu, kappa, fvL);
-        Gas<T, D>::vis_flux(uR, qR, gm1, mu, kappa, fvR);
+        Gas<T, D>::vis_flux(uL, qL, rf, gm1, mu, kappa, fvL);
+        Gas<T, D>::vis_flux(uR, qR, rf, gm1, mu, kappa, fvR);
         T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
+        T du[NV];
+        Gas<T, D>::jump(uL, uR, rf, du);
 #pragma unroll
         for (int a = 0; a < NV; ++a) {
             T fv = T(0);
 #pragma unroll
             for (int i = 0; i < D; ++i) fv += n[i] * (wl * fvL[i][a] + wr * fvR[i][a]);
-            F[a] = F[a] - fv + tau * (uL[a] - uR[a]);
+            F[a] = F[a] - fv + tau * du[a];
         }
     }
     T mL = magL[k], mR = magR[k];
@@ -396,9 +450,10 @@ __global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __re
     for (int a = 0; a < NV; ++a) uL[a] = Uf[o + a * ld];
 #pragma unroll
     for (int i = 0; i < D; ++i) n[i] = nrm[i * nb + k];
-    bool grad_is_qL = Gas<T, D>::ghosts(bctype, uL, P, gi, gl);
+    const Ref<T> rf = make_ref<T>(P);
+    bool grad_is_qL = Gas<T, D>::ghosts(bctype, uL, P, rf, gi, gl);
     T gamma = T(P.gamma);
-    Gas<T, D>::rusanov(uL, gi, n, gamma, F);
+    Gas<T, D>::rusanov(uL, gi, n, rf, gamma, F);
     if (NS) {
         T qL[D][NV], fvL[D][NV], fvR[D][NV], qg[D][NV];
 #pragma unroll
@@ -409,20 +464,32 @@ __global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __re
                 qg[j][a] = grad_is_qL ? qL[j][a] : T(0);
             }
         T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
-        Gas<T, D>::vis_flux(uL, qL, gm1, mu, kappa, fvL);
-        Gas<T, D>::vis_flux(gl, qg, gm1, mu, kappa, fvR);
+        Gas<T, D>::vis_flux(uL, qL, rf, gm1, mu, kappa, fvL);
+        Gas<T, D>::vis_flux(gl, qg, rf, gm1, mu, kappa, fvR);
         T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
+        T du[NV];
+        Gas<T, D>::jump(uL, gl, rf, du);
 #pragma unroll
         for (int a = 0; a < NV; ++a) {
             T fv = T(0);
 #pragma unroll
             for (int i = 0; i < D; ++i) fv += n[i] * (wl * fvL[i][a] + wr * fvR[i][a]);
-            F[a] = F[a] - fv + tau * (uL[a] - gl[a]);
+            F[a] = F[a] - fv + tau * du[a];
         }
     }
     T m = mag[k];
 #pragma unroll
     for (int a = 0; a < NV; ++a) Uf[o + a * ld] = m * F[a];
+}
+
+// R_E += h_ref R_rho: undo the energy split of the perturbation form
+template <typename T>
+__global__ void energy_fix_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, T* __restrict__ R, T href) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    T* r = R + (int64_t)s * nvars * ld + n;
+    r[(int64_t)(nvars - 1) * ld] += href * r[0];
 }
 
 // ============================================================ RK4 combine
@@ -481,7 +548,7 @@ __global__ void check_finite_kernel(int npts, int nvars, int64_t nelem, int64_t 
 // ============================================================ profiling
 const char* const kKernelNames[K_NKERNELS] = {"disu_gemm", "comm_sol", "comm_sol_bc", "tgradu_gemm",
                                               "gradcoru", "gradfpts_gemm", "tdisf", "comm_flux",
-                                              "comm_flux_bc", "tdivf_gemm", "rk_stage"};
+                                              "comm_flux_bc", "tdivf_gemm", "rk_stage", "energy_fix"};
 
 static cudaEvent_t prof_event(DevCtx& c) {
     if (!c.pool.empty()) {
@@ -540,11 +607,15 @@ template <typename T, int D>
 static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
     constexpr int NV = D + 2;
     const bool ns = c.system == 1;
-    // 1. U^(f) = M0 U  (K1, disu)
+    Sub<T> sub{};
+    sub.v[0] = T(c.prm.ref_rho);
+    sub.v[NV - 1] = T(c.prm.ref_E);
+    // 1. U'^(f) = M0 (U - u_ref)  (K1, disu)
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
         prof_begin(c, K_DISU, st);
-        gemm<T>(B.nfpts, B.nupts, B.nupts, B.opM0, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0, nullptr, B.ld, st);
+        gemm<T>(B.nfpts, B.nupts, B.nupts, B.opM0, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0, nullptr, B.ld, st,
+                0, B.nupts, sub);
         prof_end(c, st);
     }
     if (ns) {
@@ -570,7 +641,8 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
             int64_t N = (int64_t)NV * B.ld;
             // 3. Q~ = M6 C + (M4 - M6 M0) U  (tgradu, eq. tquptsm)
             prof_begin(c, K_TGRADU, st);
-            gemm<T>(D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.opQ, B.Qf, u[b], N, B.Q, 0, nullptr, B.ld, st);
+            gemm<T>(D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.opQ, B.Qf, u[b], N, B.Q, 0, nullptr, B.ld, st,
+                    B.nfpts, B.nfpts + B.nupts, sub);
             prof_end(c, st);
             // 4. Q = J^{-T} Q~
             prof_begin(c, K_GRADCORU, st);
@@ -634,6 +706,12 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
         gemm<T>(B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.opR, B.Uf, B.Q, (int64_t)NV * B.ld, r[b], 1, B.rcpdjac,
                 B.ld, st);
         prof_end(c, st);
+        if (c.prm.ref_h != 0.0) {
+            prof_begin(c, K_ENERGY_FIX, st);
+            energy_fix_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(B.nupts, NV, B.nelem, B.ld, (T*)r[b],
+                                                                            T(c.prm.ref_h));
+            prof_end(c, st);
+        }
     }
     return cudaGetLastError();
 }

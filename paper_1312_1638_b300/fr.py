@@ -40,7 +40,8 @@ class Params(C.Structure):
                 ("gamma", C.c_double), ("mu", C.c_double), ("prandtl", C.c_double),
                 ("ldg_beta", C.c_double), ("ldg_tau", C.c_double),
                 ("bc_rho", C.c_double), ("bc_v", C.c_double * 3), ("bc_p", C.c_double),
-                ("outflow_p", C.c_double), ("wall_cpTw", C.c_double), ("wall_v", C.c_double * 3)]
+                ("outflow_p", C.c_double), ("wall_cpTw", C.c_double), ("wall_v", C.c_double * 3),
+                ("ref_rho", C.c_double), ("ref_p", C.c_double)]
 
 
 class EBlock(C.Structure):
@@ -146,6 +147,8 @@ class Solver:
         p.wall_cpTw = params.get("wall_cpTw", 1.0)
         for i, v in enumerate(params.get("wall_v", (0.0, 0.0, 0.0))):
             p.wall_v[i] = v
+        p.ref_rho = params.get("ref_rho", 0.0)
+        p.ref_p = params.get("ref_p", 0.0)
         self.params = p
         self._keep = []
         blocks = (EBlock * len(mesh.blocks))()

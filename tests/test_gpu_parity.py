@@ -1,10 +1,20 @@
 """GPU parity: the CUDA right-hand side (through the C ABI) against the FP64
 oracle on the same seeded inputs, element by element.
 
-Tolerances: FP64 path rel-L2 <= 1e-12 per variable (both sides evaluate the
-same discretisation; only summation order and the fused operators
-M4 - M6 M0, M1 - M3 M2 differ).  FP32 path rel-L2 <= 1e-5, with the oracle
-evaluated on the same FP32-rounded input.
+Tolerances (derived from the arithmetic; the oracle is evaluated on the same
+input, FP32-rounded for the FP32 path):
+
+* componentwise: |R_gpu - R| <= tol * S with S = |J^-1| (|M3||D~| +
+  |M3||M2||F~| + |M1||F~|) the magnitude of the terms summed in the last
+  contraction (the forward-error scale of Eq. tdivflux / negdivconf);
+  tol = 1e-13 (about 900 FP64 ulps) and 2e-6 (about 34 FP32 ulps);
+* relative L2 per variable (max over variables): <= 1e-12 (FP64) and
+  <= 1e-5 (FP32) whenever the state is well conditioned,
+  kappa = ||S|| / ||R|| <= 200.  Low-Mach states have kappa ~ 1e3..1e4 and
+  only the componentwise bound applies there.
+
+FP32 runs use the perturbation form about the mean state (fr_params.ref_rho,
+ref_p), the form the library is meant to be run in.
 """
 import numpy as np
 import pytest
@@ -22,6 +32,28 @@ def torch():
     assert t.cuda.is_available(), "GPU test without a GPU"
     ensure_built()
     return t
+
+
+TOL_C = {"fp64": 1e-13, "fp32": 2e-6}
+TOL_L2 = {"fp64": 1e-12, "fp32": 1e-5}
+KAPPA_WELL = 200.0
+
+
+def check(G, R, S, prec):
+    for g, r, sc in zip(G, R, S):
+        err_c = float(np.max(np.abs(g - r) / np.maximum(sc, 1e-300)))
+        kappa = float(np.linalg.norm(sc) / np.linalg.norm(r))
+        rel = rel_l2_per_var(g, r)
+        assert err_c <= TOL_C[prec], (err_c, rel, kappa)
+        if kappa <= KAPPA_WELL:
+            assert rel <= TOL_L2[prec], (err_c, rel, kappa)
+
+
+def mean_ref(U, gamma=1.4):
+    """Mean density and pressure of a state (reference of the perturbation form)."""
+    rho = np.concatenate([u[:, 0].ravel() for u in U])
+    p = np.concatenate([((gamma - 1) * (u[:, -1] - 0.5 * (u[:, 1:-1] ** 2).sum(1) / u[:, 0])).ravel() for u in U])
+    return dict(ref_rho=float(rho.mean()), ref_p=float(p.mean()))
 
 
 def gpu_rhs(torch, s, U, inplace=False):
@@ -67,18 +99,17 @@ def _case_solver(fr, name, prec):
     return m, p, system, st, prm
 
 
+@pytest.mark.parametrize("form", ["plain", "perturbation"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_rhs_fp64_matches_oracle(torch, name):
+def test_rhs_fp64_matches_oracle(torch, name, form):
     from paper_1312_1638_b300 import fr
     m, p, system, st, prm = _case_solver(fr, name, "fp64")
     o = FRSystem(m, p, system, **prm)
     U = oracle_state(o, st)
-    R = o.rhs(U)
-    s = fr.Solver(m, p, system, "fp64", device=0, **prm)
-    G = gpu_rhs(torch, s, U)
-    for g, r in zip(G, R):
-        assert rel_l2_per_var(g, r) < 1e-12
-        assert np.abs(g - r).max() <= 1e-11 * np.abs(r).max()
+    R, S = o.rhs(U, scale=True)
+    extra = mean_ref(U) if form == "perturbation" else {}
+    s = fr.Solver(m, p, system, "fp64", device=0, **prm, **extra)
+    check(gpu_rhs(torch, s, U), R, S, "fp64")
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -87,15 +118,13 @@ def test_rhs_fp32_matches_oracle(torch, name):
     m, p, system, st, prm = _case_solver(fr, name, "fp32")
     o = FRSystem(m, p, system, **prm)
     U = [u.astype(np.float32).astype(np.float64) for u in oracle_state(o, st)]
-    R = o.rhs(U)
-    s = fr.Solver(m, p, system, "fp32", device=0, **prm)
-    G = gpu_rhs(torch, s, U)
-    for g, r in zip(G, R):
-        assert rel_l2_per_var(g, r) < 1e-5
+    R, S = o.rhs(U, scale=True)
+    s = fr.Solver(m, p, system, "fp32", device=0, **prm, **mean_ref(U))
+    check(gpu_rhs(torch, s, U), R, S, "fp32")
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_rhs_mixed_mesh_with_boundaries(torch, prec, tol):
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rhs_mixed_mesh_with_boundaries(torch, prec):
     from paper_1312_1638_b300 import fr
     m = _mixed_case()
     o = FRSystem(m, 3, "ns", **MIXED_PRM)
@@ -103,11 +132,9 @@ def test_rhs_mixed_mesh_with_boundaries(torch, prec, tol):
                                                        p0=1 / (1.4 * 0.04)))
     if prec == "fp32":
         U = [u.astype(np.float32).astype(np.float64) for u in U]
-    R = o.rhs(U)
-    s = fr.Solver(m, 3, "ns", prec, device=0, **MIXED_PRM)
-    G = gpu_rhs(torch, s, U)
-    for g, r in zip(G, R):
-        assert rel_l2_per_var(g, r) < tol
+    R, S = o.rhs(U, scale=True)
+    s = fr.Solver(m, 3, "ns", prec, device=0, **MIXED_PRM, **mean_ref(U))
+    check(gpu_rhs(torch, s, U), R, S, prec)
 
 
 def test_rhs_in_place_and_host_buffers(torch):
