@@ -209,8 +209,9 @@ fr_status fr_check_finite(fr_ctx* ctx, void* const* u, void* stream);
  * fr_profile_read synchronises on those events and returns, per kernel, the
  * number of launches and the total event-measured milliseconds since the
  * previous read, then clears them.  names receives nkernels NUL-terminated
- * names of at most 31 characters in rows of 32 bytes.  Arrays may be NULL;
- * *nkernels is always set.
+ * names of at most 31 characters in rows of 32 bytes.  *nkernels is always
+ * set; with all three arrays NULL the call only reports the count and keeps
+ * the records.
  */
 fr_status fr_profile_enable(fr_ctx* ctx, int enable);
 fr_status fr_profile_read(fr_ctx* ctx, int32_t* nkernels, char* names, int64_t* launches, double* ms);
