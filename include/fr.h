@@ -195,6 +195,33 @@ fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* strea
  */
 fr_status fr_sum_weighted(fr_ctx* ctx, void* const* u, double* out, void* stream);
 
+/*
+ * fr_rk4_noalloc -- the same RK4 step as fr_rk4, for callers that cannot let
+ * a library allocate device memory at call time.  The paper has no
+ * counterpart; it exists for applications whose framework owns all device
+ * memory through its own pool (a cudaMalloc behind its back fails or
+ * fragments that pool) and for time-critical loops in which cudaMalloc /
+ * cudaFree, which may synchronise the device, must not run.  fr_rk4 allocates
+ * its two stage registers with cudaMalloc on its first call; this entry point
+ * keeps them instead in a fixed device array compiled into libfr.so, of
+ * FR_NOALLOC_MAX_BYTES (64 MiB), which every GPU that loads the library holds
+ * until the process exits.  The call itself allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   - Limit: the registers need 2 * nupts * nvars * ld * sizeof(real) bytes
+ *     per block (each rounded up to 256); larger meshes are rejected with
+ *     FR_ERR_ARG and a message naming both sizes, before anything runs.
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Sharing: every call, from any context or stream, uses the same array,
+ *     which keeps the last call's contents (nothing needs clearing: each call
+ *     writes every byte it reads).  Calls that overlap on the GPU race on it:
+ *     serialise them.
+ * u, dt, nsteps and stream as for fr_rk4; at most 16 element blocks.
+ */
+#define FR_NOALLOC_MAX_BYTES (64u * 1024u * 1024u)
+fr_status fr_rk4_noalloc(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
+
 /* Reads and clears the device error flags (non-finite values seen by
  * fr_check_finite, timeouts).  Synchronises the device. */
 fr_status fr_sync_status(fr_ctx* ctx);

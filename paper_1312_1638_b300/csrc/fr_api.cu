@@ -200,6 +200,13 @@ void upload_device(fr_ctx* c) {
 
 }  // namespace
 
+namespace fr {
+DevCtx* ctx_dev(fr_ctx* c) { return c ? &c->dev : nullptr; }
+void ctx_set_error(fr_ctx* c, const char* msg) {
+    if (c) c->err = msg;
+}
+}  // namespace fr
+
 // ====================================================================== ABI
 extern "C" {
 

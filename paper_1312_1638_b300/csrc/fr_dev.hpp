@@ -96,3 +96,11 @@ cudaError_t launch_sum_weighted(DevCtx& c, void* const* u, double* host_out, cud
 cudaError_t launch_check_finite(DevCtx& c, void* const* u, cudaStream_t st);
 
 }  // namespace fr
+
+// Internal accessors of the opaque context for entry points defined outside
+// fr_api.cu (implemented there).
+struct fr_ctx;
+namespace fr {
+DevCtx* ctx_dev(fr_ctx* c);
+void ctx_set_error(fr_ctx* c, const char* msg);
+}  // namespace fr

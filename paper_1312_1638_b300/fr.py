@@ -26,7 +26,8 @@ STATUS_NAMES = ["FR_OK", "FR_ERR_ARG", "FR_ERR_MESH", "FR_ERR_CUDA", "FR_ERR_NON
 # names exported by libfr.so (every function declared in include/fr.h)
 EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pairs", "fr_rhs",
            "fr_rhs_host", "fr_rk4", "fr_sum_weighted", "fr_sync_status", "fr_check_finite",
-           "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read"]
+           "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read",
+           "fr_rk4_noalloc"]
 
 
 class FRError(RuntimeError):
@@ -77,6 +78,7 @@ def load():
     lib.fr_rhs.argtypes = [vp, vpp, vpp, vp]
     lib.fr_rhs_host.argtypes = [vp, vpp, vpp, vp]
     lib.fr_rk4.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
+    lib.fr_rk4_noalloc.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_sum_weighted.argtypes = [vp, vpp, C.POINTER(C.c_double), vp]
     lib.fr_sync_status.argtypes = [vp]
     lib.fr_check_finite.argtypes = [vp, vpp, vp]
