@@ -71,7 +71,12 @@ typedef enum {
 } fr_status;
 
 typedef enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 } fr_system;
-typedef enum { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1, FR_PREC_BF16X3 = 2 } fr_precision;
+/* FR_PREC_FP64: FP64 everywhere.  FR_PREC_FP32: FP32 everywhere (CUDA-core
+ * operator products).  FR_PREC_TF32X3 / FR_PREC_BF16X3: FP32 state and
+ * point-wise arithmetic; operator products on the tensor cores with both
+ * factors split in two (TF32: 11+11 bits, BF16: 8+8 bits) and three products
+ * accumulated in FP32. */
+typedef enum { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1, FR_PREC_BF16X3 = 2, FR_PREC_TF32X3 = 3 } fr_precision;
 typedef enum { FR_QUAD = 0, FR_TRI = 1, FR_HEX = 2 } fr_etype;
 /* boundary types (App. C): free-stream ("supersonic inflow") ghost, subsonic
  * outflow, no-slip isothermal wall */

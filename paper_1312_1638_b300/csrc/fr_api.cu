@@ -14,6 +14,7 @@
 #include "../../include/fr.h"
 #include "fr_dev.hpp"
 #include "fr_host.hpp"
+#include "fr_tc.hpp"
 
 struct fr_ctx {
     std::string err;
@@ -144,6 +145,14 @@ void upload_device(fr_ctx* c) {
         B.opM0 = upload_real(c, el.M0, fp64);
         B.opQ = upload_real(c, hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu), fp64);
         B.opR = upload_real(c, hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu), fp64);
+        if (c->prm.precision == FR_PREC_BF16X3 || c->prm.precision == FR_PREC_TF32X3) {
+            const int kind = c->prm.precision == FR_PREC_TF32X3 ? 0 : 1;
+            B.tcM0 = upload(c, fr::tc::pack_operator(kind, el.M0, (int)nf, (int)nu, 0));
+            B.tcQ = upload(c, fr::tc::pack_operator(kind, hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu),
+                                                    d * (int)nu, (int)nf, (int)nu));
+            B.tcR = upload(c, fr::tc::pack_operator(kind, hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu),
+                                                    (int)nu, (int)nf, (int)(d * nu)));
+        }
         if ((double)nf * V * ld >= 4294967296.0) throw Fail{FR_ERR_UNSUPPORTED, "flux-point array exceeds 2^32 entries"};
         D.blocks.push_back(B);
     }
@@ -231,8 +240,8 @@ fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx
     if (prm->ndims != 2 && prm->ndims != 3) return set_err(nullptr, FR_ERR_ARG, "ndims must be 2 or 3");
     if (mesh->ndims != prm->ndims) return set_err(nullptr, FR_ERR_ARG, "mesh and params disagree on ndims");
     if (prm->system != FR_EULER && prm->system != FR_NAVIER_STOKES) return set_err(nullptr, FR_ERR_ARG, "bad system");
-    if (prm->precision != FR_PREC_FP64 && prm->precision != FR_PREC_FP32)
-        return set_err(nullptr, FR_ERR_UNSUPPORTED, "precision not available in this build");
+    if (prm->precision < FR_PREC_FP64 || prm->precision > FR_PREC_TF32X3)
+        return set_err(nullptr, FR_ERR_ARG, "bad precision");
     if (mesh->nblocks < 1 || !mesh->blocks) return set_err(nullptr, FR_ERR_ARG, "no element blocks");
     if (mesh->nperiodic < 0 || (mesh->nperiodic > 0 && !mesh->periodic))
         return set_err(nullptr, FR_ERR_ARG, "bad periodic translations");

@@ -29,6 +29,9 @@ struct DevBlock {
     void* opM0 = nullptr;      // M0: nfpts x nupts
     void* opQ = nullptr;       // [M6 | M4 - M6 M0]: ndims*nupts x (nfpts + nupts)
     void* opR = nullptr;       // [M3 | M1 - M3 M2]: nupts x (nfpts + ndims*nupts)
+    void* tcM0 = nullptr;      // the same three operators packed for the tensor-core GEMM
+    void* tcQ = nullptr;       // (split-precision modes only)
+    void* tcR = nullptr;
     void* stage = nullptr;     // device staging for fr_rhs_host: [nupts][nvars][ld]
     void* rk_acc = nullptr;    // RK4 registers
     void* rk_tmp = nullptr;

@@ -11,6 +11,7 @@
 #include <cstdio>
 
 #include "fr_dev.hpp"
+#include "fr_tc.hpp"
 
 namespace fr {
 
@@ -103,6 +104,24 @@ static void gemm(int M, int K, int K1, const void* A, const void* B1, const void
     dim3 grid((unsigned)((N + TN - 1) / TN));
     gemm_kernel<T><<<grid, 256, 0, st>>>(M, K, K1, (const T*)A, (const T*)B1, (const T*)B2, N, (T*)C, epi,
                                          (const T*)rcp, ld, ks0, ks1, sub);
+}
+
+// Operator product dispatch: CUDA-core GEMM for FP64 / FP32, tensor-core
+// split-precision GEMM (fr_tc.cu) for TF32x3 / BF16x3.
+template <typename T>
+static cudaError_t op_gemm(DevCtx& c, const void* opA, const void* tcA, int M, int K, int K1, const void* B1,
+                    const void* B2, int64_t N, void* C, int epi, const void* rcp, int64_t ld, cudaStream_t st,
+                    int ks0, int ks1, Sub<T> sub) {
+    if (c.precision >= 2) {
+        tc::SubRef sr;
+        for (int a = 0; a < 5; ++a) sr.v[a] = (float)sub.v[a];
+        // state rows needing the reference subtracted form exactly one segment here
+        const int subseg = ks1 > ks0 ? (ks0 == 0 ? 1 : 2) : 0;
+        return tc::gemm(c.precision == 3 ? 0 : 1, M, K1, K - K1, tcA, (const float*)B1, (const float*)B2, N,
+                        (float*)C, epi, (const float*)rcp, ld, subseg, sr, c.flags, st);
+    }
+    gemm<T>(M, K, K1, opA, B1, B2, N, C, epi, rcp, ld, st, ks0, ks1, sub);
+    return cudaGetLastError();
 }
 
 // ============================================================ gas dynamics
@@ -603,6 +622,12 @@ static inline dim3 pw_grid(int64_t nelem, int npts) {
 }
 static inline unsigned lin_grid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+#define FR_TRY(call)                      \
+    do {                                  \
+        cudaError_t e_ = (call);          \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
 template <typename T, int D>
 static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
     constexpr int NV = D + 2;
@@ -614,8 +639,8 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
         prof_begin(c, K_DISU, st);
-        gemm<T>(B.nfpts, B.nupts, B.nupts, B.opM0, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0, nullptr, B.ld, st,
-                0, B.nupts, sub);
+        FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0, nullptr,
+                   B.ld, st, 0, B.nupts, sub));
         prof_end(c, st);
     }
     if (ns) {
@@ -641,8 +666,8 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
             int64_t N = (int64_t)NV * B.ld;
             // 3. Q~ = M6 C + (M4 - M6 M0) U  (tgradu, eq. tquptsm)
             prof_begin(c, K_TGRADU, st);
-            gemm<T>(D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.opQ, B.Qf, u[b], N, B.Q, 0, nullptr, B.ld, st,
-                    B.nfpts, B.nfpts + B.nupts, sub);
+            FR_TRY(op_gemm<T>(c, B.opQ, B.tcQ, D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.Qf, u[b], N, B.Q, 0, nullptr, B.ld,
+                       st, B.nfpts, B.nfpts + B.nupts, sub));
             prof_end(c, st);
             // 4. Q = J^{-T} Q~
             prof_begin(c, K_GRADCORU, st);
@@ -652,8 +677,8 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
             // 5. Q^(f) = M5 Q (block diagonal: M0 per component)
             for (int i = 0; i < D; ++i) {
                 prof_begin(c, K_GRADFPTS, st);
-                gemm<T>(B.nfpts, B.nupts, B.nupts, B.opM0, (const T*)B.Q + (int64_t)i * B.nupts * N, nullptr, N,
-                        (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st);
+                FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, (const T*)B.Q + (int64_t)i * B.nupts * N,
+                           nullptr, N, (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st, 0, 0, Sub<T>{}));
                 prof_end(c, st);
             }
         }
@@ -703,8 +728,8 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
         prof_begin(c, K_TDIVF, st);
-        gemm<T>(B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.opR, B.Uf, B.Q, (int64_t)NV * B.ld, r[b], 1, B.rcpdjac,
-                B.ld, st);
+        FR_TRY(op_gemm<T>(c, B.opR, B.tcR, B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.Uf, B.Q, (int64_t)NV * B.ld, r[b], 1,
+                   B.rcpdjac, B.ld, st, 0, 0, Sub<T>{}));
         prof_end(c, st);
         if (c.prm.ref_h != 0.0) {
             prof_begin(c, K_ENERGY_FIX, st);

@@ -1,0 +1,35 @@
+// Split-precision tensor-core operator GEMMs (tcgen05), see fr_tc.cu.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace fr {
+namespace tc {
+
+// reference state of the perturbation form, subtracted per variable from the
+// B rows that hold solution states
+struct SubRef {
+    float v[5];
+};
+
+// Pack an M x (K1 + K2) row-major FP64 operator into the shared-memory operand
+// layout of the kernel, split into hi / lo parts: K chunks of segment 1
+// (columns [0, K1)) then of segment 2 (columns [K1, K1 + K2)), each padded
+// with zero columns to whole chunks.  kind 0 = TF32, 1 = BF16.
+std::vector<uint8_t> pack_operator(int kind, const std::vector<double>& A, int M, int K1, int K2);
+
+// C[M x N] = A [B1; B2]: B1 holds K1 rows, B2 (may be NULL when K2 = 0) K2
+// rows, both with row stride N (a multiple of 128).  epi = 1 multiplies row
+// r, column c by -rcp[r][c % ld] (-1/J).  Rows of segment `subseg` (1 or 2;
+// 0 = none) have sub.v[c / ld] subtracted (perturbation form).  flags[1] is
+// raised if a wait gives up.  Host-side tensor-map encoding failures return
+// cudaErrorInvalidValue.
+cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
+                 float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
+                 cudaStream_t st);
+
+}  // namespace tc
+}  // namespace fr

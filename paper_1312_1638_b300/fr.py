@@ -18,7 +18,7 @@ LIBPATH = os.path.join(_HERE, "libfr.so")
 
 OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_OOM = range(8)
 EULER, NAVIER_STOKES = 0, 1
-FP64, FP32, BF16X3 = 0, 1, 2
+FP64, FP32, BF16X3, TF32X3 = 0, 1, 2, 3
 ETYPES = {"quad": 0, "tri": 1, "hex": 2}
 STATUS_NAMES = ["FR_OK", "FR_ERR_ARG", "FR_ERR_MESH", "FR_ERR_CUDA", "FR_ERR_NONFINITE",
                 "FR_ERR_TIMEOUT", "FR_ERR_UNSUPPORTED", "FR_ERR_OOM"]
@@ -131,7 +131,7 @@ class Solver:
         self.mesh = mesh
         self.ndims = mesh.ndims
         self.nvars = mesh.ndims + 2
-        self.precision = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}[precision]
+        self.precision = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "tf32x3": TF32X3}[precision]
         self.system = {"euler": EULER, "ns": NAVIER_STOKES}[system]
         self.device = device
         p = Params()
