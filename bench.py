@@ -46,8 +46,9 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=96, help="elements per box edge")
     ap.add_argument("--order", type=int, default=4)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 CUDA-core comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     return ap.parse_args()
@@ -305,38 +306,54 @@ def main():
     value = dof * stages * world / (ms / 1e3) / 1e9
     launches = sum(v[0] for v in prof.values())
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: the binding one of its HBM time and its
+    # arithmetic time (tensor cores for the split-precision GEMMs, CUDA cores otherwise)
     npairs = nelem * nf // 2
     srz = 8 if a.precision == "fp64" else 4
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    kname, (kl, kms) = top
-    kbytes, kflops = kernel_work(kname, nu, nf, V, D, nelem, npairs, srz)
-    avg_s = kms / kl / 1e3
-    if kflops:
-        if a.precision == "fp64":
-            roof = dict(bound="alu", achieved=kflops / avg_s / 1e12, peak=1.25, unit="TFLOP/s",
-                        peak_source="nominal FP64 rate of the B300")
+    bf16_peak = peaks.get("bf16_tflops", 1800.0)
+    arith = {  # precision -> (peak TFLOP/s, executed / algorithmic flops, unit name, source)
+        "tf32x3": (bf16_peak * 1.1 / 2.25, 3.0, "TF32 tensor",
+                   "measured BF16 dense x nominal TF32/BF16 ratio (1.1/2.25)"),
+        "bf16x3": (bf16_peak, 3.0, "BF16 tensor", "measured BF16 dense (cuBLAS burst)"),
+        "fp32": (fp32_peak, 1.0, "FP32 CUDA core", "148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
+        "fp64": (1.25, 1.0, "FP64", "nominal FP64 rate of the B300"),
+    }[a.precision]
+
+    def roof_of(name, launches, tms):
+        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz)
+        avg = tms / launches / 1e3
+        t_hbm = kb / (hbm_peak * 1e9) if kb else 0.0
+        t_alu = (kf * arith[1]) / (arith[0] * 1e12) if kf else 0.0
+        r = dict(kernel=name, avg_launch_ms=tms / launches, algorithmic_bytes_per_launch=kb,
+                 algorithmic_flops_per_launch=kf, hbm_frac=(kb / avg / 1e9) / hbm_peak if kb else None)
+        if t_alu > t_hbm:
+            bound = "tensor" if a.precision in ("tf32x3", "bf16x3") else "alu"
+            r.update(bound=bound, achieved=kf * arith[1] / avg / 1e12, peak=arith[0], unit="TFLOP/s",
+                     peak_source=arith[3], work_factor=arith[1],
+                     note="achieved counts executed tensor/ALU flops = algorithmic operator flops x work_factor "
+                          "(3 products per split-precision multiply)" if arith[1] != 1.0 else None)
         else:
-            roof = dict(bound="alu", achieved=kflops / avg_s / 1e12, peak=fp32_peak, unit="TFLOP/s",
-                        peak_source="148 SMs x 128 FP32 FMA lanes x 2 flop x max SM clock")
-    else:
-        roof = dict(bound="hbm", achieved=kbytes / avg_s / 1e9, peak=hbm_peak, unit="GB/s",
-                    peak_source=f"{peak_src} hbm_gbs")
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = kname
-    roof["algorithmic_bytes_per_launch"] = kbytes
-    roof["algorithmic_flops_per_launch"] = kflops
-    roof["avg_launch_ms"] = kms / kl
+            r.update(bound="hbm", achieved=kb / avg / 1e9, peak=hbm_peak, unit="GB/s",
+                     peak_source=f"{peak_src} hbm_gbs")
+        r["frac"] = r["achieved"] / r["peak"]
+        return r
+
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    roof = roof_of(top[0], *top[1])
     wk = f"hex{a.n}_p{a.order}_ns_{a.precision}"
-    roof["traffic"] = measured_traffic(kname, wk)
-    per_kernel = {k: dict(launches=v[0], ms=round(v[1], 3), share=round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4))
-                  for k, v in prof.items() if v[0]}
-    for k, d in per_kernel.items():
+    roof["traffic"] = measured_traffic(top[0], wk)
+    total_ms = sum(x[1] for x in prof.values())
+    per_kernel = {}
+    for k, v in prof.items():
+        if not v[0]:
+            continue
+        d = dict(launches=v[0], ms=round(v[1], 3), share=round(v[1] / max(total_ms, 1e-9), 4))
         b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz)
         if b:
             d["GB_s"] = round(b / (d["ms"] / d["launches"] / 1e3) / 1e9, 1)
         if f:
-            d["TFLOP_s"] = round(f / (d["ms"] / d["launches"] / 1e3) / 1e12, 2)
+            d["TFLOP_s_algorithmic"] = round(f / (d["ms"] / d["launches"] / 1e3) / 1e12, 2)
+        per_kernel[k] = d
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -355,33 +372,39 @@ def main():
                    note="one RHS per call: H2D of U, RHS, D2H of R, host-synchronous")
         del uh, rh
 
-    # plain FP64 GPU path on the same mesh (comparison leg)
-    fp64 = None
-    if not a.no_fp64 and a.precision != "fp64":
-        del u
-        s.close()
-        torch.cuda.empty_cache()
-        s64 = fr.Solver(mesh, a.order, "ns", "fp64", device=local, **PRM, **REF)
-        u64 = u_init.to(torch.float64)
-        r64 = torch.empty_like(u64)
-        s64.rhs([u64], [r64], stream)
+    # comparison legs on the same mesh and state: plain FP32 (CUDA-core operator
+    # products) and plain FP64, one RHS per step
+    def rhs_leg(prec, reps):
+        sl = fr.Solver(mesh, a.order, "ns", prec, device=local, **PRM, **REF)
+        dtp = torch.float64 if prec == "fp64" else torch.float32
+        ul = u_init.to(dtp)
+        rl = torch.empty_like(ul)
+        sl.rhs([ul], [rl], stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(2):
-            s64.rhs([u64], [r64], stream)
+        for _ in range(reps):
+            sl.rhs([ul], [rl], stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        t64 = e0.elapsed_time(e1) / 2
-        fp64 = dict(gdofs_per_rhs=dof / (t64 / 1e3) / 1e9, ms_per_rhs=t64)
-        s64.close()
+        t = e0.elapsed_time(e1) / reps
+        sl.close()
+        del ul, rl
+        torch.cuda.empty_cache()
+        return dict(gdofs_per_rhs=dof / (t / 1e3) / 1e9, ms_per_rhs=t, precision=prec)
+
+    s.close()
+    del u
+    torch.cuda.empty_cache()
+    fp32 = rhs_leg("fp32", 3) if (not a.no_fp32 and a.precision != "fp32") else None
+    fp64 = rhs_leg("fp64", 2) if (not a.no_fp64 and a.precision != "fp64") else None
 
     if rank != 0:
         return 0
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=a.steps, warmup=a.warmup,
         ms_per_step=ms / a.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="f32" if a.precision == "fp32" else ("f64" if a.precision == "fp64" else "bf16x3+f32"),
+        dtype={"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3+f32", "bf16x3": "bf16x3+f32"}[a.precision],
         data="synthetic",
         config=dict(workload=f"3D Navier-Stokes Taylor-Green (+seeded perturbation), periodic {a.n}^3 hex box, "
                              f"p={a.order}, {dof} DOF, precision {a.precision}",
@@ -389,7 +412,7 @@ def main():
                     l2="inputs larger than L2 (state alone is %.1f GB)" % (u_init.numel() * u_init.element_size() / 1e9),
                     parallelism=f"replicas x{world}", setup_s=round(t_setup, 1)),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
-        clocks=clk.summary(), per_kernel=per_kernel, fp64_gpu=fp64, finite=finite_ok,
+        clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, finite=finite_ok,
     )
     print(json.dumps(line))
     return 0

@@ -7,14 +7,17 @@ input, FP32-rounded for the FP32 path):
 * componentwise: |R_gpu - R| <= tol * S with S = |J^-1| (|M3||D~| +
   |M3||M2||F~| + |M1||F~|) the magnitude of the terms summed in the last
   contraction (the forward-error scale of Eq. tdivflux / negdivconf);
-  tol = 1e-13 (about 900 FP64 ulps) and 2e-6 (about 34 FP32 ulps);
-* relative L2 per variable (max over variables): <= 1e-12 (FP64) and
-  <= 1e-5 (FP32) whenever the state is well conditioned,
-  kappa = ||S|| / ||R|| <= 200.  Low-Mach states have kappa ~ 1e3..1e4 and
-  only the componentwise bound applies there.
+  tol = 1e-13 (FP64, about 900 ulps), 2e-6 (FP32, about 34 ulps), 4e-6
+  (TF32x3: each operator product carries the dropped lo*lo term and the
+  rounding of the lo parts, about 2^-21 relative) and 1e-4 (BF16x3, 2^-16);
+* relative L2 per variable (max over variables) on well-conditioned states
+  (kappa = ||S|| / ||R|| <= 200): <= 1e-12 (FP64), <= 1e-5 (FP32) and
+  <= 2e-5 (TF32x3, the split-precision bound).  Low-Mach states have kappa
+  ~ 1e3..1e4 and only the componentwise bound applies; BF16x3 has no
+  relative-L2 bound (8+8 bits cannot reach 2e-5 on any state with kappa > 2).
 
-FP32 runs use the perturbation form about the mean state (fr_params.ref_rho,
-ref_p), the form the library is meant to be run in.
+Single-precision runs use the perturbation form about the mean state
+(fr_params.ref_rho, ref_p), the form the library is meant to be run in.
 """
 import numpy as np
 import pytest
@@ -34,8 +37,8 @@ def torch():
     return t
 
 
-TOL_C = {"fp64": 1e-13, "fp32": 2e-6}
-TOL_L2 = {"fp64": 1e-12, "fp32": 1e-5}
+TOL_C = {"fp64": 1e-13, "fp32": 2e-6, "tf32x3": 4e-6, "bf16x3": 1e-4}
+TOL_L2 = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 2e-5, "bf16x3": None}
 KAPPA_WELL = 200.0
 
 
@@ -45,7 +48,7 @@ def check(G, R, S, prec):
         kappa = float(np.linalg.norm(sc) / np.linalg.norm(r))
         rel = rel_l2_per_var(g, r)
         assert err_c <= TOL_C[prec], (err_c, rel, kappa)
-        if kappa <= KAPPA_WELL:
+        if kappa <= KAPPA_WELL and TOL_L2[prec] is not None:
             assert rel <= TOL_L2[prec], (err_c, rel, kappa)
 
 
@@ -112,18 +115,20 @@ def test_rhs_fp64_matches_oracle(torch, name, form):
     check(gpu_rhs(torch, s, U), R, S, "fp64")
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_rhs_fp32_matches_oracle(torch, name):
+def test_rhs_single_precision_matches_oracle(torch, name, prec):
     from paper_1312_1638_b300 import fr
-    m, p, system, st, prm = _case_solver(fr, name, "fp32")
+    m, p, system, st, prm = _case_solver(fr, name, prec)
     o = FRSystem(m, p, system, **prm)
     U = [u.astype(np.float32).astype(np.float64) for u in oracle_state(o, st)]
     R, S = o.rhs(U, scale=True)
-    s = fr.Solver(m, p, system, "fp32", device=0, **prm, **mean_ref(U))
-    check(gpu_rhs(torch, s, U), R, S, "fp32")
+    s = fr.Solver(m, p, system, prec, device=0, **prm, **mean_ref(U))
+    check(gpu_rhs(torch, s, U), R, S, prec)
+    assert s.sync_status() == fr.OK                      # no bounded wait gave up
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_rhs_mixed_mesh_with_boundaries(torch, prec):
     from paper_1312_1638_b300 import fr
     m = _mixed_case()
