@@ -193,6 +193,29 @@ fr_status fr_rhs_host(fr_ctx* ctx, const void* const* u, void* const* r, void* s
 fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
 
 /*
+ * fr_adjoint_rhs -- out = (dR/du)^T lambda, the discrete adjoint of fr_rhs
+ * at state u (not in the paper; the transpose of the operator chain of
+ * Eq. negdivconf / App. A with the Rusanov flux of App. B and the ghost
+ * states of App. C).  Euler contexts only (FR_ERR_UNSUPPORTED otherwise).
+ * u, lambda, out: device buffers laid out like fr_rhs's; out may not alias
+ * u or lambda.  Uses context scratch allocated on the first adjoint call.
+ * Stream-ordered.
+ */
+fr_status fr_adjoint_rhs(fr_ctx* ctx, void* const* u, void* const* lambda, void* const* out, void* stream);
+
+/*
+ * fr_rk4_adjoint -- reverse sweep of `nsteps` classical RK4 steps of size dt
+ * from u0 (not in the paper): on entry lambda holds dK/du_N for the state
+ * u_N = RK4^nsteps(u0); on return it holds dK/du0.  Stage inputs are
+ * recomputed from checkpoints of the state stored every `every` steps
+ * (ceil(nsteps/every) checkpoints plus `every` states of the current block
+ * and 8 work states, allocated for the call and freed before returning).
+ * u0 is not modified.  Euler contexts only.  Synchronises `stream`.
+ */
+fr_status fr_rk4_adjoint(fr_ctx* ctx, void* const* u0, void* const* lambda, double dt, int nsteps, int every,
+                         void* stream);
+
+/*
  * fr_sum_weighted -- FP64 totals sum_e sum_rho w_rho J_rho u_{rho,alpha,n}
  * (solution-point quadrature of each variable: the conserved totals of
  * Eq. commpflux's conservation argument), written to host out[nvars].

@@ -1,0 +1,398 @@
+// Discrete adjoint of the Euler right-hand side and of classical RK4.
+//
+// Not in the paper.  The transpose of R = -J^-1 [M3 D~ + (M1 - M3 M2) F~]
+// (App. A) is applied by running the RHS steps backwards:
+//   mu  = -J^-1 lambda                           (adj_scale)
+//   g_D = M3^T mu,  g_F = (M1 - M3 M2)^T mu      (operator products)
+//   per pair: a = |n|_L g_D,L - |n|_R g_D,R,  a_uL = (dF/duL)^T a,
+//             a_uR = (dF/duR)^T a  with F the Rusanov flux (App. B);
+//   per boundary point the ghost state's dependence on u_L is included (App. C)
+//   out = M0^T a_uf + (df/du)^T adj(J)^T g_F     (point-wise, accumulated)
+// The local transposed Jacobians are written out analytically from the
+// Euler flux (Eq. eulerflux, idealgas), in plain (not perturbation) variables.
+// The RK4 adjoint recomputes stage inputs from checkpoints.
+#include <cmath>
+#include <vector>
+
+#include "../../include/fr.h"
+#include "fr_dev.hpp"
+
+namespace fr {
+
+template <typename T, int D>
+struct EulerAdj {
+    static constexpr int NV = D + 2;
+
+    // a += (d f_j,alpha / d u)^T G[j][alpha]
+    __device__ static __forceinline__ void flux_vjp(const T* u, const T G[D][NV], T gamma, T* a) {
+        const T gm1 = gamma - T(1), rho = u[0], rinv = T(1) / rho;
+        T v[D], v2 = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { v[i] = u[1 + i] * rinv; v2 += v[i] * v[i]; }
+        const T p = gm1 * (u[D + 1] - T(0.5) * rho * v2);
+        const T dp_drho = gm1 * T(0.5) * v2;
+        T S = T(0), H = T(0), Gvv = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            S += G[j][1 + j];
+            H += G[j][D + 1] * v[j];
+#pragma unroll
+            for (int i = 0; i < D; ++i) Gvv += G[j][1 + i] * v[i] * v[j];
+        }
+        const T EpR = (u[D + 1] + p) * rinv;
+        a[0] += -Gvv + dp_drho * (S + H) - EpR * H;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            T acc = G[k][0] + G[k][D + 1] * EpR - gm1 * v[k] * (S + H);
+#pragma unroll
+            for (int j = 0; j < D; ++j) acc += (G[j][1 + k] + G[k][1 + j]) * v[j];
+            a[1 + k] += acc;
+        }
+        a[D + 1] += gm1 * S + gamma * H;
+    }
+
+    __device__ static __forceinline__ void prim(const T* u, T gm1, T& rho, T* v, T& p) {
+        rho = u[0];
+        T rinv = T(1) / rho, v2 = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { v[i] = u[1 + i] * rinv; v2 += v[i] * v[i]; }
+        p = gm1 * (u[D + 1] - T(0.5) * rho * v2);
+    }
+
+    __device__ static __forceinline__ void normal_flux(const T* u, const T* n, T gm1, T* fn) {
+        T rho, v[D], p;
+        prim(u, gm1, rho, v, p);
+        T vn = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) vn += n[i] * v[i];
+        fn[0] = rho * vn;
+#pragma unroll
+        for (int i = 0; i < D; ++i) fn[1 + i] = u[1 + i] * vn + p * n[i];
+        fn[D + 1] = (u[D + 1] + p) * vn;
+    }
+
+    // (dF/duL)^T a and (dF/duR)^T a for the Rusanov flux (App. B)
+    __device__ static __forceinline__ void rusanov_vjp(const T* uL, const T* uR, const T* n, T gamma, const T* a,
+                                                       T* aL, T* aR) {
+        const T gm1 = gamma - T(1);
+        T rL, vL[D], pL, rR, vR[D], pR;
+        prim(uL, gm1, rL, vL, pL);
+        prim(uR, gm1, rR, vR, pR);
+        T q = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) q += n[i] * (vL[i] + vR[i]);
+        const T cbar = sqrt(gamma * (pL + pR) / (rL + rR));
+        const T s = cbar + T(0.5) * fabs(q);
+        const T sgn = q >= T(0) ? T(1) : T(-1);
+        T adu = T(0);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) adu += a[k] * (uL[k] - uR[k]);
+        // half of the normal-flux VJP on each side: G_j,alpha = n_j a_alpha / 2
+        T G[D][NV];
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) G[j][k] = T(0.5) * n[j] * a[k];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) { aL[k] = T(0.5) * s * a[k]; aR[k] = -T(0.5) * s * a[k]; }
+        flux_vjp(uL, G, gamma, aL);
+        flux_vjp(uR, G, gamma, aR);
+        // d s / d u_X through cbar and |q|, times (a . (uL - uR)) / 2
+        const T sum_r = rL + rR, sum_p = pL + pR;
+        const T cfac = gamma / (T(2) * cbar);
+        const T h = T(0.5) * adu;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const T* v = side == 0 ? vL : vR;
+            const T rho = side == 0 ? rL : rR;
+            T* out = side == 0 ? aL : aR;
+            T v2 = T(0), vn = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) { v2 += v[i] * v[i]; vn += n[i] * v[i]; }
+            // dp/drho = gm1 |v|^2 / 2, dp/dm_k = -gm1 v_k, dp/dE = gm1
+            out[0] += h * (cfac * (gm1 * T(0.5) * v2 / sum_r - sum_p / (sum_r * sum_r)) + T(0.5) * sgn * (-vn / rho));
+#pragma unroll
+            for (int k = 0; k < D; ++k) out[1 + k] += h * (cfac * (-gm1 * v[k]) / sum_r + T(0.5) * sgn * n[k] / rho);
+            out[D + 1] += h * cfac * gm1 / sum_r;
+        }
+    }
+
+    // inviscid ghost state (App. C), plain variables, and the transpose of
+    // its Jacobian applied to b (added to c)
+    __device__ static __forceinline__ void ghost(int bctype, const T* uL, const DevParams& P, T* g) {
+        const T gamma = T(P.gamma), gm1 = gamma - T(1);
+        if (bctype == 0) {
+            T rho = T(P.bc_rho), ke = T(0);
+            g[0] = rho;
+#pragma unroll
+            for (int i = 0; i < D; ++i) { g[1 + i] = rho * T(P.bc_v[i]); ke += T(P.bc_v[i]) * T(P.bc_v[i]); }
+            g[D + 1] = T(P.bc_p) / gm1 + T(0.5) * rho * ke;
+        } else if (bctype == 1) {
+            T ke = T(0);
+            g[0] = uL[0];
+#pragma unroll
+            for (int i = 0; i < D; ++i) { g[1 + i] = uL[1 + i]; ke += uL[1 + i] * uL[1 + i]; }
+            g[D + 1] = T(P.outflow_p) / gm1 + T(0.5) * ke / uL[0];
+        } else {
+            const T rho = uL[0], rinv = T(1) / rho;
+            T k1 = T(0);
+            g[0] = rho;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                T w = T(2) * T(P.wall_v[i]) - uL[1 + i] * rinv;
+                g[1 + i] = rho * w;
+                k1 += w * w;
+            }
+            g[D + 1] = rho * (T(P.wall_cpTw) / gamma + T(0.5) * k1);
+        }
+    }
+
+    __device__ static __forceinline__ void ghost_vjp(int bctype, const T* uL, const DevParams& P, const T* b, T* c) {
+        if (bctype == 0) return;
+        const T rho = uL[0], rinv = T(1) / rho;
+        T v[D], v2 = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { v[i] = uL[1 + i] * rinv; v2 += v[i] * v[i]; }
+        if (bctype == 1) {
+            c[0] += b[0] - T(0.5) * v2 * b[D + 1];
+#pragma unroll
+            for (int k = 0; k < D; ++k) c[1 + k] += b[1 + k] + v[k] * b[D + 1];
+            return;
+        }
+        T w[D], w2 = T(0), wv = T(0), bm = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            w[i] = T(2) * T(P.wall_v[i]) - v[i];
+            w2 += w[i] * w[i];
+            wv += w[i] * v[i];
+            bm += T(2) * T(P.wall_v[i]) * b[1 + i];
+        }
+        c[0] += b[0] + bm + (T(P.wall_cpTw) / T(P.gamma) + T(0.5) * w2 + wv) * b[D + 1];
+#pragma unroll
+        for (int k = 0; k < D; ++k) c[1 + k] += -b[1 + k] - w[k] * b[D + 1];
+    }
+};
+
+// mu = -lambda / J
+template <typename T>
+__global__ void adj_scale_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, const T* __restrict__ lam,
+                                 const T* __restrict__ rcp, T* __restrict__ mu) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    T r = rcp[(int64_t)s * ld + n];
+    for (int a = 0; a < nvars; ++a) {
+        int64_t i = ((int64_t)s * nvars + a) * ld + n;
+        mu[i] = -lam[i] * r;
+    }
+}
+
+// pairs: a = |n|_L g_D,L - |n|_R g_D,R; write (dF/duL)^T a, (dF/duR)^T a in place of g_D
+template <typename T, int D>
+__global__ void adj_pair_kernel(int64_t npairs, const uint32_t* __restrict__ offL, const uint32_t* __restrict__ offR,
+                                const T* __restrict__ ufL, const T* __restrict__ ufR, T* gL, T* gR, int64_t ldL,
+                                int64_t ldR, const T* __restrict__ nrm, const T* __restrict__ magL,
+                                const T* __restrict__ magR, T gamma) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    int64_t oL = offL[k], oR = offR[k];
+    T uL[NV], uR[NV], a[NV], n[D], aL[NV], aR[NV];
+    const T mL = magL[k], mR = magR[k];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        uL[q] = ufL[oL + q * ldL];
+        uR[q] = ufR[oR + q * ldR];
+        a[q] = mL * gL[oL + q * ldL] - mR * gR[oR + q * ldR];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) n[i] = nrm[i * npairs + k];
+    EulerAdj<T, D>::rusanov_vjp(uL, uR, n, gamma, a, aL, aR);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        gL[oL + q * ldL] = aL[q];
+        gR[oR + q * ldR] = aR[q];
+    }
+}
+
+template <typename T, int D>
+__global__ void adj_bc_kernel(int64_t nb, int bctype, const uint32_t* __restrict__ off, const T* __restrict__ uf,
+                              T* g, int64_t ld, const T* __restrict__ nrm, const T* __restrict__ mag, DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    int64_t o = off[k];
+    T uL[NV], gs[NV], a[NV], n[D], aL[NV], aR[NV];
+    const T m = mag[k];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        uL[q] = uf[o + q * ld];
+        a[q] = m * g[o + q * ld];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) n[i] = nrm[i * nb + k];
+    EulerAdj<T, D>::ghost(bctype, uL, P, gs);
+    EulerAdj<T, D>::rusanov_vjp(uL, gs, n, T(P.gamma), a, aL, aR);
+    EulerAdj<T, D>::ghost_vjp(bctype, uL, P, aR, aL);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) g[o + q * ld] = aL[q];
+}
+
+// out += (df/du)^T adj(J)^T g_F at solution points
+template <typename T, int D>
+__global__ void adj_flux_kernel(int nupts, int64_t nelem, int64_t ld, const T* __restrict__ U,
+                                const T* __restrict__ gF, const T* __restrict__ smat, T* out, T gamma) {
+    constexpr int NV = D + 2;
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    T u[NV], G[D][NV], adj[D][D], a[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        u[q] = U[((int64_t)s * NV + q) * ld + n];
+        a[q] = T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) adj[i][j] = smat[((int64_t)(i * D + j) * nupts + s) * ld + n];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc += adj[i][j] * gF[((int64_t)(i * nupts + s) * NV + q) * ld + n];
+            G[j][q] = acc;
+        }
+    EulerAdj<T, D>::flux_vjp(u, G, gamma, a);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[((int64_t)s * NV + q) * ld + n] += a[q];
+}
+
+template <typename T>
+__global__ void lincomb_kernel(int64_t n, T* __restrict__ out, T a, const T* __restrict__ x, T b,
+                               const T* __restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = a * x[i] + (y ? b * y[i] : T(0));
+}
+
+static inline unsigned lgrid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T, int D>
+static cudaError_t adjoint_impl(DevCtx& c, void* const* u, void* const* lam, void* const* out, cudaStream_t st) {
+    const T gamma = T(c.prm.gamma);
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        dim3 g((unsigned)((B.nelem + 127) / 128), (unsigned)B.nupts);
+        adj_scale_kernel<T><<<g, 128, 0, st>>>(B.nupts, B.nvars, B.nelem, B.ld, (const T*)lam[b],
+                                               (const T*)B.rcpdjac, (T*)B.adj_mu);
+        cudaError_t e;
+        if ((e = adjoint_gemm(c, 0, (int)b, u[b], B.adj_uf, st)) != cudaSuccess) return e;     // u^(f) = M0 u
+        if ((e = adjoint_gemm(c, 1, (int)b, B.adj_mu, B.Uf, st)) != cudaSuccess) return e;     // g_D
+        if ((e = adjoint_gemm(c, 2, (int)b, B.adj_mu, B.Q, st)) != cudaSuccess) return e;      // g_F
+    }
+    for (auto& g : c.pgroups) {
+        if (!g.n) continue;
+        DevBlock &L = c.blocks[g.bL], &R = c.blocks[g.bR];
+        adj_pair_kernel<T, D><<<lgrid(g.n, 128), 128, 0, st>>>(g.n, g.offL, g.offR, (const T*)L.adj_uf,
+                                                               (const T*)R.adj_uf, (T*)L.Uf, (T*)R.Uf, L.ld, R.ld,
+                                                               (const T*)g.nrm, (const T*)g.magL, (const T*)g.magR,
+                                                               gamma);
+    }
+    for (auto& g : c.bgroups) {
+        if (!g.n) continue;
+        DevBlock& B = c.blocks[g.b];
+        adj_bc_kernel<T, D><<<lgrid(g.n, 128), 128, 0, st>>>(g.n, g.bctype, g.off, (const T*)B.adj_uf, (T*)B.Uf,
+                                                             B.ld, (const T*)g.nrm, (const T*)g.mag, c.prm);
+    }
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        cudaError_t e;
+        if ((e = adjoint_gemm(c, 3, (int)b, B.Uf, out[b], st)) != cudaSuccess) return e;       // M0^T a_uf
+        dim3 g((unsigned)((B.nelem + 127) / 128), (unsigned)B.nupts);
+        adj_flux_kernel<T, D><<<g, 128, 0, st>>>(B.nupts, B.nelem, B.ld, (const T*)u[b], (const T*)B.Q,
+                                                 (const T*)B.smat, (T*)out[b], gamma);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_rhs(DevCtx& c, void* const* u, void* const* lam, void* const* out, cudaStream_t st) {
+    if (c.precision == 0) return c.ndims == 2 ? adjoint_impl<double, 2>(c, u, lam, out, st)
+                                              : adjoint_impl<double, 3>(c, u, lam, out, st);
+    return c.ndims == 2 ? adjoint_impl<float, 2>(c, u, lam, out, st) : adjoint_impl<float, 3>(c, u, lam, out, st);
+}
+
+// ---------------------------------------------------------------- RK4 adjoint
+template <typename T>
+static cudaError_t rk4_adjoint_impl(DevCtx& c, void* const* u0, void* const* lam, double dt, int nsteps, int every,
+                                    const std::vector<std::vector<void*>>& ck, const std::vector<std::vector<void*>>& blk,
+                                    const std::vector<std::vector<void*>>& tmp, cudaStream_t st) {
+    const size_t nb = c.blocks.size();
+    auto nval = [&](size_t b) { return (int64_t)c.blocks[b].nupts * c.blocks[b].nvars * c.blocks[b].ld; };
+    auto copy = [&](const std::vector<void*>& dst, void* const* src) {
+        for (size_t b = 0; b < nb; ++b)
+            cudaMemcpyAsync(dst[b], src[b], nval(b) * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    };
+    auto comb = [&](const std::vector<void*>& out, double a, void* const* x, double bb, void* const* y) {
+        for (size_t b = 0; b < nb; ++b)
+            lincomb_kernel<T><<<lgrid(nval(b), 256), 256, 0, st>>>(nval(b), (T*)out[b], T(a), (const T*)x[b], T(bb),
+                                                                   y ? (const T*)y[b] : nullptr);
+    };
+    // tmp slots: 0..3 stage inputs y1..y4, 4 k, 5 t, 6 w, 7 sum
+    const auto &y1 = tmp[0], &y2 = tmp[1], &y3 = tmp[2], &y4 = tmp[3], &k = tmp[4], &t = tmp[5], &w = tmp[6],
+               &sum = tmp[7];
+    cudaError_t e;
+    // forward sweep: checkpoint i holds u_{i * every}
+    copy(ck[0], u0);
+    for (size_t i = 1; i < ck.size(); ++i) {
+        copy(ck[i], ck[i - 1].data());
+        if ((e = launch_rk4(c, (void* const*)ck[i].data(), dt, every, st)) != cudaSuccess) return e;
+    }
+    // backward sweep, one checkpoint block at a time
+    for (int blk0 = ((nsteps - 1) / every) * every; blk0 >= 0; blk0 -= every) {
+        const int len = std::min(every, nsteps - blk0);
+        copy(blk[0], ck[blk0 / every].data());
+        for (int j = 1; j < len; ++j) {
+            copy(blk[j], blk[j - 1].data());
+            if ((e = launch_rk4(c, (void* const*)blk[j].data(), dt, 1, st)) != cudaSuccess) return e;
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            void* const* un = blk[j].data();
+            // stage inputs
+            copy(y1, un);
+            if ((e = launch_rhs(c, y1.data(), k.data(), st)) != cudaSuccess) return e;
+            comb(y2, 1.0, un, 0.5 * dt, k.data());
+            if ((e = launch_rhs(c, y2.data(), k.data(), st)) != cudaSuccess) return e;
+            comb(y3, 1.0, un, 0.5 * dt, k.data());
+            if ((e = launch_rhs(c, y3.data(), k.data(), st)) != cudaSuccess) return e;
+            comb(y4, 1.0, un, dt, k.data());
+            // adjoint of the step
+            comb(t, dt / 6.0, lam, 0.0, nullptr);
+            if ((e = launch_adjoint_rhs(c, y4.data(), t.data(), w.data(), st)) != cudaSuccess) return e;
+            copy(sum, w.data());
+            comb(t, dt / 3.0, lam, dt, w.data());
+            if ((e = launch_adjoint_rhs(c, y3.data(), t.data(), w.data(), st)) != cudaSuccess) return e;
+            comb(sum, 1.0, sum.data(), 1.0, w.data());
+            comb(t, dt / 3.0, lam, 0.5 * dt, w.data());
+            if ((e = launch_adjoint_rhs(c, y2.data(), t.data(), w.data(), st)) != cudaSuccess) return e;
+            comb(sum, 1.0, sum.data(), 1.0, w.data());
+            comb(t, dt / 6.0, lam, 0.5 * dt, w.data());
+            if ((e = launch_adjoint_rhs(c, y1.data(), t.data(), w.data(), st)) != cudaSuccess) return e;
+            comb(sum, 1.0, sum.data(), 1.0, w.data());
+            std::vector<void*> lv(lam, lam + nb);
+            comb(lv, 1.0, lam, 1.0, sum.data());
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk4_adjoint(DevCtx& c, void* const* u0, void* const* lam, double dt, int nsteps, int every,
+                               const std::vector<std::vector<void*>>& ck, const std::vector<std::vector<void*>>& blk,
+                               const std::vector<std::vector<void*>>& tmp, cudaStream_t st) {
+    return c.precision == 0 ? rk4_adjoint_impl<double>(c, u0, lam, dt, nsteps, every, ck, blk, tmp, st)
+                            : rk4_adjoint_impl<float>(c, u0, lam, dt, nsteps, every, ck, blk, tmp, st);
+}
+
+}  // namespace fr

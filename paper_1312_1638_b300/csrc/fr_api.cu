@@ -145,6 +145,26 @@ void upload_device(fr_ctx* c) {
         B.opM0 = upload_real(c, el.M0, fp64);
         B.opQ = upload_real(c, hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu), fp64);
         B.opR = upload_real(c, hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu), fp64);
+        if (c->prm.system == FR_EULER) {
+            // transposed operators of the discrete adjoint
+            auto transpose = [](const std::vector<double>& A, int r, int cl) {
+                std::vector<double> t((size_t)r * cl);
+                for (int i = 0; i < r; ++i)
+                    for (int j = 0; j < cl; ++j) t[(size_t)j * r + i] = A[(size_t)i * cl + j];
+                return t;
+            };
+            auto M3T = transpose(el.M3, (int)nu, (int)nf), M132T = transpose(el.M132, (int)nu, d * (int)nu),
+                 M0T = transpose(el.M0, (int)nf, (int)nu);
+            B.opM3T = upload_real(c, M3T, fp64);
+            B.opM132T = upload_real(c, M132T, fp64);
+            B.opM0T = upload_real(c, M0T, fp64);
+            if (c->prm.precision == FR_PREC_BF16X3 || c->prm.precision == FR_PREC_TF32X3) {
+                const int kind = c->prm.precision == FR_PREC_TF32X3 ? 0 : 1;
+                B.tcM3T = upload(c, fr::tc::pack_operator(kind, M3T, (int)nf, (int)nu, 0));
+                B.tcM132T = upload(c, fr::tc::pack_operator(kind, M132T, d * (int)nu, (int)nu, 0));
+                B.tcM0T = upload(c, fr::tc::pack_operator(kind, M0T, (int)nu, (int)nf, 0));
+            }
+        }
         if (c->prm.precision == FR_PREC_BF16X3 || c->prm.precision == FR_PREC_TF32X3) {
             const int kind = c->prm.precision == FR_PREC_TF32X3 ? 0 : 1;
             B.tcM0 = upload(c, fr::tc::pack_operator(kind, el.M0, (int)nf, (int)nu, 0));
@@ -463,6 +483,74 @@ fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* strea
         return set_err(ctx, f.st, f.msg);
     }
     cudaError_t e = fr::launch_rk4(ctx->dev, u, dt, nsteps, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+static fr_status adjoint_ready(fr_ctx* ctx) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if (ctx->prm.system != FR_EULER) return set_err(ctx, FR_ERR_UNSUPPORTED, "the adjoint covers the Euler equations");
+    size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    try {
+        for (auto& B : ctx->dev.blocks) {
+            if (!B.adj_mu) B.adj_mu = dalloc(ctx, (size_t)B.nupts * B.nvars * B.ld * rs);
+            if (!B.adj_uf) B.adj_uf = dalloc(ctx, (size_t)B.nfpts * B.nvars * B.ld * rs);
+            if (!B.rk_acc) B.rk_acc = dalloc(ctx, (size_t)B.nupts * B.nvars * B.ld * rs);
+            if (!B.rk_tmp) B.rk_tmp = dalloc(ctx, (size_t)B.nupts * B.nvars * B.ld * rs);
+        }
+    } catch (const Fail& f) {
+        return set_err(ctx, f.st, f.msg);
+    }
+    return FR_OK;
+}
+
+fr_status fr_adjoint_rhs(fr_ctx* ctx, void* const* u, void* const* lambda, void* const* out, void* stream) {
+    fr_status s = adjoint_ready(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, u) || !ptrs_ok(ctx, lambda) || !ptrs_ok(ctx, out))
+        return set_err(ctx, FR_ERR_ARG, "NULL state pointer");
+    for (size_t b = 0; b < ctx->hblocks.size(); ++b)
+        if (out[b] == u[b] || out[b] == lambda[b]) return set_err(ctx, FR_ERR_ARG, "out may not alias u or lambda");
+    cudaError_t e = fr::launch_adjoint_rhs(ctx->dev, u, lambda, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+fr_status fr_rk4_adjoint(fr_ctx* ctx, void* const* u0, void* const* lambda, double dt, int nsteps, int every,
+                         void* stream) {
+    fr_status s = adjoint_ready(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, u0) || !ptrs_ok(ctx, lambda) || nsteps < 1 || every < 1)
+        return set_err(ctx, FR_ERR_ARG, "bad argument");
+    const size_t nb = ctx->dev.blocks.size();
+    const size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const int nck = (nsteps + every - 1) / every, nblk = std::min(every, nsteps);
+    std::vector<void*> mine;
+    auto slots = [&](int n) {
+        std::vector<std::vector<void*>> v((size_t)n, std::vector<void*>(nb));
+        for (int i = 0; i < n; ++i)
+            for (size_t b = 0; b < nb; ++b) {
+                const fr::DevBlock& B = ctx->dev.blocks[b];
+                void* p = nullptr;
+                if (cudaMalloc(&p, (size_t)B.nupts * B.nvars * B.ld * rs) != cudaSuccess)
+                    throw Fail{FR_ERR_OOM, "checkpoint allocation failed"};
+                mine.push_back(p);
+                v[(size_t)i][b] = p;
+            }
+        return v;
+    };
+    cudaError_t e = cudaSuccess;
+    try {
+        auto ck = slots(nck), blk = slots(nblk), tmp = slots(8);
+        e = fr::launch_rk4_adjoint(ctx->dev, u0, lambda, dt, nsteps, every, ck, blk, tmp, (cudaStream_t)stream);
+        cudaError_t e2 = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e == cudaSuccess) e = e2;
+    } catch (const Fail& f) {
+        for (void* p : mine) cudaFree(p);
+        return set_err(ctx, f.st, f.msg);
+    }
+    for (void* p : mine) cudaFree(p);
     if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
     return FR_OK;
 }

@@ -32,6 +32,15 @@ struct DevBlock {
     void* tcM0 = nullptr;      // the same three operators packed for the tensor-core GEMM
     void* tcQ = nullptr;       // (split-precision modes only)
     void* tcR = nullptr;
+    // adjoint (Euler): transposed operators and scratch
+    void* opM3T = nullptr;     // M3^T: nfpts x nupts
+    void* opM132T = nullptr;   // (M1 - M3 M2)^T: ndims*nupts x nupts
+    void* opM0T = nullptr;     // M0^T: nupts x nfpts
+    void* tcM3T = nullptr;
+    void* tcM132T = nullptr;
+    void* tcM0T = nullptr;
+    void* adj_mu = nullptr;    // [nupts][nvars][ld]
+    void* adj_uf = nullptr;    // [nfpts][nvars][ld]
     void* stage = nullptr;     // device staging for fr_rhs_host: [nupts][nvars][ld]
     void* rk_acc = nullptr;    // RK4 registers
     void* rk_tmp = nullptr;
@@ -92,6 +101,15 @@ void prof_free(DevCtx& c);
 
 // RHS r = R(u) for every block (precision and dimension dispatched inside).
 cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t st);
+// out = (dR/du)^T lam (Euler); scratch must be allocated (adj_mu, adj_uf)
+cudaError_t launch_adjoint_rhs(DevCtx& c, void* const* u, void* const* lam, void* const* out, cudaStream_t st);
+// operator product used by the adjoint: which = 0: M0 u (plain), 1: M3^T x, 2: (M1-M3M2)^T x, 3: M0^T x
+cudaError_t adjoint_gemm(DevCtx& c, int which, int b, const void* B, void* C, cudaStream_t st);
+// RK4 adjoint: lam (dK/du_N on entry) becomes dK/du_0; ck: ceil(nsteps/every)
+// state slots, blk: `every` slots, tmp: 8 slots (each [block] -> device buffer)
+cudaError_t launch_rk4_adjoint(DevCtx& c, void* const* u0, void* const* lam, double dt, int nsteps, int every,
+                               const std::vector<std::vector<void*>>& ck, const std::vector<std::vector<void*>>& blk,
+                               const std::vector<std::vector<void*>>& tmp, cudaStream_t st);
 // classical RK4, nsteps steps of dt, in place on u
 cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st);
 // FP64 weighted totals per variable

@@ -741,6 +741,23 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
     return cudaGetLastError();
 }
 
+cudaError_t adjoint_gemm(DevCtx& c, int which, int b, const void* B, void* C, cudaStream_t st) {
+    DevBlock& Bk = c.blocks[b];
+    const int D = c.ndims, nu = Bk.nupts, nf = Bk.nfpts;
+    const int64_t N = (int64_t)c.nvars * Bk.ld;
+    const void *op = nullptr, *tcop = nullptr;
+    int M = 0, K = 0;
+    switch (which) {
+        case 0: op = Bk.opM0; tcop = Bk.tcM0; M = nf; K = nu; break;
+        case 1: op = Bk.opM3T; tcop = Bk.tcM3T; M = nf; K = nu; break;
+        case 2: op = Bk.opM132T; tcop = Bk.tcM132T; M = D * nu; K = nu; break;
+        default: op = Bk.opM0T; tcop = Bk.tcM0T; M = nu; K = nf; break;
+    }
+    if (c.precision == 0)
+        return op_gemm<double>(c, op, tcop, M, K, K, B, nullptr, N, C, 0, nullptr, Bk.ld, st, 0, 0, Sub<double>{});
+    return op_gemm<float>(c, op, tcop, M, K, K, B, nullptr, N, C, 0, nullptr, Bk.ld, st, 0, 0, Sub<float>{});
+}
+
 cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
     if (c.precision == 0) return c.ndims == 2 ? rhs_impl<double, 2>(c, u, r, st) : rhs_impl<double, 3>(c, u, r, st);
     return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st) : rhs_impl<float, 3>(c, u, r, st);

@@ -27,7 +27,7 @@ STATUS_NAMES = ["FR_OK", "FR_ERR_ARG", "FR_ERR_MESH", "FR_ERR_CUDA", "FR_ERR_NON
 EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pairs", "fr_rhs",
            "fr_rhs_host", "fr_rk4", "fr_sum_weighted", "fr_sync_status", "fr_check_finite",
            "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read",
-           "fr_rk4_noalloc"]
+           "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint"]
 
 
 class FRError(RuntimeError):
@@ -79,6 +79,8 @@ def load():
     lib.fr_rhs_host.argtypes = [vp, vpp, vpp, vp]
     lib.fr_rk4.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_rk4_noalloc.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
+    lib.fr_adjoint_rhs.argtypes = [vp, vpp, vpp, vpp, vp]
+    lib.fr_rk4_adjoint.argtypes = [vp, vpp, vpp, C.c_double, C.c_int, C.c_int, vp]
     lib.fr_sum_weighted.argtypes = [vp, vpp, C.POINTER(C.c_double), vp]
     lib.fr_sync_status.argtypes = [vp]
     lib.fr_check_finite.argtypes = [vp, vpp, vp]
@@ -253,6 +255,15 @@ class Solver:
 
     def rk4(self, u, dt, nsteps, stream=None):
         self._check(self.lib.fr_rk4(self.ctx, _ptrs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+
+    def adjoint_rhs(self, u, lam, out, stream=None):
+        """out = (dR/du)^T lam (Euler)."""
+        self._check(self.lib.fr_adjoint_rhs(self.ctx, _ptrs(u), _ptrs(lam), _ptrs(out), _stream_ptr(stream)))
+
+    def rk4_adjoint(self, u0, lam, dt, nsteps, every=10, stream=None):
+        """lam: dK/du_N on entry, dK/du0 on return (Euler)."""
+        self._check(self.lib.fr_rk4_adjoint(self.ctx, _ptrs(u0), _ptrs(lam), C.c_double(dt), nsteps, every,
+                                            _stream_ptr(stream)))
 
     def sum_weighted(self, u, stream=None):
         out = np.zeros(self.nvars)
