@@ -187,10 +187,18 @@ fr_status fr_rhs_host(fr_ctx* ctx, const void* const* u, void* const* r, void* s
 
 /*
  * fr_rk4 -- advance u in place by `nsteps` classical RK4 steps of size dt
- * (end of Sec. 2; Sec. 5.1).  Uses two library-owned state registers.
+ * (end of Sec. 2; Sec. 5.1).  Uses two library-owned state registers,
+ * allocated on the first call.  Unless disabled with
+ * fr_set_option(ctx, "graphs", 0) or while kernel timing is enabled, one step
+ * is captured once as a CUDA graph (on a private stream) and replayed nsteps
+ * times on `stream`; the graph is re-captured when u's pointers or dt change.
  * Stream-ordered; returns after enqueueing.
  */
 fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
+
+/* Context options: "graphs" (default 1) enables the RK4-step CUDA graph of
+ * fr_rk4.  FR_ERR_ARG for an unknown name. */
+fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value);
 
 /*
  * fr_adjoint_rhs -- out = (dR/du)^T lambda, the discrete adjoint of fr_rhs

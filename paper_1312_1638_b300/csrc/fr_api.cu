@@ -26,6 +26,12 @@ struct fr_ctx {
     std::vector<fr::HostBnd> bnds;       // boundary flux points
     fr::DevCtx dev;
     std::vector<void*> allocs;
+    // CUDA graph of one RK4 step, replayed by fr_rk4 (keyed by state pointers and dt)
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t rk_exec = nullptr;
+    std::vector<void*> rk_ptrs;
+    double rk_dt = 0.0;
 };
 
 static thread_local std::string g_setup_err;
@@ -249,6 +255,8 @@ void fr_destroy(fr_ctx* ctx) {
         cudaSetDevice(ctx->dev.device);
         cudaDeviceSynchronize();
         fr::prof_free(ctx->dev);
+        if (ctx->rk_exec) cudaGraphExecDestroy(ctx->rk_exec);
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
         for (void* p : ctx->allocs) cudaFree(p);
     }
     delete ctx;
@@ -329,6 +337,7 @@ fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx
         if (device >= 0) {
             c->dev.device = device;
             upload_device(c.get());
+            if (prm->precision == FR_PREC_BF16X3 || prm->precision == FR_PREC_TF32X3) CK(fr::tc::prepare());
             // the host pair list is only kept for inspection of small meshes
             if (c->pairs.size() > (size_t)4000000) { c->pairs.clear(); c->pairs.shrink_to_fit(); }
         } else {
@@ -482,9 +491,49 @@ fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* strea
     } catch (const Fail& f) {
         return set_err(ctx, f.st, f.msg);
     }
-    cudaError_t e = fr::launch_rk4(ctx->dev, u, dt, nsteps, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (ctx->use_graphs && !ctx->dev.prof && nsteps > 0) {
+        // one RK4 step captured on a private stream, replayed on the caller's stream
+        std::vector<void*> key(u, u + ctx->dev.blocks.size());
+        if (!ctx->rk_exec || key != ctx->rk_ptrs || dt != ctx->rk_dt) {
+            if (ctx->rk_exec) {
+                cudaGraphExecDestroy(ctx->rk_exec);
+                ctx->rk_exec = nullptr;
+            }
+            if (!ctx->cap_stream && (e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+                return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t el = fr::launch_rk4(ctx->dev, u, dt, 1, ctx->cap_stream);
+                e = cudaStreamEndCapture(ctx->cap_stream, &g);
+                if (e == cudaSuccess) e = el;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->rk_exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ctx->rk_exec = nullptr;
+                return set_err(ctx, FR_ERR_CUDA, std::string("RK4 graph capture: ") + cudaGetErrorString(e));
+            }
+            ctx->rk_ptrs = key;
+            ctx->rk_dt = dt;
+        }
+        for (int i = 0; i < nsteps && e == cudaSuccess; ++i) e = cudaGraphLaunch(ctx->rk_exec, st);
+    } else {
+        e = fr::launch_rk4(ctx->dev, u, dt, nsteps, st);
+    }
     if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
     return FR_OK;
+}
+
+fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value) {
+    if (!ctx || !name) return FR_ERR_ARG;
+    if (std::string(name) == "graphs") {
+        ctx->use_graphs = value != 0;
+        return FR_OK;
+    }
+    return set_err(ctx, FR_ERR_ARG, std::string("unknown option ") + name);
 }
 
 static fr_status adjoint_ready(fr_ctx* ctx) {

@@ -485,15 +485,33 @@ static bool make_map(CUtensorMap* m, const float* base, int64_t N, int rows, int
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+static int g_nsm = 0;
+static bool g_attr[2] = {false, false};
+
+cudaError_t prepare() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (g_nsm <= 0) g_nsm = 148;
+    if ((e = cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024)) !=
+        cudaSuccess)
+        return e;
+    g_attr[0] = g_attr[1] = true;
+    return encode_fn() ? cudaSuccess : cudaErrorSymbolNotFound;
+}
+
 template <int KIND>
 static cudaError_t launch(const TcArgs& a, const CUtensorMap& m1, const CUtensorMap& m2, int nsm, cudaStream_t st) {
     const Layout L = make_layout(KIND, a.M);
-    static int attr_bytes = 0;
-    if (attr_bytes < L.smem) {
+    if (!g_attr[KIND]) {
         cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              225 * 1024);
         if (e != cudaSuccess) return e;
-        attr_bytes = 225 * 1024;
+        g_attr[KIND] = true;
     }
     const int grid = std::min(a.ntiles, nsm);
     tc_gemm_kernel<KIND><<<grid, NTHREADS, L.smem, st>>>(a, m1, m2);
@@ -503,13 +521,11 @@ static cudaError_t launch(const TcArgs& a, const CUtensorMap& m1, const CUtensor
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
                  cudaStream_t st) {
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm <= 0) nsm = 148;
+    if (!g_nsm) {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
     }
+    const int nsm = g_nsm;
     if (N % BN != 0) return cudaErrorInvalidValue;
     const int esz = kind == 0 ? 4 : 2, kce = ROWB / esz;
     CUtensorMap m1, m2;

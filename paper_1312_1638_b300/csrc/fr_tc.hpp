@@ -21,6 +21,10 @@ struct SubRef {
 // with zero columns to whole chunks.  kind 0 = TF32, 1 = BF16.
 std::vector<uint8_t> pack_operator(int kind, const std::vector<double>& A, int M, int K1, int K2);
 
+// One-time launch set-up (shared-memory limits, SM count) on the current
+// device; called at context set-up so that later launches can be captured.
+cudaError_t prepare();
+
 // C[M x N] = A [B1; B2]: B1 holds K1 rows, B2 (may be NULL when K2 = 0) K2
 // rows, both with row stride N (a multiple of 128).  epi = 1 multiplies row
 // r, column c by -rcp[r][c % ld] (-1/J).  Rows of segment `subseg` (1 or 2;

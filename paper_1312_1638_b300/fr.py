@@ -27,7 +27,7 @@ STATUS_NAMES = ["FR_OK", "FR_ERR_ARG", "FR_ERR_MESH", "FR_ERR_CUDA", "FR_ERR_NON
 EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pairs", "fr_rhs",
            "fr_rhs_host", "fr_rk4", "fr_sum_weighted", "fr_sync_status", "fr_check_finite",
            "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read",
-           "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint"]
+           "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint", "fr_set_option"]
 
 
 class FRError(RuntimeError):
@@ -80,6 +80,7 @@ def load():
     lib.fr_rk4.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_rk4_noalloc.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_adjoint_rhs.argtypes = [vp, vpp, vpp, vpp, vp]
+    lib.fr_set_option.argtypes = [vp, C.c_char_p, C.c_int64]
     lib.fr_rk4_adjoint.argtypes = [vp, vpp, vpp, C.c_double, C.c_int, C.c_int, vp]
     lib.fr_sum_weighted.argtypes = [vp, vpp, C.POINTER(C.c_double), vp]
     lib.fr_sync_status.argtypes = [vp]
@@ -273,6 +274,9 @@ class Solver:
 
     def check_finite(self, u, stream=None):
         self._check(self.lib.fr_check_finite(self.ctx, _ptrs(u), _stream_ptr(stream)))
+
+    def set_option(self, name, value):
+        self._check(self.lib.fr_set_option(self.ctx, name.encode(), int(value)))
 
     def profile_enable(self, on=True):
         self._check(self.lib.fr_profile_enable(self.ctx, 1 if on else 0))
