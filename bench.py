@@ -188,7 +188,7 @@ def kernel_work(name, nu, nf, V, D, nelem, npairs, s):
     if name == "comm_flux":
         return npairs * ((4 * V + 2 * D * V + D + 2) * s + 8), 0.0
     if name == "rk_stage":
-        return 5 * nu * V * s * E, 0.0
+        return 17 * nu * V * s * E / 4, 0.0       # stages read/write 4, 5, 5, 3 values per entry
     return None, None
 
 

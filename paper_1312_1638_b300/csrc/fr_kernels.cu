@@ -512,23 +512,32 @@ __global__ void energy_fix_kernel(int nupts, int nvars, int64_t nelem, int64_t l
 }
 
 // ============================================================ RK4 combine
-// acc += a_acc * k; tmp = u + a_tmp * k, where k lives in tmp (in place)
+// RK4 stage combine per solution point, all variables at once, with the
+// energy-split correction k_E += h_ref k_rho applied to the stage RHS first
+// (k lives in tmp):
+//   mode 0 (first stage):  acc = u + a_acc k;  tmp = u + a_tmp k
+//   mode 1:                acc += a_acc k;     tmp = u + a_tmp k
+//   mode 2 (last stage):   u = acc + a_acc k
 template <typename T>
-__global__ void rk_stage_kernel(int64_t n, T* __restrict__ acc, T* __restrict__ tmp, const T* __restrict__ u,
-                                T a_acc, T a_tmp) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T k = tmp[i];
-    acc[i] += a_acc * k;
-    tmp[i] = u[i] + a_tmp * k;
-}
-
-template <typename T>
-__global__ void rk_final_kernel(int64_t n, const T* __restrict__ acc, const T* __restrict__ k, T* __restrict__ u,
-                                T a) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    u[i] = acc[i] + a * k[i];
+__global__ void rk_point_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, T* __restrict__ acc,
+                                T* __restrict__ tmp, T* __restrict__ u, T a_acc, T a_tmp, T href, int mode) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    const int64_t base = (int64_t)s * nvars * ld + n;
+    T k[5];
+    for (int a = 0; a < nvars; ++a) k[a] = tmp[base + a * ld];
+    k[nvars - 1] += href * k[0];
+    for (int a = 0; a < nvars; ++a) {
+        const int64_t i = base + a * ld;
+        if (mode == 2) {
+            u[i] = acc[i] + a_acc * k[a];
+        } else {
+            const T ui = u[i];
+            acc[i] = (mode == 0 ? ui : acc[i]) + a_acc * k[a];
+            tmp[i] = ui + a_tmp * k[a];
+        }
+    }
 }
 
 // ============================================================ diagnostics
@@ -629,7 +638,7 @@ static inline unsigned lin_grid(int64_t n, int bs) { return (unsigned)((n + bs -
     } while (0)
 
 template <typename T, int D>
-static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
+static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st, bool energy_fix = true) {
     constexpr int NV = D + 2;
     const bool ns = c.system == 1;
     Sub<T> sub{};
@@ -731,7 +740,7 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
         FR_TRY(op_gemm<T>(c, B.opR, B.tcR, B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.Uf, B.Q, (int64_t)NV * B.ld, r[b], 1,
                    B.rcpdjac, B.ld, st, 0, 0, Sub<T>{}));
         prof_end(c, st);
-        if (c.prm.ref_h != 0.0) {
+        if (energy_fix && c.prm.ref_h != 0.0) {
             prof_begin(c, K_ENERGY_FIX, st);
             energy_fix_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(B.nupts, NV, B.nelem, B.ld, (T*)r[b],
                                                                             T(c.prm.ref_h));
@@ -763,32 +772,30 @@ cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t s
     return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st) : rhs_impl<float, 3>(c, u, r, st);
 }
 
+// RHS without the final energy-split correction (the RK4 stage kernels apply it)
+static cudaError_t launch_rhs_nofix(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
+    if (c.precision == 0)
+        return c.ndims == 2 ? rhs_impl<double, 2>(c, u, r, st, false) : rhs_impl<double, 3>(c, u, r, st, false);
+    return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st, false) : rhs_impl<float, 3>(c, u, r, st, false);
+}
+
 template <typename T>
 static cudaError_t rk4_impl(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {
     std::vector<void*> tmp(c.blocks.size());
     for (size_t b = 0; b < c.blocks.size(); ++b) tmp[b] = c.blocks[b].rk_tmp;
     for (int step = 0; step < nsteps; ++step) {
-        for (size_t b = 0; b < c.blocks.size(); ++b) {
-            DevBlock& B = c.blocks[b];
-            size_t bytes = (size_t)B.nupts * B.nvars * B.ld * sizeof(T);
-            cudaMemcpyAsync(B.rk_acc, u[b], bytes, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(B.rk_tmp, u[b], bytes, cudaMemcpyDeviceToDevice, st);
-        }
         const double a_acc[4] = {dt / 6, dt / 3, dt / 3, dt / 6};
         const double a_tmp[3] = {dt / 2, dt / 2, dt};
         for (int s = 0; s < 4; ++s) {
-            cudaError_t e = launch_rhs(c, tmp.data(), tmp.data(), st);
+            // stage 1 reads u directly; later stages read the stage state in tmp
+            cudaError_t e = launch_rhs_nofix(c, s == 0 ? u : tmp.data(), tmp.data(), st);
             if (e != cudaSuccess) return e;
             for (size_t b = 0; b < c.blocks.size(); ++b) {
                 DevBlock& B = c.blocks[b];
-                int64_t n = (int64_t)B.nupts * B.nvars * B.ld;
                 prof_begin(c, K_RK_STAGE, st);
-                if (s < 3)
-                    rk_stage_kernel<T><<<lin_grid(n, 256), 256, 0, st>>>(n, (T*)B.rk_acc, (T*)B.rk_tmp,
-                                                                         (const T*)u[b], T(a_acc[s]), T(a_tmp[s]));
-                else
-                    rk_final_kernel<T><<<lin_grid(n, 256), 256, 0, st>>>(n, (const T*)B.rk_acc, (const T*)B.rk_tmp,
-                                                                         (T*)u[b], T(a_acc[3]));
+                rk_point_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                    B.nupts, B.nvars, B.nelem, B.ld, (T*)B.rk_acc, (T*)B.rk_tmp, (T*)u[b], T(a_acc[s]),
+                    T(s < 3 ? a_tmp[s] : 0.0), T(c.prm.ref_h), s == 0 ? 0 : (s == 3 ? 2 : 1));
                 prof_end(c, st);
             }
         }
