@@ -9,24 +9,35 @@
 // The operator is split once on the host and stored in the shared-memory
 // operand layout; the state is split on the fly.
 //
-// Persistent, warp-specialised kernel (one CTA per SM, 10 warps).  The MMA
-// M dimension is 128 state columns (one per TMEM lane) and the N dimension is
-// the operator's rows (NR, padded to 16; split in two instructions when above
-// 256), so each thread of the epilogue owns one state column and every
-// operator row of it, and each warp store writes 32 consecutive columns.
+// Persistent, warp-specialised kernel (one CTA per SM).  The MMA M dimension
+// is 128 state columns (one per TMEM lane) and the N dimension is a block of
+// at most 256 operator rows (padded to 16), so each thread of the epilogue
+// owns one state column and every row of the block, and each warp store
+// writes 32 consecutive columns.  Operators of more than 256 rows are cut into
+// equal row blocks; a work item is (column tile, row block), and the row
+// blocks of one column tile run on neighbouring CTAs at the same time, so the
+// second read of the state tile is served by L2.  Operators of at most 128
+// rows take two 128-column subtiles per work item, so that each operator
+// chunk feeds two MMAs.
 //   warp 0      producer: per K chunk, one bulk copy of the packed operator
-//               and one 2D TMA load of the FP32 state tile [chunk rows x 128
-//               columns]; both complete on the stage's "full" mbarrier;
+//               and one 2D TMA load of the FP32 state tile [chunk rows x
+//               128 or 256 columns]; both complete on the stage's "full"
+//               mbarrier;
 //   warp 1      MMA issuer (one thread) and owner of tensor memory: three
-//               tcgen05.mma per 32-byte K step (state_hi op_hi, state_lo
-//               op_hi, state_hi op_lo), committed to the stage's "empty"
-//               barrier and, after the last chunk of a column tile, to that
-//               tile's accumulator barrier;
+//               tcgen05.mma per 32-byte K step and subtile (state_hi op_hi,
+//               state_lo op_hi, state_hi op_lo), committed to the stage's
+//               "empty" barrier and, after the last chunk of a work item, to
+//               its accumulator barrier;
 //   warps 2-5   converters: read the FP32 tile, subtract the perturbation
 //               reference where the rows are solution states, split into
 //               hi / lo and write the K-major core-matrix operand layout;
-//   warps 6-9   epilogue: tcgen05.ld of the accumulators (one TMEM lane
-//               quadrant per warp), optional -1/J scaling, coalesced stores.
+//   warps 6-    epilogue: tcgen05.ld of the accumulators (TMEM lane quadrant
+//               = warp % 4; 12 warps interleave 16-row groups when the tile
+//               has one subtile, 4 warps when it has two), optional -1/J
+//               scaling, coalesced stores.  Direct global stores from four
+//               warps could not drain a 160-row accumulator as fast as the
+//               MMAs fill the next one; twelve warps keep more stores in
+//               flight.
 // Shared-memory stages form a ring; accumulators are double-buffered in
 // tensor memory whenever two fit.  Every mbarrier wait gives up after about
 // two seconds of clock cycles and raises the context's timeout flag.
@@ -45,13 +56,12 @@
 namespace fr {
 namespace tc {
 
-constexpr int BN = 128;                        // state columns per tile (MMA M, one per TMEM lane)
+constexpr int BN = 128;                        // state columns per subtile (MMA M, one per TMEM lane)
 constexpr int KSTEPS = 2;                      // 32-byte MMA K steps per chunk
 constexpr int ROWB = 32 * KSTEPS;              // bytes of K per operand row per chunk
 constexpr int SPART = BN * ROWB;               // one part (hi or lo) of the state operand per chunk
-constexpr int NTHREADS = 320;
 constexpr int MAX_NST = 6;
-constexpr int MAX_NR = 384;                    // operator rows per launch (TMEM: 384 FP32 columns)
+constexpr int MAX_RB = 256;                    // operator rows per block (MMA N limit)
 
 // Byte offset of (row r, K byte kb) inside one operand part: core matrices of
 // 8 rows x 16 bytes, 2*KSTEPS of them along K, then the next 8-row group.
@@ -59,33 +69,45 @@ __host__ __device__ constexpr int core_off(int r, int kb) {
     return ((r >> 3) * (2 * KSTEPS) + (kb >> 4)) * 128 + (r & 7) * 16 + (kb & 15);
 }
 
-// operator rows of one launch, padded so that one or two MMA instructions
-// (N a multiple of 16, at most 256 each) cover them
-__host__ __device__ constexpr int pad_rows(int nr) {
-    return nr <= 256 ? (nr + 15) / 16 * 16 : (nr + 31) / 32 * 32;
+// Row blocks of an M-row operator: nrb equal blocks of rbr rows (a multiple
+// of 16, at most MAX_RB); the last block may hold fewer real rows.
+struct RowBlocks {
+    int nrb, rbr;
+};
+__host__ __device__ inline RowBlocks row_blocks(int M) {
+    RowBlocks r;
+    const int n0 = (M + MAX_RB - 1) / MAX_RB;
+    r.rbr = ((M + n0 - 1) / n0 + 15) / 16 * 16;
+    r.nrb = (M + r.rbr - 1) / r.rbr;            // no empty trailing block
+    return r;
 }
 
+// 128-column subtiles per work item: two when the row block is at most 128
+// rows, so that both accumulators still fit twice in tensor memory
+__host__ __device__ constexpr int subtiles_for(int rbr) { return rbr <= 128 ? 2 : 1; }
+// epilogue warp groups (4 warps each, one per TMEM lane quadrant)
+__host__ __device__ constexpr int epi_groups(int nt) { return nt == 2 ? 1 : 3; }
+__host__ __device__ constexpr int nthreads_for(int nt) { return 192 + 128 * epi_groups(nt); }
+
 struct Layout {
-    int nrp, nsplit, nh;          // padded rows, MMA instructions per K step, N per instruction
+    int nrp;                      // rows per block (MMA N)
     int opart, a_bytes, stg_bytes, off_stg, off_bhi, off_blo, stage, nst, tbuf, smem;
 };
 
-__host__ __device__ inline Layout make_layout(int kind, int nr) {
+__host__ __device__ inline Layout make_layout(int kind, int rbr, int nt) {
     Layout L;
-    L.nrp = pad_rows(nr);
-    L.nsplit = L.nrp <= 256 ? 1 : 2;
-    L.nh = L.nrp / L.nsplit;
+    L.nrp = rbr;
     L.opart = L.nrp * ROWB;
     L.a_bytes = 2 * L.opart;
     const int kce = ROWB / (kind == 0 ? 4 : 2);
-    L.stg_bytes = kce * BN * 4;
+    L.stg_bytes = kce * BN * nt * 4;
     L.off_stg = L.a_bytes;
-    L.off_bhi = L.off_stg + L.stg_bytes;
-    L.off_blo = L.off_bhi + SPART;
-    L.stage = L.off_blo + SPART;
+    L.off_bhi = L.off_stg + L.stg_bytes;              // subtile t at + t * SPART
+    L.off_blo = L.off_bhi + nt * SPART;
+    L.stage = L.off_blo + nt * SPART;
     L.nst = (220 * 1024) / L.stage;
     if (L.nst > MAX_NST) L.nst = MAX_NST;
-    L.tbuf = 2 * L.nrp <= 512 ? 2 : 1;
+    L.tbuf = 2 * nt * L.nrp <= 512 ? 2 : 1;
     L.smem = L.nst * L.stage + 1024;
     return L;
 }
@@ -161,24 +183,30 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uin
 }
 
 struct TcArgs {
-    int M;              // operator rows handled by this launch
-    int row0;           // first operator row of this launch
+    int M;              // operator rows
+    int nrb, rbr;       // row blocks and rows per block
     int nch1, nch2;     // K chunks of segment 1 (B1) and 2 (B2)
     int subseg;         // segment whose rows get the reference subtracted (0: none)
-    const uint8_t* Apack;   // this launch's packed operator: nch chunks of Layout::a_bytes
+    const uint8_t* Apack;   // packed operator: nrb blocks of nch chunks of Layout::a_bytes
     int64_t N, ld;
     float* C;
     int epi;
     const float* rcp;
-    SubRef sub;
+    float sub0, sub1, sub2, sub3, sub4;
     int* flags;
     long long limit;
-    int ntiles;
+    int ntiles;         // column tiles (NT * 128 columns each)
+    int nwork;          // ntiles * nrb
 };
 
-template <int KIND>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__device__ __forceinline__ float sub_of(const TcArgs& a, int64_t v) {
+    return v == 0 ? a.sub0 : v == 1 ? a.sub1 : v == 2 ? a.sub2 : v == 3 ? a.sub3 : a.sub4;
+}
+
+template <int KIND, int NT>
+__global__ void __launch_bounds__(nthreads_for(NT), 1)
 tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2) {
+    constexpr int EG = epi_groups(NT);
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[MAX_NST], bar_conv[MAX_NST], bar_empty[MAX_NST];
     __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
@@ -186,7 +214,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nch = a.nch1 + a.nch2;
-    const Layout L = make_layout(KIND, a.M);
+    const Layout L = make_layout(KIND, a.rbr, NT);
     constexpr int ESZ = KIND == 0 ? 4 : 2;
     constexpr int KCE = ROWB / ESZ;
 
@@ -203,7 +231,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
         }
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_tfull[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar_tempty[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_tempty[b])), "r"(128 * EG));
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -217,8 +245,10 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
         // ---------------------------------------------------------- producer
         if (lane == 0) {
             int it = 0;
-            for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-                const int col0 = tile * BN;
+            for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x) {
+                const int tile = w / a.nrb, rb = w - tile * a.nrb;
+                const int col0 = tile * NT * BN;
+                const uint8_t* ablk = a.Apack + (size_t)rb * nch * L.a_bytes;
                 for (int c = 0; c < nch; ++c, ++it) {
                     const int s = it % L.nst, k = it / L.nst;
                     if (k > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (k - 1) & 1, a.limit)) { ok = false; break; }
@@ -227,7 +257,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
                                  "r"((uint32_t)(L.a_bytes + L.stg_bytes))
                                  : "memory");
-                    const uint8_t* src = a.Apack + (size_t)c * L.a_bytes;
+                    const uint8_t* src = ablk + (size_t)c * L.a_bytes;
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                             smem_u32(st)),
@@ -248,30 +278,30 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t id = instr_desc<KIND>(L.nh);
-            int it = 0, tc = 0;
-            for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++tc) {
-                const int b = tc % L.tbuf;
-                if (!mbar_wait(smem_u32(&bar_tempty[b]), ((tc / L.tbuf) & 1) ^ 1, a.limit)) { ok = false; break; }
+            const uint32_t id = instr_desc<KIND>(L.nrp);
+            int it = 0, wc = 0;
+            for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x, ++wc) {
+                const int b = wc % L.tbuf;
+                if (!mbar_wait(smem_u32(&bar_tempty[b]), ((wc / L.tbuf) & 1) ^ 1, a.limit)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t dbase = tmem + (uint32_t)(b * L.nrp);
+                const uint32_t dbase = tmem + (uint32_t)(b * NT * L.nrp);
                 for (int c = 0; c < nch; ++c, ++it) {
                     const int s = it % L.nst, k = it / L.nst;
                     if (!mbar_wait(smem_u32(&bar_conv[s]), k & 1, a.limit)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t st = smem_u32(smem + s * L.stage);
                     const uint32_t o_hi = st, o_lo = st + L.opart;            // operator parts (MMA B)
-                    const uint32_t s_hi = st + L.off_bhi, s_lo = st + L.off_blo;  // state parts (MMA A)
 #pragma unroll
-                    for (int j = 0; j < KSTEPS; ++j) {
-                        const uint32_t o = 2 * j * 128;
-                        const uint32_t first = (c == 0 && j == 0) ? 0u : 1u;
-                        for (int h = 0; h < L.nsplit; ++h) {
-                            const uint32_t d = dbase + (uint32_t)(h * L.nh);
-                            const uint32_t ro = (uint32_t)(h * L.nh / 8) * (2 * KSTEPS * 128);   // row-group offset
-                            mma<KIND>(d, make_desc(s_hi + o), make_desc(o_hi + ro + o), id, first);
-                            mma<KIND>(d, make_desc(s_lo + o), make_desc(o_hi + ro + o), id, 1u);
-                            mma<KIND>(d, make_desc(s_hi + o), make_desc(o_lo + ro + o), id, 1u);
+                    for (int t = 0; t < NT; ++t) {
+                        const uint32_t s_hi = st + L.off_bhi + t * SPART, s_lo = st + L.off_blo + t * SPART;
+                        const uint32_t d = dbase + (uint32_t)(t * L.nrp);
+#pragma unroll
+                        for (int j = 0; j < KSTEPS; ++j) {
+                            const uint32_t o = 2 * j * 128;
+                            const uint32_t first = (c == 0 && j == 0) ? 0u : 1u;
+                            mma<KIND>(d, make_desc(s_hi + o), make_desc(o_hi + o), id, first);
+                            mma<KIND>(d, make_desc(s_lo + o), make_desc(o_hi + o), id, 1u);
+                            mma<KIND>(d, make_desc(s_hi + o), make_desc(o_lo + o), id, 1u);
                         }
                     }
                     asm volatile(
@@ -288,49 +318,60 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
         }
     } else if (warp < 6) {
         // ---------------------------------------------------------- converters
-        const int ct = tid - 64;                       // state column within the tile = MMA A row
+        const int ct = tid - 64;                       // state column within a subtile = MMA A row
+        constexpr int ncols = NT * BN;
         int it = 0;
-        for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-            const int64_t gc = (int64_t)tile * BN + ct;
-            const float subv = gc < a.N ? a.sub.v[gc / a.ld] : 0.f;
+        for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x) {
+            const int tile = w / a.nrb;
+            float subv[NT];
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const int64_t gc = (int64_t)tile * ncols + t * BN + ct;
+                subv[t] = gc < a.N ? sub_of(a, gc / a.ld) : 0.f;
+            }
             for (int c = 0; c < nch; ++c, ++it) {
                 const int s = it % L.nst, k = it / L.nst;
                 if (!mbar_wait(smem_u32(&bar_full[s]), k & 1, a.limit)) { ok = false; break; }
                 uint8_t* st = smem + s * L.stage;
                 const float* stg = (const float*)(st + L.off_stg);
                 const bool seg1 = c < a.nch1;
-                const float sv = (a.subseg == (seg1 ? 1 : 2)) ? subv : 0.f;
+                const bool dosub = a.subseg == (seg1 ? 1 : 2);
 #pragma unroll
-                for (int g = 0; g < ROWB / 16; ++g) {
-                    constexpr int PER = 16 / ESZ;
-                    float x[PER];
+                for (int t = 0; t < NT; ++t) {
+                    const float sv = dosub ? subv[t] : 0.f;
+                    const int cc = t * BN + ct;
 #pragma unroll
-                    for (int q = 0; q < PER; ++q) x[q] = stg[(g * PER + q) * BN + ct] - sv;
-                    uint4 h, l;
-                    if (KIND == 0) {
-                        uint32_t hh[4], ll[4];
+                    for (int g = 0; g < ROWB / 16; ++g) {
+                        constexpr int PER = 16 / ESZ;
+                        float x[PER];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            hh[q] = to_tf32(x[q]);
-                            ll[q] = to_tf32(x[q] - __uint_as_float(hh[q]));
+                        for (int q = 0; q < PER; ++q) x[q] = stg[(g * PER + q) * ncols + cc] - sv;
+                        uint4 h, l;
+                        if (KIND == 0) {
+                            uint32_t hh[4], ll[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                hh[q] = to_tf32(x[q]);
+                                ll[q] = to_tf32(x[q] - __uint_as_float(hh[q]));
+                            }
+                            h = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+                            l = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+                        } else {
+                            uint32_t hh[4], ll[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                uint16_t h0 = to_bf16(x[2 * q]), h1 = to_bf16(x[2 * q + 1]);
+                                float r0 = x[2 * q] - __uint_as_float((uint32_t)h0 << 16);
+                                float r1 = x[2 * q + 1] - __uint_as_float((uint32_t)h1 << 16);
+                                hh[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                                ll[q] = (uint32_t)to_bf16(r0) | ((uint32_t)to_bf16(r1) << 16);
+                            }
+                            h = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+                            l = make_uint4(ll[0], ll[1], ll[2], ll[3]);
                         }
-                        h = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-                        l = make_uint4(ll[0], ll[1], ll[2], ll[3]);
-                    } else {
-                        uint32_t hh[4], ll[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            uint16_t h0 = to_bf16(x[2 * q]), h1 = to_bf16(x[2 * q + 1]);
-                            float r0 = x[2 * q] - __uint_as_float((uint32_t)h0 << 16);
-                            float r1 = x[2 * q + 1] - __uint_as_float((uint32_t)h1 << 16);
-                            hh[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                            ll[q] = (uint32_t)to_bf16(r0) | ((uint32_t)to_bf16(r1) << 16);
-                        }
-                        h = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-                        l = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+                        *(uint4*)(st + L.off_bhi + t * SPART + core_off(ct, 16 * g)) = h;
+                        *(uint4*)(st + L.off_blo + t * SPART + core_off(ct, 16 * g)) = l;
                     }
-                    *(uint4*)(st + L.off_bhi + core_off(ct, 16 * g)) = h;
-                    *(uint4*)(st + L.off_blo + core_off(ct, 16 * g)) = l;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(smem_u32(&bar_conv[s]));
@@ -340,51 +381,53 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
     } else {
         // ---------------------------------------------------------- epilogue
         const int q = warp & 3;                        // TMEM lane quadrant of this warp
-        int tc = 0;
-        for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++tc) {
-            const int b = tc % L.tbuf;
-            if (!mbar_wait(smem_u32(&bar_tfull[b]), (tc / L.tbuf) & 1, a.limit)) { ok = false; break; }
+        const int grp = (warp - 6) >> 2;               // 16-row groups grp, grp + EG, ...
+        int wc = 0;
+        for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x, ++wc) {
+            const int tile = w / a.nrb, rb = w - tile * a.nrb;
+            const int rbase = rb * a.rbr;                         // first operator row of the block
+            const int mr = min(a.rbr, a.M - rbase);               // real rows in the block
+            const int b = wc % L.tbuf;
+            if (!mbar_wait(smem_u32(&bar_tfull[b]), (wc / L.tbuf) & 1, a.limit)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int64_t col = (int64_t)tile * BN + q * 32 + lane;    // this thread's state column
-            const float* rcp_col = a.epi == 1 ? a.rcp + (int64_t)a.row0 * a.ld + col % a.ld : nullptr;
-            float* c_col = a.C + (int64_t)a.row0 * a.N + col;
-            // -1/J of the next 16 rows is loaded before the previous 16 are stored, so the
-            // loads never wait behind stores they might alias
-            float rc[16];
-            if (a.epi == 1) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) rc[j] = j < a.M ? __ldg(rcp_col + (int64_t)j * a.ld) : 0.f;
-            }
+            for (int t = 0; t < NT; ++t) {
+                const int64_t col = (int64_t)tile * NT * BN + t * BN + q * 32 + lane;    // this thread's state column
+                const bool col_ok = col < a.N;
+                const float* rcp_col =
+                    (a.epi == 1 && col_ok) ? a.rcp + (int64_t)rbase * a.ld + col % a.ld : nullptr;
+                float* c_col = a.C + (int64_t)rbase * a.N + col;
 #pragma unroll 1
-            for (int r0 = 0; r0 < a.M; r0 += 16) {
-                uint32_t r[16];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * L.nrp + r0);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                    "%12, %13, %14, %15}, [%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                      "=r"(r[14]), "=r"(r[15])
-                    : "r"(taddr));
-                float rn[16];
-                if (a.epi == 1) {
+                for (int r0 = 16 * grp; r0 < mr; r0 += 16 * EG) {
+                    uint32_t r[16];
+                    const uint32_t taddr =
+                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT * L.nrp + t * L.nrp + r0);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15}, [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(taddr));
+                    // -1/J is loaded while the tensor-memory load is in flight
+                    float rc[16];
+                    if (rcp_col) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        rn[j] = r0 + 16 + j < a.M ? __ldg(rcp_col + (int64_t)(r0 + 16 + j) * a.ld) : 0.f;
-                }
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float* cp = c_col + (int64_t)r0 * a.N;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (r0 + j < a.M) {
-                        float v = __uint_as_float(r[j]);
-                        if (a.epi == 1) v = -v * rc[j];
-                        cp[(int64_t)j * a.N] = v;
+                        for (int j = 0; j < 16; ++j)
+                            rc[j] = r0 + j < mr ? __ldg(rcp_col + (int64_t)(r0 + j) * a.ld) : 0.f;
                     }
-                }
-                if (a.epi == 1) {
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (col_ok) {
+                        float* cp = c_col + (int64_t)r0 * a.N;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) rc[j] = rn[j];
+                        for (int j = 0; j < 16; ++j) {
+                            if (r0 + j < mr) {
+                                float v = __uint_as_float(r[j]);
+                                if (rcp_col) v = -v * rc[j];
+                                cp[(int64_t)j * a.N] = v;
+                            }
+                        }
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -426,10 +469,11 @@ std::vector<uint8_t> pack_operator(int kind, const std::vector<double>& A, int M
     const int nch1 = (K1 + kce - 1) / kce, nch2 = (K2 + kce - 1) / kce, nch = nch1 + nch2;
     const int K = K1 + K2;
     std::vector<uint8_t> out;
-    // row blocks of at most MAX_NR rows, each: nch chunks of [hi part | lo part]
-    for (int rb = 0; rb < M; rb += MAX_NR) {
-        const int nr = std::min(MAX_NR, M - rb);
-        const int nrp = pad_rows(nr), opart = nrp * ROWB;
+    // nrb row blocks of rbr rows, each: nch chunks of [hi part | lo part]
+    const RowBlocks B = row_blocks(M);
+    for (int rb = 0; rb < B.nrb * B.rbr; rb += B.rbr) {
+        const int nr = std::min(B.rbr, M - rb);
+        const int nrp = B.rbr, opart = nrp * ROWB;
         const size_t base = out.size();
         out.resize(base + (size_t)nch * 2 * opart, 0);
         for (int c = 0; c < nch; ++c) {
@@ -472,13 +516,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2D map over a row-major FP32 matrix [rows][N], box = kce rows x 128 columns
-static bool make_map(CUtensorMap* m, const float* base, int64_t N, int rows, int kce) {
+// 2D map over a row-major FP32 matrix [rows][N], box = kce rows x (nt * 128) columns
+static bool make_map(CUtensorMap* m, const float* base, int64_t N, int rows, int kce, int nt) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)N * 4};
-    cuuint32_t box[2] = {(cuuint32_t)BN, (cuuint32_t)kce};
+    cuuint32_t box[2] = {(cuuint32_t)(BN * nt), (cuuint32_t)kce};
     cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -488,33 +532,37 @@ static bool make_map(CUtensorMap* m, const float* base, int64_t N, int rows, int
 static int g_nsm = 0;
 static bool g_attr[2] = {false, false};
 
+template <int KIND>
+static cudaError_t set_smem() {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_gemm_kernel<KIND, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
+    return e;
+}
+
 cudaError_t prepare() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     if (g_nsm <= 0) g_nsm = 148;
-    if ((e = cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024)) !=
-        cudaSuccess)
-        return e;
+    if ((e = set_smem<0>()) != cudaSuccess || (e = set_smem<1>()) != cudaSuccess) return e;
     g_attr[0] = g_attr[1] = true;
     return encode_fn() ? cudaSuccess : cudaErrorSymbolNotFound;
 }
 
 template <int KIND>
-static cudaError_t launch(const TcArgs& a, const CUtensorMap& m1, const CUtensorMap& m2, int nsm, cudaStream_t st) {
-    const Layout L = make_layout(KIND, a.M);
+static cudaError_t launch(const TcArgs& a, int nt, const CUtensorMap& m1, const CUtensorMap& m2, int nsm,
+                          cudaStream_t st) {
+    const Layout L = make_layout(KIND, a.rbr, nt);
     if (!g_attr[KIND]) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             225 * 1024);
+        cudaError_t e = set_smem<KIND>();
         if (e != cudaSuccess) return e;
         g_attr[KIND] = true;
     }
-    const int grid = std::min(a.ntiles, nsm);
-    tc_gemm_kernel<KIND><<<grid, NTHREADS, L.smem, st>>>(a, m1, m2);
+    const int grid = std::min(a.nwork, nsm);
+    if (nt == 2) tc_gemm_kernel<KIND, 2><<<grid, nthreads_for(2), L.smem, st>>>(a, m1, m2);
+    else tc_gemm_kernel<KIND, 1><<<grid, nthreads_for(1), L.smem, st>>>(a, m1, m2);
     return cudaGetLastError();
 }
 
@@ -525,39 +573,40 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
     }
-    const int nsm = g_nsm;
-    if (N % BN != 0) return cudaErrorInvalidValue;
+    if (N % BN != 0 || M <= 0) return cudaErrorInvalidValue;
     const int esz = kind == 0 ? 4 : 2, kce = ROWB / esz;
-    CUtensorMap m1, m2;
-    if (!make_map(&m1, B1, N, K1, kce)) return cudaErrorInvalidValue;
-    if (K2 > 0) {
-        if (!make_map(&m2, B2, N, K2, kce)) return cudaErrorInvalidValue;
-    } else {
-        m2 = m1;
-    }
+    const RowBlocks B = row_blocks(M);
+    const int nt = subtiles_for(B.rbr);
     TcArgs a;
+    a.M = M;
+    a.nrb = B.nrb;
+    a.rbr = B.rbr;
     a.nch1 = (K1 + kce - 1) / kce;
     a.nch2 = K2 > 0 ? (K2 + kce - 1) / kce : 0;
     a.subseg = subseg;
+    a.Apack = (const uint8_t*)Apack;
     a.N = N;
     a.ld = ld;
     a.C = C;
     a.epi = epi;
     a.rcp = rcp;
-    a.sub = sub;
+    a.sub0 = sub.v[0];
+    a.sub1 = sub.v[1];
+    a.sub2 = sub.v[2];
+    a.sub3 = sub.v[3];
+    a.sub4 = sub.v[4];
     a.flags = flags;
     a.limit = 4000000000LL;                  // ~2 s of SM clock cycles per wait
-    a.ntiles = (int)(N / BN);
-    size_t off = 0;
-    for (int rb = 0; rb < M; rb += MAX_NR) {
-        a.M = std::min(MAX_NR, M - rb);
-        a.row0 = rb;
-        a.Apack = (const uint8_t*)Apack + off;
-        cudaError_t e = kind == 0 ? launch<0>(a, m1, m2, nsm, st) : launch<1>(a, m1, m2, nsm, st);
-        if (e != cudaSuccess) return e;
-        off += (size_t)(a.nch1 + a.nch2) * 2 * pad_rows(a.M) * ROWB;
+    a.ntiles = (int)((N + nt * BN - 1) / (nt * BN));
+    a.nwork = a.ntiles * a.nrb;
+    CUtensorMap m1, m2;
+    if (!make_map(&m1, B1, N, K1, kce, nt)) return cudaErrorInvalidValue;
+    if (K2 > 0) {
+        if (!make_map(&m2, B2, N, K2, kce, nt)) return cudaErrorInvalidValue;
+    } else {
+        m2 = m1;
     }
-    return cudaSuccess;
+    return kind == 0 ? launch<0>(a, nt, m1, m2, g_nsm, st) : launch<1>(a, nt, m1, m2, g_nsm, st);
 }
 
 }  // namespace tc
