@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 CUDA-core comparison leg")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16x3 tensor-core comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     return ap.parse_args()
@@ -164,7 +165,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline bookkeeping
-def kernel_work(name, nu, nf, V, D, nelem, npairs, s):
+def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False):
     """Algorithmic (bytes, flops) of one launch of each kernel on the whole block.
 
     Bytes count every value the kernel must read or write once (state, metric
@@ -174,7 +175,10 @@ def kernel_work(name, nu, nf, V, D, nelem, npairs, s):
     if name == "disu_gemm":
         return (nu + nf) * V * s * E, 2.0 * nf * nu * V * E
     if name == "tgradu_gemm":
-        return (nf + nu + D * nu) * V * s * E, 2.0 * D * nu * (nf + nu) * V * E
+        # on the tensor-core path the gradient transform (gradcoru) runs in this
+        # kernel's epilogue: + metric terms adj(J) and 1/J, read once per element
+        extra = (D * D * nu + nu) * s * E if fused else 0
+        return (nf + nu + D * nu) * V * s * E + extra, 2.0 * D * nu * (nf + nu) * V * E
     if name == "gradfpts_gemm":
         return (nu + nf) * V * s * E, 2.0 * nf * nu * V * E
     if name == "tdivf_gemm":
@@ -214,6 +218,28 @@ def measured_traffic(kernel, workload_key):
     return ent.get("bytes_per_launch")
 
 
+# ---------------------------------------------------------------- replicas
+def replica_value(ms_local, units_per_rank, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` independent replicas: every rank
+    processed units_per_rank units; the job time is the slowest rank's.
+    Returns (value in units per second / 1e9, max ms over ranks)."""
+    ms = ms_local
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return units_per_rank * world / (ms / 1e3) / 1e9, ms
+
+
+def operator_flops_per_rhs(nu, nf, V, D, nelem):
+    """Dense operator flops of one NS right-hand side (App. A)."""
+    f = 0.0
+    for k, n in (("disu_gemm", 1), ("tgradu_gemm", 1), ("gradfpts_gemm", D), ("tdivf_gemm", 1)):
+        f += n * kernel_work(k, nu, nf, V, D, nelem, 0, 4)[1]
+    return f
+
+
 # ---------------------------------------------------------------- GPU leg
 def main():
     a = _args()
@@ -250,7 +276,15 @@ def main():
     # FP32 / FP64 CUDA-core peaks from unit counts and the maximum SM clock:
     # 148 SMs x 128 FP32 lanes x 2 flop; FP64 at the B300 rate of 1.25 TFLOP/s nominal.
     sm_max = peaks.get("sm_max_mhz", 2032.0)
-    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_nominal = 148 * 128 * 2 * sm_max * 1e6 / 1e12
+    try:
+        fp32_peak, fp64_peak = fr.fma_peak(local)
+        alu_src = "measured FMA probe (fr_fma_peak)"
+    except fr.FRError:
+        fp32_peak, fp64_peak = fp32_nominal, 1.25
+        alu_src = "nominal unit counts x clock"
+    alu_peaks = dict(fp32_tflops=round(fp32_peak, 2), fp64_tflops=round(fp64_peak, 3), source=alu_src,
+                     fp32_nominal_tflops=round(fp32_nominal, 1), fp64_nominal_tflops=1.25)
 
     t_setup = time.perf_counter()
     mesh = periodic_box("hex", a.n, 0.0, 2 * np.pi)
@@ -295,32 +329,29 @@ def main():
     ms = ev0.elapsed_time(ev1)
     prof = s.profile_read()
     s.profile_enable(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    stages = 4 * a.steps
+    value, ms = replica_value(ms, dof * stages, world, dist, "cuda")
     assert s.sync_status() == fr.OK
     s.check_finite([u])
     finite_ok = s.sync_status() == fr.OK
-    stages = 4 * a.steps
-    value = dof * stages * world / (ms / 1e3) / 1e9
     launches = sum(v[0] for v in prof.values())
 
     # roofline of the dominant kernel: the binding one of its HBM time and its
     # arithmetic time (tensor cores for the split-precision GEMMs, CUDA cores otherwise)
     npairs = nelem * nf // 2
     srz = 8 if a.precision == "fp64" else 4
+    tc_path = a.precision in ("tf32x3", "bf16x3")
     bf16_peak = peaks.get("bf16_tflops", 1800.0)
     arith = {  # precision -> (peak TFLOP/s, executed / algorithmic flops, unit name, source)
         "tf32x3": (bf16_peak * 1.1 / 2.25, 3.0, "TF32 tensor",
                    "measured BF16 dense x nominal TF32/BF16 ratio (1.1/2.25)"),
         "bf16x3": (bf16_peak, 3.0, "BF16 tensor", "measured BF16 dense (cuBLAS burst)"),
-        "fp32": (fp32_peak, 1.0, "FP32 CUDA core", "148 SMs x 128 FP32 lanes x 2 flop x max SM clock"),
-        "fp64": (1.25, 1.0, "FP64", "nominal FP64 rate of the B300"),
+        "fp32": (fp32_peak, 1.0, "FP32 CUDA core", alu_src),
+        "fp64": (fp64_peak, 1.0, "FP64", alu_src),
     }[a.precision]
 
     def roof_of(name, launches, tms):
-        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz)
+        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz, tc_path)
         avg = tms / launches / 1e3
         t_hbm = kb / (hbm_peak * 1e9) if kb else 0.0
         t_alu = (kf * arith[1]) / (arith[0] * 1e12) if kf else 0.0
@@ -348,7 +379,7 @@ def main():
         if not v[0]:
             continue
         d = dict(launches=v[0], ms=round(v[1], 3), share=round(v[1] / max(total_ms, 1e-9), 4))
-        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz)
+        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz, tc_path)
         if b:
             d["GB_s"] = round(b / (d["ms"] / d["launches"] / 1e3) / 1e9, 1)
         if f:
@@ -391,13 +422,22 @@ def main():
         sl.close()
         del ul, rl
         torch.cuda.empty_cache()
-        return dict(gdofs_per_rhs=dof / (t / 1e3) / 1e9, ms_per_rhs=t, precision=prec)
+        fl = operator_flops_per_rhs(nu, nf, V, D, nelem)
+        pk, wf, pname = {"fp32": (fp32_peak, 1.0, "FP32 FMA (measured)"), "fp64": (fp64_peak, 1.0, "FP64 FMA (measured)"),
+                         "bf16x3": (bf16_peak, 3.0, "BF16 tensor (measured cuBLAS)"),
+                         "tf32x3": (bf16_peak * 1.1 / 2.25, 3.0, "TF32 tensor")}[prec]
+        whole = fl * wf / (t / 1e3) / 1e12
+        return dict(gdofs_per_rhs=dof / (t / 1e3) / 1e9, ms_per_rhs=t, precision=prec,
+                    operator_tflops_whole_rhs=round(whole, 2), alu_peak_tflops=round(pk, 2), alu_peak=pname,
+                    alu_frac_whole_rhs=round(whole / pk, 3),
+                    note="operator flops (x3 for split precision) over the whole RHS time, all kernels included")
 
     s.close()
     del u
     torch.cuda.empty_cache()
     fp32 = rhs_leg("fp32", 3) if (not a.no_fp32 and a.precision != "fp32") else None
     fp64 = rhs_leg("fp64", 2) if (not a.no_fp64 and a.precision != "fp64") else None
+    bf16 = rhs_leg("bf16x3", 3) if (not a.no_bf16 and a.precision != "bf16x3") else None
 
     if rank != 0:
         return 0
@@ -412,7 +452,8 @@ def main():
                     l2="inputs larger than L2 (state alone is %.1f GB)" % (u_init.numel() * u_init.element_size() / 1e9),
                     parallelism=f"replicas x{world}", setup_s=round(t_setup, 1)),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
-        clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, finite=finite_ok,
+        clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16,
+        alu_peaks=alu_peaks, finite=finite_ok,
     )
     print(json.dumps(line))
     return 0

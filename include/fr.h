@@ -285,6 +285,16 @@ const char* fr_last_error(const fr_ctx* ctx);
 /* Frees everything the context owns.  Synchronises its device. */
 void fr_destroy(fr_ctx* ctx);
 
+/*
+ * Measured FMA throughput of the CUDA cores of device cuda_device, in TFLOP/s
+ * (2 flop per FMA): eight independent FP32 (resp. FP64) FMA chains per thread
+ * over 8 blocks of 256 threads per SM, best of three timed launches.  Used as
+ * the ALU roofline of the plain FP32 and FP64 paths.  Synchronous; sets the
+ * calling thread's current device.  FR_ERR_ARG for NULL outputs, FR_ERR_CUDA
+ * on any CUDA failure.
+ */
+fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops);
+
 /* ABI version (increments on any signature change). */
 int32_t fr_version(void);   /* 2 */
 

@@ -174,8 +174,16 @@ void upload_device(fr_ctx* c) {
         if (c->prm.precision == FR_PREC_BF16X3 || c->prm.precision == FR_PREC_TF32X3) {
             const int kind = c->prm.precision == FR_PREC_TF32X3 ? 0 : 1;
             B.tcM0 = upload(c, fr::tc::pack_operator(kind, el.M0, (int)nf, (int)nu, 0));
-            B.tcQ = upload(c, fr::tc::pack_operator(kind, hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu),
-                                                    d * (int)nu, (int)nf, (int)nu));
+            // corrected-gradient operator with its rows reordered point-major,
+            // (i, s) -> s * d + i, for the fused gradient transform epilogue
+            const std::vector<double> Q = hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu);
+            const size_t kq = nf + nu;
+            std::vector<double> Qp(Q.size());
+            for (int i = 0; i < d; ++i)
+                for (size_t s = 0; s < nu; ++s)
+                    std::copy(&Q[((size_t)i * nu + s) * kq], &Q[((size_t)i * nu + s) * kq] + kq,
+                              &Qp[(s * d + i) * kq]);
+            B.tcQ = upload(c, fr::tc::pack_operator(kind, Qp, d * (int)nu, (int)nf, (int)nu, d));
             B.tcR = upload(c, fr::tc::pack_operator(kind, hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu),
                                                     (int)nu, (int)nf, (int)(d * nu)));
         }
@@ -246,6 +254,12 @@ void ctx_set_error(fr_ctx* c, const char* msg) {
 extern "C" {
 
 int32_t fr_version(void) { return 2; }
+
+fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops) {
+    if (!fp32_tflops || !fp64_tflops) return FR_ERR_ARG;
+    if (cudaSetDevice(cuda_device) != cudaSuccess) return FR_ERR_CUDA;
+    return fr::measure_fma(fp32_tflops, fp64_tflops) == cudaSuccess ? FR_OK : FR_ERR_CUDA;
+}
 
 const char* fr_last_error(const fr_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_err.c_str(); }
 

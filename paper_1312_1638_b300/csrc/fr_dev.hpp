@@ -115,6 +115,8 @@ cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStr
 // FP64 weighted totals per variable
 cudaError_t launch_sum_weighted(DevCtx& c, void* const* u, double* host_out, cudaStream_t st);
 cudaError_t launch_check_finite(DevCtx& c, void* const* u, cudaStream_t st);
+// FP32 and FP64 FMA throughput of the current device (TFLOP/s), synchronous
+cudaError_t measure_fma(double* fp32_tflops, double* fp64_tflops);
 
 }  // namespace fr
 

@@ -674,15 +674,25 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
             DevBlock& B = c.blocks[b];
             int64_t N = (int64_t)NV * B.ld;
             // 3. Q~ = M6 C + (M4 - M6 M0) U  (tgradu, eq. tquptsm)
+            // 4. Q = J^{-T} Q~ (gradcoru; in the tensor-core GEMM's epilogue)
             prof_begin(c, K_TGRADU, st);
-            FR_TRY(op_gemm<T>(c, B.opQ, B.tcQ, D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.Qf, u[b], N, B.Q, 0, nullptr, B.ld,
-                       st, B.nfpts, B.nfpts + B.nupts, sub));
-            prof_end(c, st);
-            // 4. Q = J^{-T} Q~
-            prof_begin(c, K_GRADCORU, st);
-            grad_transform_kernel<T, D><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
-                B.nupts, B.nelem, B.ld, (const T*)B.smat, (const T*)B.rcpdjac, (T*)B.Q);
-            prof_end(c, st);
+            if (c.precision >= 2) {
+                tc::SubRef sr;
+                for (int a = 0; a < 5; ++a) sr.v[a] = (float)sub.v[a];
+                const tc::GradXform gx{(const float*)B.smat, D, B.nupts, NV};
+                FR_TRY(tc::gemm(c.precision == 3 ? 0 : 1, D * B.nupts, B.nfpts, B.nupts, B.tcQ, (const float*)B.Qf,
+                                (const float*)u[b], N, (float*)B.Q, 0, (const float*)B.rcpdjac, B.ld, 2, sr, c.flags,
+                                st, &gx));
+                prof_end(c, st);
+            } else {
+                FR_TRY(op_gemm<T>(c, B.opQ, B.tcQ, D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.Qf, u[b], N, B.Q, 0,
+                                  nullptr, B.ld, st, B.nfpts, B.nfpts + B.nupts, sub));
+                prof_end(c, st);
+                prof_begin(c, K_GRADCORU, st);
+                grad_transform_kernel<T, D><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                    B.nupts, B.nelem, B.ld, (const T*)B.smat, (const T*)B.rcpdjac, (T*)B.Q);
+                prof_end(c, st);
+            }
             // 5. Q^(f) = M5 Q (block diagonal: M0 per component)
             for (int i = 0; i < D; ++i) {
                 prof_begin(c, K_GRADFPTS, st);
@@ -839,6 +849,62 @@ cudaError_t launch_check_finite(DevCtx& c, void* const* u, cudaStream_t st) {
                                                                                (const float*)u[b], c.flags);
     }
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FMA peak probe
+// Eight independent FMA chains per thread, enough warps to fill every
+// scheduler; the result is only stored when it equals an impossible value,
+// which keeps the chains alive without a memory stream.
+template <typename T>
+__global__ void fma_probe_kernel(T* out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k) * (T)1e-3;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += x[k];
+    if (sum == (T)-12345.678) out[0] = sum;
+}
+
+template <typename T>
+static cudaError_t time_fma(int nsm, int iters, double* tflops) {
+    T* out = nullptr;
+    cudaError_t e = cudaMalloc(&out, sizeof(T));
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int grid = nsm * 8, block = 256;
+    float best = 1e30f;
+    for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+        cudaEventRecord(e0, 0);
+        fma_probe_kernel<T><<<grid, block>>>(out, iters, (T)0.999999, (T)1e-7);
+        cudaEventRecord(e1, 0);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = std::min(best, ms);               // first launch is the warm-up
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    *tflops = 2.0 * 8.0 * iters * (double)grid * block / (best * 1e-3) / 1e12;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    return e;
+}
+
+cudaError_t measure_fma(double* fp32_tflops, double* fp64_tflops) {
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = time_fma<float>(nsm, 1 << 16, fp32_tflops);
+    if (e == cudaSuccess) e = time_fma<double>(nsm, 1 << 11, fp64_tflops);
+    return e;
 }
 
 }  // namespace fr

@@ -69,34 +69,48 @@ __host__ __device__ constexpr int core_off(int r, int kb) {
     return ((r >> 3) * (2 * KSTEPS) + (kb >> 4)) * 128 + (r & 7) * 16 + (kb & 15);
 }
 
-// Row blocks of an M-row operator: nrb equal blocks of rbr rows (a multiple
-// of 16, at most MAX_RB); the last block may hold fewer real rows.
+// Row blocks of an M-row operator.  group = 1: nrb equal blocks of rr rows
+// (a multiple of 16, at most MAX_RB), the last one possibly shorter.  group =
+// g > 1 (rows ordered point-major, g rows per point): every block holds whole
+// points, rr = g * (points per block), and the MMA width nrp covers whole
+// 16-point units, 16 g ceil(points / 16) <= MAX_RB.
 struct RowBlocks {
-    int nrb, rbr;
+    int nrb, rr, nrp;
 };
-__host__ __device__ inline RowBlocks row_blocks(int M) {
+__host__ __device__ inline RowBlocks row_blocks(int M, int group) {
     RowBlocks r;
-    const int n0 = (M + MAX_RB - 1) / MAX_RB;
-    r.rbr = ((M + n0 - 1) / n0 + 15) / 16 * 16;
-    r.nrb = (M + r.rbr - 1) / r.rbr;            // no empty trailing block
+    if (group <= 1) {
+        const int n0 = (M + MAX_RB - 1) / MAX_RB;
+        r.nrp = ((M + n0 - 1) / n0 + 15) / 16 * 16;
+        r.rr = r.nrp;
+    } else {
+        const int npts = M / group, cap = (MAX_RB / (16 * group)) * 16;
+        const int n0 = (npts + cap - 1) / cap, ppb = (npts + n0 - 1) / n0;
+        r.rr = ppb * group;
+        r.nrp = 16 * group * ((ppb + 15) / 16);
+    }
+    r.nrb = (M + r.rr - 1) / r.rr;              // no empty trailing block
     return r;
 }
 
 // 128-column subtiles per work item: two when the row block is at most 128
 // rows, so that both accumulators still fit twice in tensor memory
-__host__ __device__ constexpr int subtiles_for(int rbr) { return rbr <= 128 ? 2 : 1; }
+__host__ __device__ constexpr int subtiles_for(int nrp) { return nrp <= 128 ? 2 : 1; }
 // epilogue warp groups (4 warps each, one per TMEM lane quadrant)
-__host__ __device__ constexpr int epi_groups(int nt) { return nt == 2 ? 1 : 3; }
-__host__ __device__ constexpr int nthreads_for(int nt) { return 192 + 128 * epi_groups(nt); }
+// (the gradient transform epilogue, gd > 0, holds more registers per thread)
+constexpr int GX_EG = 4;                       // epilogue warp groups with the gradient transform
+constexpr int GX_PB = 2;                       // points whose metric terms are loaded together
+__host__ __device__ constexpr int epi_groups(int nt, int gd) { return gd ? GX_EG : nt == 2 ? 1 : 3; }
+__host__ __device__ constexpr int nthreads_for(int nt, int gd) { return 192 + 128 * epi_groups(nt, gd); }
 
 struct Layout {
     int nrp;                      // rows per block (MMA N)
     int opart, a_bytes, stg_bytes, off_stg, off_bhi, off_blo, stage, nst, tbuf, smem;
 };
 
-__host__ __device__ inline Layout make_layout(int kind, int rbr, int nt) {
+__host__ __device__ inline Layout make_layout(int kind, int nrp, int nt) {
     Layout L;
-    L.nrp = rbr;
+    L.nrp = nrp;
     L.opart = L.nrp * ROWB;
     L.a_bytes = 2 * L.opart;
     const int kce = ROWB / (kind == 0 ? 4 : 2);
@@ -184,7 +198,7 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uin
 
 struct TcArgs {
     int M;              // operator rows
-    int nrb, rbr;       // row blocks and rows per block
+    int nrb, rr, nrp;   // row blocks, operator rows per block, padded rows per block (MMA N)
     int nch1, nch2;     // K chunks of segment 1 (B1) and 2 (B2)
     int subseg;         // segment whose rows get the reference subtracted (0: none)
     const uint8_t* Apack;   // packed operator: nrb blocks of nch chunks of Layout::a_bytes
@@ -197,16 +211,82 @@ struct TcArgs {
     long long limit;
     int ntiles;         // column tiles (NT * 128 columns each)
     int nwork;          // ntiles * nrb
+    // gradient transform epilogue (epi = 2): rows are (point, direction) pairs
+    // s * gD + i; row j * gnu + s of C receives rcp(s) sum_i smat[i][j](s) acc(s, i)
+    const float* smat;
+    int gD, gnu;
+    int vinter;         // > 0: work order interleaves the vinter variables of one element range
 };
+
+// column tile of the tl-th tile in work order
+__device__ __forceinline__ int col_tile(const TcArgs& a, int tl) {
+    if (!a.vinter) return tl;
+    const int per = a.ntiles / a.vinter;
+    return (tl % a.vinter) * per + tl / a.vinter;
+}
+
+// Epilogue of the gradient transform: 8-point units of one row block,
+// q_i = acc(s, i) from tensor memory, Q_j(s) = rcp(s) sum_i adj_ij(s) q_i
+// (Q = J^-T Q~, with adj = J J^-1 and rcp = 1/J stored per point).
+template <int D>
+__device__ __forceinline__ void epi_grad(const TcArgs& a, uint32_t tcol, int p0, int np, int u_first, int u_step,
+                                         int64_t col, bool col_ok) {
+    const int64_t n = col % a.ld, ld = a.ld, N = a.N;
+    const float* sm = a.smat + n;
+    const float* rc = a.rcp + n;
+    float* cc = a.C + col;
+    const int64_t es = (int64_t)a.gnu * ld;           // stride between the D*D metric entries
+#pragma unroll 1
+    for (int u0 = u_first; u0 < np; u0 += u_step) {
+        uint32_t r[8 * D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const uint32_t ta = tcol + (uint32_t)(u0 * D + 8 * k);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(r[8 * k + 0]), "=r"(r[8 * k + 1]), "=r"(r[8 * k + 2]), "=r"(r[8 * k + 3]),
+                  "=r"(r[8 * k + 4]), "=r"(r[8 * k + 5]), "=r"(r[8 * k + 6]), "=r"(r[8 * k + 7])
+                : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!col_ok) continue;
+#pragma unroll
+        for (int pg = 0; pg < 8; pg += GX_PB) {
+            // the metric terms of GX_PB points are loaded before any of them is used
+            float m[GX_PB][D * D], rj[GX_PB];
+#pragma unroll
+            for (int k = 0; k < GX_PB; ++k) {
+                const int s = min(p0 + u0 + pg + k, p0 + np - 1);       // clamped: rows past np are not stored
+                const float* ps = sm + (int64_t)s * ld;
+#pragma unroll
+                for (int e = 0; e < D * D; ++e) m[k][e] = __ldg(ps + e * es);
+                rj[k] = __ldg(rc + (int64_t)s * ld);
+            }
+#pragma unroll
+            for (int k = 0; k < GX_PB; ++k) {
+                const int s = p0 + u0 + pg + k;
+                if (u0 + pg + k < np) {
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) acc += m[k][i * D + j] * __uint_as_float(r[(pg + k) * D + i]);
+                        cc[((int64_t)j * a.gnu + s) * N] = acc * rj[k];
+                    }
+                }
+            }
+        }
+    }
+}
 
 __device__ __forceinline__ float sub_of(const TcArgs& a, int64_t v) {
     return v == 0 ? a.sub0 : v == 1 ? a.sub1 : v == 2 ? a.sub2 : v == 3 ? a.sub3 : a.sub4;
 }
 
-template <int KIND, int NT>
-__global__ void __launch_bounds__(nthreads_for(NT), 1)
+template <int KIND, int NT, int GD>
+__global__ void __launch_bounds__(nthreads_for(NT, GD), 1)
 tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2) {
-    constexpr int EG = epi_groups(NT);
+    constexpr int EG = epi_groups(NT, GD);
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[MAX_NST], bar_conv[MAX_NST], bar_empty[MAX_NST];
     __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
@@ -214,7 +294,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nch = a.nch1 + a.nch2;
-    const Layout L = make_layout(KIND, a.rbr, NT);
+    const Layout L = make_layout(KIND, a.nrp, NT);
     constexpr int ESZ = KIND == 0 ? 4 : 2;
     constexpr int KCE = ROWB / ESZ;
 
@@ -246,8 +326,8 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
         if (lane == 0) {
             int it = 0;
             for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x) {
-                const int tile = w / a.nrb, rb = w - tile * a.nrb;
-                const int col0 = tile * NT * BN;
+                const int tl = w / a.nrb, rb = w - tl * a.nrb;
+                const int col0 = col_tile(a, tl) * NT * BN;
                 const uint8_t* ablk = a.Apack + (size_t)rb * nch * L.a_bytes;
                 for (int c = 0; c < nch; ++c, ++it) {
                     const int s = it % L.nst, k = it / L.nst;
@@ -322,7 +402,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
         constexpr int ncols = NT * BN;
         int it = 0;
         for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x) {
-            const int tile = w / a.nrb;
+            const int tile = col_tile(a, w / a.nrb);
             float subv[NT];
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
@@ -384,9 +464,10 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
         const int grp = (warp - 6) >> 2;               // 16-row groups grp, grp + EG, ...
         int wc = 0;
         for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x, ++wc) {
-            const int tile = w / a.nrb, rb = w - tile * a.nrb;
-            const int rbase = rb * a.rbr;                         // first operator row of the block
-            const int mr = min(a.rbr, a.M - rbase);               // real rows in the block
+            const int tl = w / a.nrb, rb = w - tl * a.nrb;
+            const int tile = col_tile(a, tl);
+            const int rbase = rb * a.rr;                          // first operator row of the block
+            const int mr = min(a.rr, a.M - rbase);                // real rows in the block
             const int b = wc % L.tbuf;
             if (!mbar_wait(smem_u32(&bar_tfull[b]), (wc / L.tbuf) & 1, a.limit)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -394,14 +475,18 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
             for (int t = 0; t < NT; ++t) {
                 const int64_t col = (int64_t)tile * NT * BN + t * BN + q * 32 + lane;    // this thread's state column
                 const bool col_ok = col < a.N;
+                const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT * L.nrp + t * L.nrp);
+                if constexpr (GD > 0) {
+                    epi_grad<GD>(a, tcol, rbase / GD, mr / GD, 8 * grp, 8 * EG, col, col_ok);
+                    continue;
+                }
                 const float* rcp_col =
                     (a.epi == 1 && col_ok) ? a.rcp + (int64_t)rbase * a.ld + col % a.ld : nullptr;
                 float* c_col = a.C + (int64_t)rbase * a.N + col;
 #pragma unroll 1
                 for (int r0 = 16 * grp; r0 < mr; r0 += 16 * EG) {
                     uint32_t r[16];
-                    const uint32_t taddr =
-                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT * L.nrp + t * L.nrp + r0);
+                    const uint32_t taddr = tcol + (uint32_t)r0;
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
                         "%12, %13, %14, %15}, [%16];"
@@ -464,16 +549,16 @@ static float f_of(uint32_t u) {
     return f;
 }
 
-std::vector<uint8_t> pack_operator(int kind, const std::vector<double>& A, int M, int K1, int K2) {
+std::vector<uint8_t> pack_operator(int kind, const std::vector<double>& A, int M, int K1, int K2, int group) {
     const int esz = kind == 0 ? 4 : 2, kce = ROWB / esz;
     const int nch1 = (K1 + kce - 1) / kce, nch2 = (K2 + kce - 1) / kce, nch = nch1 + nch2;
     const int K = K1 + K2;
     std::vector<uint8_t> out;
-    // nrb row blocks of rbr rows, each: nch chunks of [hi part | lo part]
-    const RowBlocks B = row_blocks(M);
-    for (int rb = 0; rb < B.nrb * B.rbr; rb += B.rbr) {
-        const int nr = std::min(B.rbr, M - rb);
-        const int nrp = B.rbr, opart = nrp * ROWB;
+    // nrb row blocks of rr rows padded to nrp, each: nch chunks of [hi part | lo part]
+    const RowBlocks B = row_blocks(M, group);
+    for (int rb = 0; rb < B.nrb * B.rr; rb += B.rr) {
+        const int nr = std::min(B.rr, M - rb);
+        const int nrp = B.nrp, opart = nrp * ROWB;
         const size_t base = out.size();
         out.resize(base + (size_t)nch * 2 * opart, 0);
         for (int c = 0; c < nch; ++c) {
@@ -534,10 +619,14 @@ static bool g_attr[2] = {false, false};
 
 template <int KIND>
 static cudaError_t set_smem() {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<KIND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_gemm_kernel<KIND, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
-    return e;
+    const void* fns[6] = {(const void*)tc_gemm_kernel<KIND, 1, 0>, (const void*)tc_gemm_kernel<KIND, 2, 0>,
+                          (const void*)tc_gemm_kernel<KIND, 1, 2>, (const void*)tc_gemm_kernel<KIND, 2, 2>,
+                          (const void*)tc_gemm_kernel<KIND, 1, 3>, (const void*)tc_gemm_kernel<KIND, 2, 3>};
+    for (const void* f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t prepare() {
@@ -554,33 +643,44 @@ cudaError_t prepare() {
 template <int KIND>
 static cudaError_t launch(const TcArgs& a, int nt, const CUtensorMap& m1, const CUtensorMap& m2, int nsm,
                           cudaStream_t st) {
-    const Layout L = make_layout(KIND, a.rbr, nt);
+    const Layout L = make_layout(KIND, a.nrp, nt);
     if (!g_attr[KIND]) {
         cudaError_t e = set_smem<KIND>();
         if (e != cudaSuccess) return e;
         g_attr[KIND] = true;
     }
     const int grid = std::min(a.nwork, nsm);
-    if (nt == 2) tc_gemm_kernel<KIND, 2><<<grid, nthreads_for(2), L.smem, st>>>(a, m1, m2);
-    else tc_gemm_kernel<KIND, 1><<<grid, nthreads_for(1), L.smem, st>>>(a, m1, m2);
+    const int gd = a.epi == 2 ? a.gD : 0;
+    if (nt == 2) {
+        if (gd == 3) tc_gemm_kernel<KIND, 2, 3><<<grid, nthreads_for(2, 3), L.smem, st>>>(a, m1, m2);
+        else if (gd == 2) tc_gemm_kernel<KIND, 2, 2><<<grid, nthreads_for(2, 2), L.smem, st>>>(a, m1, m2);
+        else tc_gemm_kernel<KIND, 2, 0><<<grid, nthreads_for(2, 0), L.smem, st>>>(a, m1, m2);
+    } else {
+        if (gd == 3) tc_gemm_kernel<KIND, 1, 3><<<grid, nthreads_for(1, 3), L.smem, st>>>(a, m1, m2);
+        else if (gd == 2) tc_gemm_kernel<KIND, 1, 2><<<grid, nthreads_for(1, 2), L.smem, st>>>(a, m1, m2);
+        else tc_gemm_kernel<KIND, 1, 0><<<grid, nthreads_for(1, 0), L.smem, st>>>(a, m1, m2);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
-                 cudaStream_t st) {
+                 cudaStream_t st, const GradXform* gx) {
     if (!g_nsm) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
     }
     if (N % BN != 0 || M <= 0) return cudaErrorInvalidValue;
     const int esz = kind == 0 ? 4 : 2, kce = ROWB / esz;
-    const RowBlocks B = row_blocks(M);
-    const int nt = subtiles_for(B.rbr);
+    if (gx && (gx->ndims < 2 || gx->ndims > 3 || M != gx->ndims * gx->nupts || !gx->smat || !rcp))
+        return cudaErrorInvalidValue;
+    const RowBlocks B = row_blocks(M, gx ? gx->ndims : 1);
+    const int nt = subtiles_for(B.nrp);
     TcArgs a;
     a.M = M;
     a.nrb = B.nrb;
-    a.rbr = B.rbr;
+    a.rr = B.rr;
+    a.nrp = B.nrp;
     a.nch1 = (K1 + kce - 1) / kce;
     a.nch2 = K2 > 0 ? (K2 + kce - 1) / kce : 0;
     a.subseg = subseg;
@@ -599,6 +699,12 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
     a.limit = 4000000000LL;                  // ~2 s of SM clock cycles per wait
     a.ntiles = (int)((N + nt * BN - 1) / (nt * BN));
     a.nwork = a.ntiles * a.nrb;
+    a.smat = gx ? gx->smat : nullptr;
+    a.gD = gx ? gx->ndims : 0;
+    a.gnu = gx ? gx->nupts : 0;
+    if (gx) a.epi = 2;
+    // the variables of one element range share the metric terms through L2
+    a.vinter = (gx && gx->nvars > 1 && ld % (nt * BN) == 0 && N == (int64_t)gx->nvars * ld) ? gx->nvars : 0;
     CUtensorMap m1, m2;
     if (!make_map(&m1, B1, N, K1, kce, nt)) return cudaErrorInvalidValue;
     if (K2 > 0) {

@@ -19,7 +19,20 @@ struct SubRef {
 // layout of the kernel, split into hi / lo parts: K chunks of segment 1
 // (columns [0, K1)) then of segment 2 (columns [K1, K1 + K2)), each padded
 // with zero columns to whole chunks.  kind 0 = TF32, 1 = BF16.
-std::vector<uint8_t> pack_operator(int kind, const std::vector<double>& A, int M, int K1, int K2);
+// group = g > 1: the rows are (point, component) pairs ordered point-major,
+// g per point, and every row block holds whole points (the layout the
+// gradient transform epilogue needs).
+std::vector<uint8_t> pack_operator(int kind, const std::vector<double>& A, int M, int K1, int K2, int group = 1);
+
+// Gradient transform fused into the epilogue of the corrected-gradient
+// product: the operator's rows are s * ndims + i (packed with group ndims),
+// and row j * nupts + s of C receives rcp(s) sum_i smat[i][j](s) acc(s, i),
+// Q = J^-T Q~ (smat = J J^-1 as [ndims*ndims][nupts][ld], rcp = 1/J as
+// [nupts][ld]).  nvars: variables in the N = nvars * ld columns.
+struct GradXform {
+    const float* smat;
+    int ndims, nupts, nvars;
+};
 
 // One-time launch set-up (shared-memory limits, SM count) on the current
 // device; called at context set-up so that later launches can be captured.
@@ -29,11 +42,12 @@ cudaError_t prepare();
 // rows, both with row stride N (a multiple of 128).  epi = 1 multiplies row
 // r, column c by -rcp[r][c % ld] (-1/J).  Rows of segment `subseg` (1 or 2;
 // 0 = none) have sub.v[c / ld] subtracted (perturbation form).  flags[1] is
-// raised if a wait gives up.  Host-side tensor-map encoding failures return
-// cudaErrorInvalidValue.
+// raised if a wait gives up.  gx (optional) selects the gradient transform
+// epilogue, with rcp = 1/J.  Host-side tensor-map encoding failures and
+// inconsistent arguments return cudaErrorInvalidValue.
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
-                 cudaStream_t st);
+                 cudaStream_t st, const GradXform* gx = nullptr);
 
 }  // namespace tc
 }  // namespace fr

@@ -27,7 +27,7 @@ STATUS_NAMES = ["FR_OK", "FR_ERR_ARG", "FR_ERR_MESH", "FR_ERR_CUDA", "FR_ERR_NON
 EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pairs", "fr_rhs",
            "fr_rhs_host", "fr_rk4", "fr_sum_weighted", "fr_sync_status", "fr_check_finite",
            "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read",
-           "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint", "fr_set_option"]
+           "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint", "fr_set_option", "fr_fma_peak"]
 
 
 class FRError(RuntimeError):
@@ -119,6 +119,16 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(stream.cuda_stream)
+
+
+def fma_peak(device=0):
+    """Measured (FP32, FP64) FMA throughput of the CUDA cores, TFLOP/s."""
+    lib = load()
+    f32, f64 = C.c_double(0), C.c_double(0)
+    st = lib.fr_fma_peak(int(device), C.byref(f32), C.byref(f64))
+    if st != OK:
+        raise FRError(st, "fr_fma_peak failed")
+    return f32.value, f64.value
 
 
 class Solver:
