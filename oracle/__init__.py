@@ -13,6 +13,7 @@ Contents (each module cites the part of the paper it follows):
 * ``geometry``  element mappings and metric terms (Sec. 2)
 * ``physics``   Euler/NS fluxes (Sec. 4), Rusanov (App. B), LDG (Sec. 4.3),
                 boundary ghosts (App. C)
+* ``steppers`` forward Euler and DOPRI5 (Sec. 3 lists them beside RK4)
 * ``system``    pairing, the RHS of Eq. negdivconf, classical RK4
 * ``adjoint``   discrete adjoint of RHS and RK4 (not in the paper)
 

@@ -269,6 +269,16 @@ class FRSystem:
                  for u, a, b, c, e in zip(U, k1, k2, k3, k4)]
         return U
 
+    def euler(self, U, dt, nsteps=1):
+        """Forward Euler (Sec. 3)."""
+        from .steppers import euler
+        return euler(self.rhs, U, dt, nsteps)
+
+    def dopri5(self, U, dt, nsteps=1, atol=1e-6, rtol=1e-6):
+        """nsteps fixed DOPRI5 steps (Sec. 3); returns (U, error norm of the last step)."""
+        from .steppers import dopri5
+        return dopri5(self.rhs, U, dt, nsteps, atol, rtol)
+
     # ------------------------------------------------------------ diagnostics
     def quadrature_weights(self, b):
         """w_rho J_rho at solution points ([nupts, nelem]): the solution-point
