@@ -17,6 +17,17 @@ App. A (operator matrices).  Readings of the paper used here:
   flux point sigma, i.e. int(phi_sigma v) = surface-int(l_sigma v) for all v in
   the solution space, with the exact mass matrix and reference arc length /
   face area.
+* SD and HU correction functions (Sec. 5.1 runs DG, SD and HU "as defined in"
+  Vincent, Castonguay and Jameson 2011, whose formulas the paper does not
+  print): the one-parameter VCJH family in 1D,
+      g_R = (P_p + (eta P_{p-1} + P_{p+1}) / (1 + eta)) / 2,
+      eta = c (2p+1) (a_p p!)^2 / 2,  a_p = (2p)! / (2^p (p!)^2),
+  with c_DG = 0, c_SD = 2p / ((2p+1)(p+1)(a_p p!)^2) and
+  c_HU = 2(p+1) / ((2p+1) p (a_p p!)^2), i.e. eta = 0, p/(p+1), (p+1)/p; on a
+  tensor element div g_sigma = g_R'(s xi_n) times the 1D Lagrange factors of
+  sigma's tangential coordinates (xi_n the coordinate normal to sigma's face,
+  s its outward sign).  Triangles: DG only (the simplex VCJH construction is
+  a separate paper the source does not summarise).
 * M6 as printed in App. A is garbled; it is read as
   (M6)_{(i sigma), rho} = n_{rho,i} (div g_rho)(x_sigma^(u)), which makes
   Eq. tquptsm reproduce Eq. transqu with component stride N^(u).
@@ -29,6 +40,19 @@ import numpy as np
 from .polys import gauss_legendre, legendre, jacobi, lagrange
 
 NDIMS = {"quad": 2, "tri": 2, "hex": 3}
+# VCJH parameter eta(p) of the named correction functions (Vincent et al. 2011)
+VCJH_ETA = {"dg": lambda p: 0.0, "sd": lambda p: p / (p + 1.0), "hu": lambda p: (p + 1.0) / p}
+
+
+def vcjh_right(p, correction, x):
+    """Right VCJH correction function g_R and its derivative at x."""
+    eta = VCJH_ETA[correction](p)
+    lp, dp = legendre(p, x)
+    lm, dm = legendre(p - 1, x) if p >= 1 else (np.zeros_like(lp), np.zeros_like(lp))
+    l1, d1 = legendre(p + 1, x)
+    g = 0.5 * (lp + (eta * lm + l1) / (1.0 + eta))
+    dg = 0.5 * (dp + (eta * dm + d1) / (1.0 + eta))
+    return g, dg
 NFACES = {"quad": 4, "tri": 3, "hex": 6}
 
 
@@ -75,8 +99,13 @@ def _face_maps(etype):
 class RefElement:
     """Standard element of type ``etype`` at polynomial order ``p``."""
 
-    def __init__(self, etype: str, p: int):
+    def __init__(self, etype: str, p: int, correction: str = "dg"):
+        if correction not in VCJH_ETA:
+            raise ValueError(f"unknown correction {correction!r}")
+        if correction != "dg" and etype == "tri":
+            raise ValueError("SD / HU corrections are defined here for tensor elements only")
         self.etype, self.p = etype, p
+        self.correction = correction
         self.ndims = NDIMS[etype]
         self.nfaces = NFACES[etype]
         gl, _ = gauss_legendre(p + 1)
@@ -117,6 +146,25 @@ class RefElement:
         # ---- nodal basis via the generalised Vandermonde matrix -------------
         self.V = self.psi(self.upts.T)                              # [nbasis, nupts]
         self._build_operators()
+
+    def _vcjh_M3(self):
+        """div g_sigma at the solution points for a tensor element: the VCJH
+        g_R' along the face normal times the tangential 1D Lagrange factors."""
+        d, nu, nf = self.ndims, self.nupts, self.nfpts
+        M3 = np.zeros((nu, nf))
+        for sg in range(nf):
+            ax = int(np.argmax(np.abs(self.fnorm[sg])))
+            sgn = np.sign(self.fnorm[sg, ax])
+            _, dg = vcjh_right(self.p, self.correction, sgn * self.upts[:, ax])
+            col = dg.copy()
+            for k in range(d):
+                if k == ax:
+                    continue
+                j = int(np.argmin(np.abs(self.gl - self.fpts[sg, k])))
+                lk, _ = lagrange(self.gl, self.upts[:, k])
+                col *= lk[j]
+            M3[:, sg] = col
+        return M3
 
     # --- spanning basis psi (any basis of the order-p space works, Sec. 2) ---
     def _psi_grad(self, x):
@@ -229,5 +277,7 @@ class RefElement:
             E[:, ids] = (Lface * w) @ lf.T
         self.mass = mass
         self.M3 = np.linalg.solve(mass, E)                         # [nu, nf]
+        if self.correction != "dg":
+            self.M3 = self._vcjh_M3()
         # M6 (reading): (M6)_{(i sigma), rho} = n_{rho,i} M3[sigma, rho]
         self.M6 = (self.fnorm.T[:, None, :] * self.M3[None, :, :]).reshape(d * nu, nf)

@@ -57,7 +57,8 @@ class FRSystem:
         self.prm.update(params)
         self.ndims = mesh.ndims
         self.nvars = self.ndims + 2
-        self.eles = [RefElement(b.etype, order) for b in mesh.blocks]
+        self.correction = self.prm.pop("correction", "dg")
+        self.eles = [RefElement(b.etype, order, self.correction) for b in mesh.blocks]
         self.geo = []
         for b, el in zip(mesh.blocks, self.eles):
             Xu, det, adj = solution_point_metrics(b.etype, b.nodes, el.upts)

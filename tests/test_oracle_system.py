@@ -103,9 +103,9 @@ def test_rk4_amplification_factor():
         assert np.allclose(out, expect, rtol=1e-14)
 
 
-def _vortex_error(n, p, tend=0.5, cfl=0.02):
+def _vortex_error(n, p, tend=0.5, cfl=0.02, correction="dg"):
     m = periodic_box("quad", n, -10.0, 10.0)
-    s = FRSystem(m, p, "euler", gamma=1.4)
+    s = FRSystem(m, p, "euler", gamma=1.4, correction=correction)
     U = state(s, lambda X: fields.isentropic_vortex(X, S=5.0, M=0.4, R=1.5))
     h = 20.0 / n
     nst = int(np.ceil(tend / (cfl * h)))
