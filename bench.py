@@ -196,24 +196,36 @@ def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False):
     return None, None
 
 
-def source_sha():
+# source files that define each profiled kernel: a committed traffic figure is
+# used only while these files are unchanged
+KERNEL_SOURCES = {
+    "tc": ("fr_tc.cu", "fr_tc.hpp"),
+    "pointwise": ("fr_kernels.cu", "fr_dev.hpp"),
+}
+
+
+def kernel_sources(kernel):
+    return KERNEL_SOURCES["tc" if kernel.endswith("_gemm") else "pointwise"]
+
+
+def source_sha(files):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1312_1638_b300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in sorted(files):
         h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(kernel, workload_key):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+    was taken on the current sources of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         tab = json.load(open(path))
     except (OSError, ValueError):
         return None
     ent = tab.get(f"{workload_key}/{kernel}")
-    if not ent or ent.get("source_sha") != source_sha():
+    if not ent or ent.get("source_sha") != source_sha(kernel_sources(kernel)):
         return None
     return ent.get("bytes_per_launch")
 
