@@ -186,6 +186,29 @@ fr_status fr_rhs(fr_ctx* ctx, void* const* u, void* const* r, void* stream);
 fr_status fr_rhs_host(fr_ctx* ctx, const void* const* u, void* const* r, void* stream);
 
 /*
+ * Forward Euler (Sec. 3 lists it among the time steppers): nsteps steps of
+ * u <- u + dt R(u), in place.  Stream-ordered, no host synchronisation; the
+ * first call allocates one state-sized scratch array per block.
+ * FR_ERR_ARG for a NULL/misaligned pointer or nsteps < 0.
+ */
+fr_status fr_euler(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
+
+/*
+ * DOPRI5 (Sec. 3): nsteps fixed steps of the Dormand-Prince 5(4) pair
+ * (Dormand and Prince 1980), in place, propagating the 5th-order solution.
+ * The slope at the new solution is reused as the first slope of the next step
+ * of the same call (6 right-hand sides per step after the first, 7 for the
+ * first).  err (may be NULL): on return, the RMS norm of the last step's
+ * embedded error estimate E = u5 - u4 scaled per entry by
+ * atol + rtol max(|u_n|, |u_n+1|) over every real entry; then the call
+ * synchronises the stream.  With err NULL it is stream-ordered.  The first
+ * call allocates 8 state-sized scratch arrays per block.
+ * FR_ERR_ARG for bad pointers, nsteps < 0, or (err != NULL) atol <= 0 or rtol < 0.
+ */
+fr_status fr_dopri5(fr_ctx* ctx, void* const* u, double dt, int nsteps, double atol, double rtol, double* err,
+                    void* stream);
+
+/*
  * fr_rk4 -- advance u in place by `nsteps` classical RK4 steps of size dt
  * (end of Sec. 2; Sec. 5.1).  Uses two library-owned state registers,
  * allocated on the first call.  Unless disabled with

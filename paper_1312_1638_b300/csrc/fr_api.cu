@@ -491,6 +491,41 @@ fr_status fr_rhs_host(fr_ctx* ctx, const void* const* u, void* const* r, void* s
     return FR_OK;
 }
 
+fr_status fr_euler(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, u) || nsteps < 0) return set_err(ctx, FR_ERR_ARG, "bad argument");
+    const size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    try {
+        for (auto& B : ctx->dev.blocks)
+            if (!B.rk_tmp) B.rk_tmp = dalloc(ctx, (size_t)B.nupts * B.nvars * B.ld * rs);
+    } catch (const Fail& f) {
+        return set_err(ctx, f.st, f.msg);
+    }
+    cudaError_t e = fr::launch_euler(ctx->dev, u, dt, nsteps, (cudaStream_t)stream);
+    return e == cudaSuccess ? FR_OK : set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+}
+
+fr_status fr_dopri5(fr_ctx* ctx, void* const* u, double dt, int nsteps, double atol, double rtol, double* err,
+                    void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if (!ptrs_ok(ctx, u) || nsteps < 0) return set_err(ctx, FR_ERR_ARG, "bad argument");
+    if (err && !(atol > 0.0 && rtol >= 0.0)) return set_err(ctx, FR_ERR_ARG, "atol must be > 0 and rtol >= 0");
+    const size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    try {
+        for (auto& B : ctx->dev.blocks) {
+            const size_t bytes = (size_t)B.nupts * B.nvars * B.ld * rs;
+            if (!B.dp_k) B.dp_k = dalloc(ctx, 7 * bytes);
+            if (!B.dp_y) B.dp_y = dalloc(ctx, bytes);
+        }
+    } catch (const Fail& f) {
+        return set_err(ctx, f.st, f.msg);
+    }
+    cudaError_t e = fr::launch_dopri5(ctx->dev, u, dt, nsteps, atol, rtol, err, (cudaStream_t)stream);
+    return e == cudaSuccess ? FR_OK : set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+}
+
 fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream) {
     fr_status s = check_dev(ctx);
     if (s != FR_OK) return s;

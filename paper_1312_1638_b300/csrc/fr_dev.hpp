@@ -44,6 +44,8 @@ struct DevBlock {
     void* stage = nullptr;     // device staging for fr_rhs_host: [nupts][nvars][ld]
     void* rk_acc = nullptr;    // RK4 registers
     void* rk_tmp = nullptr;
+    void* dp_k = nullptr;          // DOPRI5: 7 slope arrays, one state size apart
+    void* dp_y = nullptr;          // DOPRI5: stage input / new solution
 };
 
 struct DevPairGroup {          // interior pairs between block bL and block bR
@@ -112,6 +114,9 @@ cudaError_t launch_rk4_adjoint(DevCtx& c, void* const* u0, void* const* lam, dou
                                const std::vector<std::vector<void*>>& tmp, cudaStream_t st);
 // classical RK4, nsteps steps of dt, in place on u
 cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st);
+cudaError_t launch_euler(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st);
+cudaError_t launch_dopri5(DevCtx& c, void* const* u, double dt, int nsteps, double atol, double rtol, double* err,
+                          cudaStream_t st);
 // FP64 weighted totals per variable
 cudaError_t launch_sum_weighted(DevCtx& c, void* const* u, double* host_out, cudaStream_t st);
 cudaError_t launch_check_finite(DevCtx& c, void* const* u, cudaStream_t st);

@@ -7,6 +7,8 @@
 //
 // State layout is SoA (Sec. 3.3): [points][nvars][ld], so every operator
 // product is C[M x N] = A[M x K] B[K x N] with N = nvars * ld columns.
+#include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 
@@ -815,6 +817,178 @@ static cudaError_t rk4_impl(DevCtx& c, void* const* u, double dt, int nsteps, cu
 
 cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {
     return c.precision == 0 ? rk4_impl<double>(c, u, dt, nsteps, st) : rk4_impl<float>(c, u, dt, nsteps, st);
+}
+
+// ------------------------------------------------------------------ Euler / DOPRI5
+// forward Euler stage: u += dt k, with the energy-split correction k_E += h_ref k_rho
+template <typename T>
+__global__ void euler_point_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, const T* __restrict__ k,
+                                   T* __restrict__ u, T dt, T href) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    const int64_t base = (int64_t)s * nvars * ld + n;
+    T kk[5];
+    for (int a = 0; a < nvars; ++a) kk[a] = k[base + a * ld];
+    kk[nvars - 1] += href * kk[0];
+    for (int a = 0; a < nvars; ++a) u[base + a * ld] += dt * kk[a];
+}
+
+struct Coef7 {
+    double c[7];
+    const void* k[7];
+};
+
+// y = u + sum_j c_j k_j over nk slopes (slopes already carry the energy-split correction)
+template <typename T>
+__global__ void lincomb_point_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, const T* __restrict__ u,
+                                     T* __restrict__ y, Coef7 cf, int nk) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    const int64_t base = (int64_t)s * nvars * ld + n;
+    for (int a = 0; a < nvars; ++a) {
+        const int64_t i = base + a * ld;
+        T v = u[i];
+        for (int j = 0; j < nk; ++j) v += T(cf.c[j]) * ((const T*)cf.k[j])[i];
+        y[i] = v;
+    }
+}
+
+// sum over real entries of (e / (atol + rtol max(|u0|, |u1|)))^2, e = sum_j d_j k_j,
+// block-reduced in FP64 and added to *acc
+template <typename T>
+__global__ void dp_err_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, const T* __restrict__ u0,
+                              const T* __restrict__ u1, Coef7 cf, double atol, double rtol, double* acc) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    double sum = 0.0;
+    if (n < nelem) {
+        const int64_t base = (int64_t)s * nvars * ld + n;
+        for (int a = 0; a < nvars; ++a) {
+            const int64_t i = base + a * ld;
+            double e = 0.0;
+            for (int j = 0; j < 7; ++j) e += cf.c[j] * (double)((const T*)cf.k[j])[i];
+            const double sc = atol + rtol * fmax(fabs((double)u0[i]), fabs((double)u1[i]));
+            sum += (e / sc) * (e / sc);
+        }
+    }
+    __shared__ double red[128];
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(acc, red[0]);
+}
+
+template <typename T>
+static cudaError_t euler_impl(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {
+    std::vector<void*> k(c.blocks.size());
+    for (size_t b = 0; b < c.blocks.size(); ++b) k[b] = c.blocks[b].rk_tmp;
+    for (int step = 0; step < nsteps; ++step) {
+        cudaError_t e = launch_rhs_nofix(c, u, k.data(), st);
+        if (e != cudaSuccess) return e;
+        for (size_t b = 0; b < c.blocks.size(); ++b) {
+            DevBlock& B = c.blocks[b];
+            prof_begin(c, K_RK_STAGE, st);
+            euler_point_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                B.nupts, B.nvars, B.nelem, B.ld, (const T*)k[b], (T*)u[b], T(dt), T(c.prm.ref_h));
+            prof_end(c, st);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euler(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {
+    return c.precision == 0 ? euler_impl<double>(c, u, dt, nsteps, st) : euler_impl<float>(c, u, dt, nsteps, st);
+}
+
+// Dormand-Prince 5(4) tableau (A strictly lower, row 7 = b), b and the embedded 4th-order bs
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+static const double DP_B[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
+static const double DP_BS[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100,
+                                1.0 / 40};
+
+template <typename T>
+static cudaError_t dopri5_impl(DevCtx& c, void* const* u, double dt, int nsteps, double atol, double rtol,
+                               double* err, cudaStream_t st) {
+    const size_t nb = c.blocks.size();
+    // slope slots (rotated so that the last slope of a step is the first of the next)
+    std::vector<std::array<void*, 7>> ks(nb);
+    std::vector<void*> y(nb), kv(nb);
+    for (size_t b = 0; b < nb; ++b) {
+        DevBlock& B = c.blocks[b];
+        const size_t S = (size_t)B.nupts * B.nvars * B.ld * sizeof(T);
+        for (int j = 0; j < 7; ++j) ks[b][j] = (char*)B.dp_k + j * S;
+        y[b] = B.dp_y;
+    }
+    auto slot = [&](int j) {
+        for (size_t b = 0; b < nb; ++b) kv[b] = ks[b][j];
+        return kv.data();
+    };
+    cudaError_t e;
+    for (int step = 0; step < nsteps; ++step) {
+        if (step == 0 && (e = launch_rhs(c, u, slot(0), st)) != cudaSuccess) return e;
+        for (int i = 1; i < 7; ++i) {
+            for (size_t b = 0; b < nb; ++b) {
+                DevBlock& B = c.blocks[b];
+                Coef7 cf{};
+                for (int j = 0; j < i; ++j) {
+                    cf.c[j] = dt * DP_A[i][j];
+                    cf.k[j] = ks[b][j];
+                }
+                prof_begin(c, K_RK_STAGE, st);
+                lincomb_point_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                    B.nupts, B.nvars, B.nelem, B.ld, (const T*)u[b], (T*)y[b], cf, i);
+                prof_end(c, st);
+            }
+            if ((e = launch_rhs(c, y.data(), slot(i), st)) != cudaSuccess) return e;
+        }
+        // y holds the 5th-order solution; error estimate of the last step before u is overwritten
+        if (err && step == nsteps - 1) {
+            if ((e = cudaMemsetAsync(c.partial, 0, sizeof(double), st)) != cudaSuccess) return e;
+            for (size_t b = 0; b < nb; ++b) {
+                DevBlock& B = c.blocks[b];
+                Coef7 cf{};
+                for (int j = 0; j < 7; ++j) {
+                    cf.c[j] = dt * (DP_B[j] - DP_BS[j]);
+                    cf.k[j] = ks[b][j];
+                }
+                dp_err_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                    B.nupts, B.nvars, B.nelem, B.ld, (const T*)u[b], (const T*)y[b], cf, atol, rtol, c.partial);
+            }
+        }
+        for (size_t b = 0; b < nb; ++b) {
+            DevBlock& B = c.blocks[b];
+            const size_t S = (size_t)B.nupts * B.nvars * B.ld * sizeof(T);
+            if ((e = cudaMemcpyAsync(u[b], y[b], S, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+            std::swap(ks[b][0], ks[b][6]);               // first same as last
+        }
+    }
+    if (err) {
+        double sum = 0.0;
+        if ((e = cudaMemcpyAsync(&sum, c.partial, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        double cnt = 0.0;
+        for (auto& B : c.blocks) cnt += (double)B.nupts * B.nvars * B.nelem;
+        *err = nsteps > 0 ? std::sqrt(sum / cnt) : 0.0;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dopri5(DevCtx& c, void* const* u, double dt, int nsteps, double atol, double rtol, double* err,
+                          cudaStream_t st) {
+    return c.precision == 0 ? dopri5_impl<double>(c, u, dt, nsteps, atol, rtol, err, st)
+                            : dopri5_impl<float>(c, u, dt, nsteps, atol, rtol, err, st);
 }
 
 cudaError_t launch_sum_weighted(DevCtx& c, void* const* u, double* out, cudaStream_t st) {

@@ -27,7 +27,8 @@ STATUS_NAMES = ["FR_OK", "FR_ERR_ARG", "FR_ERR_MESH", "FR_ERR_CUDA", "FR_ERR_NON
 EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pairs", "fr_rhs",
            "fr_rhs_host", "fr_rk4", "fr_sum_weighted", "fr_sync_status", "fr_check_finite",
            "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read",
-           "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint", "fr_set_option", "fr_fma_peak"]
+           "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint", "fr_set_option", "fr_fma_peak",
+           "fr_euler", "fr_dopri5"]
 
 
 class FRError(RuntimeError):
@@ -119,6 +120,44 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(stream.cuda_stream)
+
+
+def adaptive_dopri5(step, save, restore, t_end, dt0, safety=0.9, facmin=0.2, facmax=10.0, max_steps=100000):
+    """Step-size control for an embedded 5(4) pair (host logic).
+
+    step(dt) advances the state by one DOPRI5 step and returns the scaled
+    error norm of that step; save() / restore() keep and put back the state
+    before a step, so that a rejected step (norm > 1) leaves no trace.  After
+    each step dt is multiplied by a proportional-integral factor
+    safety * err^(-0.17) * err_prev^(0.04) (accepted) or safety * err^(-1/5)
+    (rejected), clamped to [facmin, facmax].  The paper names DOPRI5 without a
+    controller (Sec. 3); the gains are those Hairer and Wanner recommend for
+    this pair (Solving ODEs I, Sec. II.4).  Returns dict(t, accepted=[dt...],
+    rejected=n)."""
+    t, dt, prev = 0.0, float(dt0), 1e-4
+    acc, rej = [], 0
+    while t < t_end * (1 - 1e-14):
+        if len(acc) + rej >= max_steps:
+            raise RuntimeError(f"adaptive DOPRI5: {max_steps} steps without reaching t_end")
+        h = min(dt, t_end - t)
+        save()
+        err = float(step(h))
+        if not np.isfinite(err):
+            restore()
+            rej += 1
+            dt = h * facmin
+            continue
+        if err <= 1.0:
+            t += h
+            acc.append(h)
+            fac = safety * max(err, 1e-10) ** (-0.17) * prev ** 0.04
+            prev = max(err, 1e-4)
+        else:
+            restore()
+            rej += 1
+            fac = safety * err ** (-1.0 / 5)
+        dt = h * min(facmax, max(facmin, fac))
+    return dict(t=t, accepted=acc, rejected=rej)
 
 
 def fma_peak(device=0):
@@ -266,6 +305,37 @@ class Solver:
 
     def rk4(self, u, dt, nsteps, stream=None):
         self._check(self.lib.fr_rk4(self.ctx, _ptrs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+
+    def euler(self, u, dt, nsteps, stream=None):
+        """nsteps forward Euler steps in place."""
+        self._check(self.lib.fr_euler(self.ctx, _ptrs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+
+    def dopri5(self, u, dt, nsteps, atol=1e-6, rtol=1e-6, error=False, stream=None):
+        """nsteps fixed DOPRI5 steps in place; with error=True returns the
+        scaled RMS norm of the last step's embedded error estimate (synchronises)."""
+        e = C.c_double(0.0)
+        self._check(self.lib.fr_dopri5(self.ctx, _ptrs(u), C.c_double(dt), nsteps, C.c_double(atol),
+                                       C.c_double(rtol), C.byref(e) if error else None, _stream_ptr(stream)))
+        return e.value if error else None
+
+    def dopri5_adaptive(self, u, t_end, dt0, atol=1e-6, rtol=1e-6, stream=None, **ctl):
+        """Integrate u in place from 0 to t_end with error-controlled DOPRI5
+        steps (see `adaptive_dopri5`); returns its record."""
+        import torch
+        backup = [torch.empty_like(x) for x in u]
+
+        def step(dt):
+            return self.dopri5(u, dt, 1, atol, rtol, error=True, stream=stream)
+
+        def save():
+            for b, x in zip(backup, u):
+                b.copy_(x)
+
+        def restore():
+            for b, x in zip(backup, u):
+                x.copy_(b)
+
+        return adaptive_dopri5(step, save, restore, t_end, dt0, **ctl)
 
     def adjoint_rhs(self, u, lam, out, stream=None):
         """out = (dR/du)^T lam (Euler)."""
