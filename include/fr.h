@@ -110,7 +110,16 @@ typedef struct {
      * accurate at low Mach number, where u and the fluxes are dominated by
      * constants whose divergence vanishes. */
     double ref_rho, ref_p;
+    /* Correction functions (Sec. 5.1 runs "DG, SD and HU as defined in"
+     * Vincent, Castonguay and Jameson 2011): the VCJH family
+     * g_R = (P_p + (eta P_{p-1} + P_{p+1}) / (1 + eta)) / 2 with eta = 0 (DG),
+     * p/(p+1) (SD) or (p+1)/p (HU).  SD and HU are defined for quadrilaterals
+     * and hexahedra; a mesh with triangles accepts DG only
+     * (FR_ERR_UNSUPPORTED otherwise). */
+    int32_t correction;   /* fr_correction */
 } fr_params;
+
+typedef enum { FR_CORR_DG = 0, FR_CORR_SD = 1, FR_CORR_HU = 2 } fr_correction;
 
 /* One block of elements of a single type, host memory, read during fr_setup only. */
 typedef struct {
@@ -319,7 +328,7 @@ void fr_destroy(fr_ctx* ctx);
 fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops);
 
 /* ABI version (increments on any signature change). */
-int32_t fr_version(void);   /* 2 */
+int32_t fr_version(void);   /* 3 */
 
 #ifdef __cplusplus
 }

@@ -253,7 +253,7 @@ void ctx_set_error(fr_ctx* c, const char* msg) {
 // ====================================================================== ABI
 extern "C" {
 
-int32_t fr_version(void) { return 2; }
+int32_t fr_version(void) { return 3; }
 
 fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops) {
     if (!fp32_tflops || !fp64_tflops) return FR_ERR_ARG;
@@ -305,7 +305,9 @@ fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx
             if (!cache.count(et)) {
                 std::unique_ptr<fr::ElemType> el(new fr::ElemType());
                 std::string err;
-                if (!fr::build_element(et, prm->order, *el, err)) throw Fail{FR_ERR_ARG, err};
+                if (et == FR_TRI && prm->correction != FR_CORR_DG)
+                    throw Fail{FR_ERR_UNSUPPORTED, "SD / HU correction functions are defined for quads and hexes only"};
+                if (!fr::build_element(et, prm->order, *el, err, prm->correction)) throw Fail{FR_ERR_ARG, err};
                 cache[et] = el.get();
                 c->etypes.push_back(std::move(el));
             }

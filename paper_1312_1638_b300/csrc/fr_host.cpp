@@ -6,10 +6,12 @@
 //     through the Gauss-Legendre points (the Vandermonde construction of Sec. 2
 //     with a tensor Lagrange spanning set gives exactly this); for triangles a
 //     monomial Vandermonde matrix inverted by Gauss-Jordan elimination;
-//   * DG correction functions: for tensor elements the derivative of the right
-//     Radau polynomial g_R = (P_p + P_{p+1})/2 times the tangential Lagrange
-//     factors; for triangles the lift of the face Lagrange polynomial through
-//     the exact (collapsed-Gauss) mass matrix;
+//   * correction functions: for tensor elements the derivative of the right
+//     VCJH correction function g_R = (P_p + (eta P_{p-1} + P_{p+1})/(1+eta))/2
+//     (eta = 0: DG, the right Radau polynomial; p/(p+1): SD; (p+1)/p: HU)
+//     times the tangential Lagrange factors; for triangles (DG only) the lift
+//     of the face Lagrange polynomial through the exact (collapsed-Gauss)
+//     mass matrix;
 //   * metric terms from the Lagrange shape functions of each element.
 #include "fr_host.hpp"
 
@@ -195,8 +197,11 @@ void ElemType::nodal(const ldbl* x, ldbl* val, ldbl* grad) const {
     }
 }
 
-bool build_element(int et, int p, ElemType& el, std::string& err) {
+bool build_element(int et, int p, ElemType& el, std::string& err, int correction) {
     if (p < 1 || p > 10) { err = "order must be in [1, 10]"; return false; }
+    if (correction < 0 || correction > 2) { err = "correction must be 0 (DG), 1 (SD) or 2 (HU)"; return false; }
+    if (et == ET_TRI && correction != 0) { err = "SD / HU correction functions need a tensor element"; return false; }
+    const ldbl eta = correction == 0 ? 0.0L : correction == 1 ? (ldbl)p / (p + 1) : (ldbl)(p + 1) / p;
     el = ElemType();
     el.etype = et; el.p = p;
     el.ndims = ndims_of(et);
@@ -276,10 +281,11 @@ bool build_element(int et, int p, ElemType& el, std::string& err) {
             for (int i = 0; i < d; ++i) if (fabsl(fn[s * d + i]) > 0.5L) ax = i;
             ldbl sg = fn[s * d + ax] > 0 ? 1 : -1;
             for (int r = 0; r < nu; ++r) {
-                ldbl xs = sg * up[r * d + ax], p0, d0, p1, d1;
+                ldbl xs = sg * up[r * d + ax], p0, d0, p1, d1, pm, dm;
                 legendre_pd(p, xs, p0, d0);
                 legendre_pd(p + 1, xs, p1, d1);
-                ldbl v = 0.5L * (d0 + d1);
+                legendre_pd(p - 1, xs, pm, dm);
+                ldbl v = 0.5L * (d0 + (eta * dm + d1) / (1.0L + eta));   // g_R'(xs)
                 for (int k = 0; k < d; ++k) {
                     if (k == ax) continue;
                     ldbl L[16];

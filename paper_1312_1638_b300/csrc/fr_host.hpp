@@ -37,7 +37,8 @@ struct ElemType {
     void nodal(const long double* x, long double* val, long double* grad) const;
 };
 
-bool build_element(int etype, int p, ElemType& el, std::string& err);
+// correction: 0 = DG, 1 = SD, 2 = HU (VCJH eta = 0, p/(p+1), (p+1)/p; tensor elements)
+bool build_element(int etype, int p, ElemType& el, std::string& err, int correction = 0);
 
 // Reference coordinates of the centre of face f and the map from face
 // parameters (t) or (a, b) to reference coordinates.

@@ -128,6 +128,23 @@ def test_rhs_single_precision_matches_oracle(torch, name, prec):
     assert s.sync_status() == fr.OK                      # no bounded wait gave up
 
 
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("corr", ["sd", "hu"])
+@pytest.mark.parametrize("name", ["quad_ns_p3_jitter_ragged", "hex_euler_p4", "hex_ns_p3_tgv"])
+def test_rhs_sd_hu_corrections_match_oracle(torch, name, corr, prec):
+    """SD and HU correction functions (VCJH family, Sec. 5.1) on tensor elements."""
+    from paper_1312_1638_b300 import fr
+    m, p, system, st, prm = _case_solver(fr, name, prec)
+    o = FRSystem(m, p, system, correction=corr, **prm)
+    U = oracle_state(o, st)
+    if prec != "fp64":
+        U = [u.astype(np.float32).astype(np.float64) for u in U]
+    R, S = o.rhs(U, scale=True)
+    s = fr.Solver(m, p, system, prec, device=0, correction=corr, **prm, **mean_ref(U))
+    check(gpu_rhs(torch, s, U), R, S, prec)
+    assert s.sync_status() == fr.OK
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_rhs_mixed_mesh_with_boundaries(torch, prec):
     from paper_1312_1638_b300 import fr

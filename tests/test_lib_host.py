@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol(fr):
     for n in names:
         assert hasattr(lib, n), n
     assert set(names) == set(fr.EXPORTS)
-    assert fr.load().fr_version() == 2
+    assert fr.load().fr_version() == 3
 
 
 CASES = [("quad", 3, 1, 0.1), ("quad", 3, 4, 0.1), ("hex", 2, 2, 0.1), ("hex", 2, 4, 0.0)]
@@ -42,6 +42,25 @@ def test_operators_and_points_match_oracle(fr, etype, n, p, jit):
                      (7, el.M4 - el.M6 @ el.M0), (8, el.M1 - el.M3 @ el.M2)]:
         assert np.allclose(s.operator(0, which), M, atol=1e-12), which
     assert np.allclose(s.solution_points(0), o.solution_coords(0), atol=1e-13)
+
+
+@pytest.mark.parametrize("corr", ["sd", "hu"])
+@pytest.mark.parametrize("etype,p", [("quad", 1), ("quad", 4), ("hex", 2), ("hex", 3)])
+def test_vcjh_operators_match_oracle(fr, etype, p, corr):
+    m = periodic_box(etype, 2, 0.0, 1.0, jitter=0.1, seed=1)
+    s = fr.Solver(m, p, "ns", "fp64", device=-1, correction=corr)
+    el = FRSystem(m, p, "ns", correction=corr).eles[0]
+    for which, M in [(3, el.M3), (6, el.M6), (7, el.M4 - el.M6 @ el.M0), (8, el.M1 - el.M3 @ el.M2)]:
+        assert np.allclose(s.operator(0, which), M, atol=1e-12), which
+    assert not np.allclose(s.operator(0, 3), FRSystem(m, p, "ns").eles[0].M3)
+
+
+def test_vcjh_on_triangles_is_unsupported(fr):
+    from fr_inputs import annulus_mixed
+    m = annulus_mixed(ntheta=12, nr_quad=2, nr_tri=2, r0=0.5, r1=3.0, jitter=0.0, seed=1)
+    with pytest.raises(fr.FRError) as e:
+        fr.Solver(m, 2, "euler", "fp64", device=-1, correction="sd")
+    assert e.value.status == fr.ERR_UNSUPPORTED
 
 
 def _pair_set(rows):
