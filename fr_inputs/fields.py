@@ -123,3 +123,23 @@ def smooth_random(x, gamma=1.4, amp=0.1, nmodes=6, seed=0, rho0=1.0, p0=1.0, vel
     vel = [vel0[d] + amp * s() for d in range(ndims)]
     p = p0 * (1.0 + amp * s())
     return conserved(rho, vel, p, gamma)
+
+
+def couette(x, gamma=1.4, prandtl=0.72, cpTw=1005.0 * 300.0, vw=69.445, p=1e5, h=1.0):
+    """Steady compressible Couette flow between isothermal plates at y = 0
+    (at rest) and y = h (moving at vw along x), constant viscosity (Sec. 5.2):
+    rho = gamma/(gamma-1) 2p / (2 C_pT_w + Pr vw^2 phi (1 - phi)), v = vw phi x,
+    p constant, phi = y / h."""
+    phi = x[1] / h
+    rho = gamma / (gamma - 1.0) * 2.0 * p / (2.0 * cpTw + prandtl * vw ** 2 * phi * (1.0 - phi))
+    zero = 0.0 * phi
+    return conserved(rho, [vw * phi, zero], p + zero, gamma)
+
+
+def couette_mean_density(gamma=1.4, prandtl=0.72, cpTw=1005.0 * 300.0, vw=69.445, p=1e5, n=64):
+    """<rho(phi)> over phi in [0, 1] (Gauss-Legendre), the constant initial
+    density of the Couette runs (Sec. 5.2)."""
+    t, w = np.polynomial.legendre.leggauss(n)
+    phi = 0.5 * (t + 1.0)
+    rho = gamma / (gamma - 1.0) * 2.0 * p / (2.0 * cpTw + prandtl * vw ** 2 * phi * (1.0 - phi))
+    return float(0.5 * np.sum(w * rho))

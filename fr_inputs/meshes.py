@@ -188,3 +188,58 @@ def single_element(etype: str, nodes: np.ndarray) -> Mesh:
     bfaces = np.asarray([(0, 0, f, 0) for f in range(nf)], np.int64)
     return Mesh(ndims, [Block(etype, np.asarray(nodes, np.float64)[None])], bfaces,
                 np.zeros((0, ndims)))
+
+
+def channel_mixed(nx: int, ny: int, lx: float = 1.0, h: float = 1.0, tri_rows: int = -1,
+                  jitter: float = 0.0, seed: int = 0) -> Mesh:
+    """Channel [0, lx] x [0, h], periodic in x, walls at y = 0 and y = h.
+
+    nx x ny cells; the lower rows are 4-node quads and the upper ``tri_rows``
+    rows (default: half of them) are cells split into two 3-node triangles on a
+    seeded random diagonal, a mixed mesh like the paper's Couette meshes
+    (Sec. 5.2; those meshes are not published).  Interior nodes move by
+    U(-jitter, jitter) times the cell size (periodic-consistently in x; wall
+    rows only along x).  Bottom faces are no-slip isothermal walls (bctype 2),
+    top faces the second wall type (bctype 3, the moving plate).
+    """
+    rng = np.random.default_rng(seed)
+    if tri_rows < 0:
+        tri_rows = ny // 2
+    dx, dy = lx / nx, h / ny
+    X, Y = np.meshgrid(dx * np.arange(nx + 1), dy * np.arange(ny + 1), indexing="ij")
+    jx = rng.uniform(-jitter, jitter, size=(nx, ny + 1)) * dx
+    jy = rng.uniform(-jitter, jitter, size=(nx, ny + 1)) * dy
+    jy[:, 0] = jy[:, -1] = 0.0
+    jx = np.concatenate([jx, jx[:1]], axis=0)                 # node nx is the image of node 0
+    jy = np.concatenate([jy, jy[:1]], axis=0)
+    P = np.stack([X + jx, Y + jy], axis=-1)                   # [nx+1, ny+1, 2]
+    P[nx, :, 0] = P[0, :, 0] + lx
+    quads, tris, bq, bt = [], [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            c00, c10, c01, c11 = P[i, j], P[i + 1, j], P[i, j + 1], P[i + 1, j + 1]
+            if j < ny - tri_rows:
+                if j == 0:
+                    bq.append((len(quads), 0, 2))             # eta = -1 face on y = 0
+                if j == ny - 1:
+                    bq.append((len(quads), 2, 3))             # eta = +1 face on y = h
+                quads.append([c00, c10, c01, c11])
+            else:
+                if rng.random() < 0.5:
+                    t1, t2 = [c00, c10, c11], [c00, c11, c01]
+                else:
+                    t1, t2 = [c00, c10, c01], [c10, c11, c01]
+                if j == 0:
+                    bt.append((len(tris), 0, 2))              # edge v0 v1 of t1 on y = 0
+                tris.append(t1)
+                if j == ny - 1:
+                    bt.append((len(tris), 1, 3))              # edge v1 v2 of t2 on y = h
+                tris.append(t2)
+    blocks, bf = [], []
+    if quads:
+        blocks.append(Block("quad", np.asarray(quads, np.float64)))
+        bf += [(0, e, f, t) for e, f, t in bq]
+    if tris:
+        blocks.append(Block("tri", np.asarray(tris, np.float64)))
+        bf += [(len(blocks) - 1, e, f, t) for e, f, t in bt]
+    return Mesh(2, blocks, np.asarray(bf, np.int64).reshape(-1, 4), np.array([[lx, 0.0]]))

@@ -107,7 +107,7 @@ def ldg_viscous_normal(fvL, fvR, n, beta):
 
 
 # ---------------------------------------------------------------- boundaries
-BC_INFLOW, BC_OUTFLOW, BC_WALL = 0, 1, 2
+BC_INFLOW, BC_OUTFLOW, BC_WALL, BC_WALL2 = 0, 1, 2, 3
 
 
 def ghost_states(btype, uL, qL, prm):
@@ -136,9 +136,11 @@ def ghost_states(btype, uL, qL, prm):
         g[nd + 1] = prm["outflow_p"] / (gamma - 1.0) + 0.5 * rho * sum(vi * vi for vi in v)
         qg = None if qL is None else np.zeros_like(qL)
         return g, g, qg
-    if btype == BC_WALL:
+    if btype in (BC_WALL, BC_WALL2):
+        # BC_WALL2: a second isothermal wall (same C_p T_w) moving at wall2_v,
+        # e.g. the moving plate of Couette flow (Sec. 5.2)
         rho, v, _ = primitives(uL, gamma)
-        vw = prm["wall_v"][:nd]
+        vw = prm["wall_v" if btype == BC_WALL else "wall2_v"][:nd]
         cpTw = prm["wall_cpTw"]
         gi = np.empty_like(uL)
         vm = [2.0 * vw[i] - v[i] for i in range(nd)]

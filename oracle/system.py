@@ -43,7 +43,7 @@ EULER, NAVIER_STOKES = "euler", "ns"
 
 DEFAULTS = dict(gamma=1.4, mu=0.0, prandtl=0.72, ldg_beta=0.5, ldg_tau=0.1,
                 bc_rho=1.0, bc_v=(1.0, 0.0, 0.0), bc_p=1.0, outflow_p=1.0,
-                wall_cpTw=1.0, wall_v=(0.0, 0.0, 0.0))
+                wall_cpTw=1.0, wall_v=(0.0, 0.0, 0.0), wall2_v=(0.0, 0.0, 0.0))
 
 
 class FRSystem:

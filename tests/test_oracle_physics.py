@@ -134,6 +134,14 @@ def test_ghost_states_read_back():
     # both ghosts sit at the wall temperature: C_p T = gamma/(gamma-1) p/rho
     assert np.allclose(G / (G - 1) * pi / ri, 3.0) and np.allclose(G / (G - 1) * pl / rl, 3.0)
     assert np.array_equal(qg, q)
+    # the second wall type moves at wall2_v at the same temperature
+    prm2 = dict(prm, wall2_v=(-0.5, 0.3, 0.0))
+    gi, gl, qg = ph.ghost_states(ph.BC_WALL2, uL, q, prm2)
+    ri, vi, pi = ph.primitives(gi, G)
+    rl, vl, pl = ph.primitives(gl, G)
+    assert np.allclose(0.5 * (vi[0] + v0[0]), -0.5) and np.allclose(0.5 * (vi[1] + v0[1]), 0.3)
+    assert np.allclose(vl[0], -0.5) and np.allclose(vl[1], 0.3)
+    assert np.allclose(G / (G - 1) * pl / rl, 3.0) and np.array_equal(qg, q)
 
 
 @pytest.mark.parametrize("etype,nn", [("quad", 4), ("quad", 9), ("tri", 3), ("tri", 6), ("hex", 8)])
