@@ -79,8 +79,10 @@ typedef enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 } fr_system;
 typedef enum { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1, FR_PREC_BF16X3 = 2, FR_PREC_TF32X3 = 3 } fr_precision;
 typedef enum { FR_QUAD = 0, FR_TRI = 1, FR_HEX = 2 } fr_etype;
 /* boundary types (App. C): free-stream ("supersonic inflow") ghost, subsonic
- * outflow, no-slip isothermal wall */
-typedef enum { FR_BC_FREESTREAM = 0, FR_BC_OUTFLOW = 1, FR_BC_WALL = 2 } fr_bctype;
+ * outflow, no-slip isothermal wall (velocity wall_v), and a second no-slip
+ * isothermal wall at the same C_pT_w moving at wall2_v (the moving plate of
+ * the Couette problem, Sec. 5.2) */
+typedef enum { FR_BC_FREESTREAM = 0, FR_BC_OUTFLOW = 1, FR_BC_WALL = 2, FR_BC_WALL_MOVING = 3 } fr_bctype;
 
 /* Physical and numerical parameters (Sec. 4, Sec. 4.3, App. C). */
 typedef struct {
@@ -117,6 +119,7 @@ typedef struct {
      * and hexahedra; a mesh with triangles accepts DG only
      * (FR_ERR_UNSUPPORTED otherwise). */
     int32_t correction;   /* fr_correction */
+    double wall2_v[3];    /* velocity of FR_BC_WALL_MOVING faces */
 } fr_params;
 
 typedef enum { FR_CORR_DG = 0, FR_CORR_SD = 1, FR_CORR_HU = 2 } fr_correction;
@@ -328,7 +331,7 @@ void fr_destroy(fr_ctx* ctx);
 fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops);
 
 /* ABI version (increments on any signature change). */
-int32_t fr_version(void);   /* 3 */
+int32_t fr_version(void);   /* 4 */
 
 #ifdef __cplusplus
 }

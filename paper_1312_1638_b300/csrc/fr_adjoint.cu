@@ -134,12 +134,13 @@ struct EulerAdj {
             for (int i = 0; i < D; ++i) { g[1 + i] = uL[1 + i]; ke += uL[1 + i] * uL[1 + i]; }
             g[D + 1] = T(P.outflow_p) / gm1 + T(0.5) * ke / uL[0];
         } else {
+            const double* wv = bctype == 3 ? P.wall2_v : P.wall_v;
             const T rho = uL[0], rinv = T(1) / rho;
             T k1 = T(0);
             g[0] = rho;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                T w = T(2) * T(P.wall_v[i]) - uL[1 + i] * rinv;
+                T w = T(2) * T(wv[i]) - uL[1 + i] * rinv;
                 g[1 + i] = rho * w;
                 k1 += w * w;
             }
@@ -159,13 +160,14 @@ struct EulerAdj {
             for (int k = 0; k < D; ++k) c[1 + k] += b[1 + k] + v[k] * b[D + 1];
             return;
         }
+        const double* vwall = bctype == 3 ? P.wall2_v : P.wall_v;
         T w[D], w2 = T(0), wv = T(0), bm = T(0);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            w[i] = T(2) * T(P.wall_v[i]) - v[i];
+            w[i] = T(2) * T(vwall[i]) - v[i];
             w2 += w[i] * w[i];
             wv += w[i] * v[i];
-            bm += T(2) * T(P.wall_v[i]) * b[1 + i];
+            bm += T(2) * T(vwall[i]) * b[1 + i];
         }
         c[0] += b[0] + bm + (T(P.wall_cpTw) / T(P.gamma) + T(0.5) * w2 + wv) * b[D + 1];
 #pragma unroll

@@ -253,7 +253,7 @@ void ctx_set_error(fr_ctx* c, const char* msg) {
 // ====================================================================== ABI
 extern "C" {
 
-int32_t fr_version(void) { return 3; }
+int32_t fr_version(void) { return 4; }
 
 fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops) {
     if (!fp32_tflops || !fp64_tflops) return FR_ERR_ARG;
@@ -349,7 +349,11 @@ fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx
         P.ref_E = P.ref_p / (prm->gamma - 1.0);
         P.ref_h = prm->ref_rho > 0 ? prm->gamma * P.ref_E / prm->ref_rho : 0.0;
         P.bc_rho = prm->bc_rho; P.bc_p = prm->bc_p; P.outflow_p = prm->outflow_p; P.wall_cpTw = prm->wall_cpTw;
-        for (int i = 0; i < 3; ++i) { P.bc_v[i] = prm->bc_v[i]; P.wall_v[i] = prm->wall_v[i]; }
+        for (int i = 0; i < 3; ++i) {
+            P.bc_v[i] = prm->bc_v[i];
+            P.wall_v[i] = prm->wall_v[i];
+            P.wall2_v[i] = prm->wall2_v[i];
+        }
         if (device >= 0) {
             c->dev.device = device;
             upload_device(c.get());

@@ -11,7 +11,7 @@ namespace fr {
 // Physical / numerical parameters as passed to kernels (Sec. 4, App. C).
 struct DevParams {
     double gamma, mu, prandtl, beta, tau;
-    double bc_rho, bc_v[3], bc_p, outflow_p, wall_cpTw, wall_v[3];
+    double bc_rho, bc_v[3], bc_p, outflow_p, wall_cpTw, wall_v[3], wall2_v[3];
     // perturbation form: reference state at rest (all zero = plain form)
     double ref_rho, ref_E, ref_p, ref_h;
 };

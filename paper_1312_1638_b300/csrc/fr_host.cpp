@@ -642,7 +642,7 @@ bool pair_mesh(int d, const std::vector<HostBlock>& blocks, const int64_t* bface
     for (int64_t k = 0; k < nbfaces; ++k) {
         int64_t b = bfaces[4 * k], e = bfaces[4 * k + 1], f = bfaces[4 * k + 2], t = bfaces[4 * k + 3];
         if (b < 0 || b >= (int64_t)blocks.size() || e < 0 || e >= blocks[b].nelem || f < 0 ||
-            f >= blocks[b].el->nfaces || t < 0 || t > 2) {
+            f >= blocks[b].el->nfaces || t < 0 || t > 3) {
             err = "bad boundary face entry"; return false;
         }
         btype[foff[b] + e * blocks[b].el->nfaces + f] = (int32_t)t;

@@ -277,12 +277,14 @@ struct Gas {
             for (int a = 0; a < NV; ++a) gl[a] = gi[a];
             return false;
         }
+        // walls (types 2 and 3 differ only in their velocity)
+        const double* wv = bctype == 3 ? P.wall2_v : P.wall_v;
         T rinv = T(1) / rho, cpt = T(P.wall_cpTw / P.gamma), k1 = T(0), k2 = T(0);
         T e0 = T(P.ref_rho * P.wall_cpTw / P.gamma - P.ref_E);
         gi[0] = uL[0]; gl[0] = uL[0];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            T vw = T(P.wall_v[i]);
+            T vw = T(wv[i]);
             T vm = T(2) * vw - uL[1 + i] * rinv;
             gi[1 + i] = rho * vm; k1 += vm * vm;
             gl[1 + i] = rho * vw; k2 += vw * vw;

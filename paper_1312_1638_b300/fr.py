@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("ldg_beta", C.c_double), ("ldg_tau", C.c_double),
                 ("bc_rho", C.c_double), ("bc_v", C.c_double * 3), ("bc_p", C.c_double),
                 ("outflow_p", C.c_double), ("wall_cpTw", C.c_double), ("wall_v", C.c_double * 3),
-                ("ref_rho", C.c_double), ("ref_p", C.c_double), ("correction", C.c_int32)]
+                ("ref_rho", C.c_double), ("ref_p", C.c_double), ("correction", C.c_int32),
+                ("wall2_v", C.c_double * 3)]
 
 CORRECTIONS = {"dg": 0, "sd": 1, "hu": 2}
 
@@ -206,6 +207,8 @@ class Solver:
         p.ref_rho = params.get("ref_rho", 0.0)
         p.ref_p = params.get("ref_p", 0.0)
         p.correction = CORRECTIONS[params.get("correction", "dg")]
+        for i, v in enumerate(params.get("wall2_v", (0.0, 0.0, 0.0))):
+            p.wall2_v[i] = v
         self.params = p
         self._keep = []
         blocks = (EBlock * len(mesh.blocks))()

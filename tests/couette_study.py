@@ -1,0 +1,109 @@
+"""Couette-flow validation of the Navier-Stokes solver (Sec. 5.2) on the GPU.
+
+Setup as in the paper: plates at y = 0 (at rest) and y = H = 1 (moving at
+v_w = 69.445 m/s along x), isothermal at T_w = 300 K, gamma = 1.4, Pr = 0.72,
+mu = 0.417, C_p = 1005, p_c = 1e5 (Mach 0.2, Re 200), Rusanov, LDG
+beta = 1/2, tau = 0.1, DG correction functions, FP64.  Initial state:
+rho = <rho(phi)>, v = v_w x, p = p_c.  Every 0.1 time units the L2 energy
+error sigma(t)^2 = sum_e sum_j (E - E_exact)^2 J_j w_j (solution-point
+quadrature, through fr_sum_weighted) is evaluated; the run has converged at
+the first t with sigma(t) / sigma(t + 0.1) <= 1.01.  The paper's mixed meshes
+are not published: ``channel_mixed`` (quads below, split triangles above,
+jittered interior nodes, periodic in x) stands in for them.
+
+    python -m tests.couette_study      # the full table (p = 1..4, four meshes)
+"""
+
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+
+from fr_inputs import fields
+from fr_inputs.meshes import channel_mixed
+
+G, PR, MU, CP, TW, PC, VW, H = 1.4, 0.72, 0.417, 1005.0, 300.0, 1e5, 69.445, 1.0
+CPTW = CP * TW
+PRM = dict(gamma=G, mu=MU, prandtl=PR, ldg_beta=0.5, ldg_tau=0.1, wall_cpTw=CPTW,
+           wall_v=(0.0, 0.0, 0.0), wall2_v=(VW, 0.0, 0.0))
+
+
+def run(p, n, precision="fp64", cfl=0.3, t_max=5.0, jitter=0.1, seed=1):
+    """Steady Couette flow on channel_mixed(n, n); returns dict(sigma, t_inf, steps)."""
+    import torch
+    from paper_1312_1638_b300 import fr
+
+    m = channel_mixed(n, n, jitter=jitter, seed=seed)
+    rho0 = fields.couette_mean_density(G, PR, CPTW, VW, PC)
+    s = fr.Solver(m, p, "ns", precision, device=0, **PRM, ref_rho=rho0, ref_p=PC)
+    dt_np = torch.float64 if precision == "fp64" else torch.float32
+    u, ex = [], []
+    for b in range(len(m.blocks)):
+        L = s.layout(b)
+        X = s.solution_points(b)                                   # [ndims, nupts, nelem]
+        U0 = fields.uniform(X, rho0, (VW, 0.0), PC, G)            # [V, nupts, nelem]
+        Ue = fields.couette(X, G, PR, CPTW, VW, PC, H)
+        ub = torch.zeros((L["nupts"], L["nvars"], L["ld"]), dtype=dt_np, device="cuda")
+        ub[:, :, :L["nelem"]] = torch.from_numpy(U0.transpose(1, 0, 2)).to(dt_np)
+        u.append(ub)
+        ex.append(torch.from_numpy(Ue[-1]).to(dt_np).cuda())      # exact total energy [nupts, nelem]
+    h = H / n
+    c = np.sqrt(G * PC / rho0)
+    dt = cfl * h / ((c + VW) * (p + 1) ** 2)
+    nper = int(np.ceil(0.1 / dt))
+    dt = 0.1 / nper
+
+    def sigma():
+        err = []
+        for b, ub in enumerate(u):
+            L = s.layout(b)
+            e = torch.zeros_like(ub)
+            e[:, -1, :L["nelem"]] = (ub[:, -1, :L["nelem"]] - ex[b]) ** 2
+            err.append(e)
+        return float(np.sqrt(s.sum_weighted(err)[-1]))
+
+    prev, t, steps = sigma(), 0.0, 0
+    while t < t_max:
+        s.rk4(u, dt, nper)
+        t += 0.1
+        steps += nper
+        cur = sigma()
+        if not np.isfinite(cur):
+            raise FloatingPointError(f"Couette p={p} n={n}: non-finite state at t={t:.1f}")
+        if prev / cur <= 1.01:
+            break
+        prev = cur
+    s.check_finite(u)
+    assert s.sync_status() == fr.OK
+    s.close()
+    return dict(sigma=cur, t_inf=t, steps=steps, dt=dt, h=h)
+
+
+def order(hs, sigmas):
+    """Least-squares slope of log sigma against log h, with its standard error."""
+    x, y = np.log(hs), np.log(sigmas)
+    A = np.stack([x, np.ones_like(x)], 1)
+    coef, res, _, _ = np.linalg.lstsq(A, y, rcond=None)
+    dof = max(len(x) - 2, 1)
+    s2 = float(res[0]) / dof if res.size else 0.0
+    se = np.sqrt(s2 / np.sum((x - x.mean()) ** 2))
+    return float(coef[0]), float(se)
+
+
+def main(orders=(1, 2, 3, 4), meshes=(4, 6, 8, 12)):
+    print("| p | n x n cells | sigma(t_inf) | t_inf | RK4 steps |")
+    print("|---|---|---|---|---|")
+    for p in orders:
+        hs, sg = [], []
+        for n in meshes:
+            r = run(p, n)
+            hs.append(r["h"])
+            sg.append(r["sigma"])
+            print(f"| {p} | {n} x {n} | {r['sigma']:.4e} | {r['t_inf']:.1f} | {r['steps']} |", flush=True)
+        o, se = order(hs, sg)
+        print(f"| {p} | order | {o:.2f} +- {se:.2f} (expected {p + 1}) | | |", flush=True)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -32,6 +32,11 @@ def _case(kind):
     if kind == "hex":
         m = periodic_box("hex", 3, 0.0, 2 * np.pi, jitter=0.1, seed=1)
         p, prm = 3, dict(gamma=1.4)
+    elif kind == "channel":
+        # walls at rest below and moving above (boundary types 2 and 3)
+        from fr_inputs.meshes import channel_mixed
+        m = channel_mixed(4, 4, jitter=0.1, seed=5)
+        p, prm = 2, dict(gamma=1.4, wall_cpTw=3.5, wall_v=(0.1, 0.0, 0.0), wall2_v=(0.7, -0.05, 0.0))
     else:
         m = annulus_mixed(ntheta=16, nr_quad=2, nr_tri=2, r0=0.5, r1=3.0, jitter=0.05, seed=3)
         m.bfaces[(m.bfaces[:, 0] == 1) & (m.bfaces[:, 1] % 2 == 0), 3] = 1
@@ -42,7 +47,7 @@ def _case(kind):
     return m, p, prm, o, U
 
 
-@pytest.mark.parametrize("kind", ["hex", "mixed"])
+@pytest.mark.parametrize("kind", ["hex", "mixed", "channel"])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5), ("tf32x3", 2e-5)])
 def test_adjoint_rhs_matches_oracle(torch, kind, prec, tol):
     from paper_1312_1638_b300 import fr
