@@ -330,6 +330,53 @@ void fr_destroy(fr_ctx* ctx);
  */
 fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops);
 
+/*
+ * Partitioned right-hand side (Sec. 3.6: the element set split between ranks,
+ * with "int" kernels on pairs inside a partition and "mpi" kernels on pairs
+ * whose other side lives on another rank, fed by an exchange of the
+ * flux-point values of those pairs).
+ *
+ * fr_setup_part builds the context of partition `rank` of the mesh: part has
+ * one entry per element, block-major (all elements of block 0, then block 1,
+ * ...), with values in [0, nparts); the context holds the elements of its
+ * rank (in increasing global order within each block; every block must keep
+ * at least one element, else FR_ERR_ARG), the pairs and boundary faces among
+ * them, and for every neighbour rank the pairs shared with it, in exchange
+ * slots: first the pairs whose global L side (the same L as in fr_setup)
+ * lies on the lower of the two ranks, then the others, each sorted by that
+ * side's (block, element, flux point).  Both ranks derive the same slots from
+ * the global pairing, so either side evaluates a shared pair with the same
+ * arguments as the unpartitioned right-hand side.  Same errors as fr_setup.
+ * A partitioned context serves fr_rhs_parts, fr_layout, fr_solution_points,
+ * fr_operator, fr_pairs (its own pairs), fr_sum_weighted, fr_check_finite;
+ * fr_rhs and the steppers return FR_ERR_UNSUPPORTED for it.
+ */
+fr_status fr_setup_part(const fr_mesh* mesh, const fr_params* prm, int cuda_device, const int32_t* part,
+                        int32_t nparts, int32_t rank, fr_ctx** out);
+
+/*
+ * Exchange slots of a partitioned context: *nnbr neighbour ranks (ascending)
+ * in ranks[], their slot counts in nslots[], and for every slot, neighbour by
+ * neighbour, the global L side (block, element, flux point) as 3 int64 in
+ * keys[].  Arrays may be NULL (sizes only).  Host-only contexts work too.
+ */
+fr_status fr_part_slots(const fr_ctx* ctx, int32_t* nnbr, int32_t* ranks, int64_t* nslots, int64_t* keys);
+
+/*
+ * One right-hand side of every partition, all on the calling device:
+ * parts[p] is the context of rank p, u[p] / r[p] its per-block state and
+ * result pointers (layout of fr_layout on parts[p]).  Per partition and stage:
+ * interpolation and packing of the shared flux-point values; exchange of the
+ * packed values (device-to-device copies on a library stream, ordered after
+ * the packing by events) while the interior-pair kernels run; then the
+ * shared-pair kernels.  Navier-Stokes exchanges U^(f) and, after the gradient
+ * stage, Q^(f).  Results equal those of fr_rhs on the whole mesh (bit for bit
+ * in FP64 and FP32 arithmetic: every pair is evaluated with the same inputs).
+ * Stream-ordered on `stream`.  FR_ERR_ARG for missing or mismatched contexts.
+ */
+fr_status fr_rhs_parts(fr_ctx* const* parts, int32_t nparts, void* const* const* u, void* const* const* r,
+                       void* stream);
+
 /* ABI version (increments on any signature change). */
 int32_t fr_version(void);   /* 4 */
 

@@ -1,6 +1,7 @@
 // C ABI of the FR library: context set-up (host work + device upload) and the
 // stream-ordered entry points declared in include/fr.h.
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -32,7 +33,28 @@ struct fr_ctx {
     cudaGraphExec_t rk_exec = nullptr;
     std::vector<void*> rk_ptrs;
     double rk_dt = 0.0;
+    // partitioned context (fr_setup_part): this rank, the number of ranks, the
+    // neighbour ranks and, per neighbour, the key (global L block, element,
+    // flux point) of every exchange slot
+    int part_rank = -1, part_n = 0;
+    std::vector<int> nbr_q;
+    std::vector<std::vector<std::array<int64_t, 3>>> nbr_keys;
+    cudaStream_t xstream = nullptr;     // exchange copies (fr_rhs_parts, owned by rank 0's context)
+    cudaEvent_t xev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
+
+namespace {
+// one cross-partition flux-point pair seen from this rank
+struct MpiPair {
+    int q;                   // neighbour rank
+    int b;                   // my (local) block
+    int32_t f;               // my flux point
+    int64_t n;               // my local element
+    bool mine_L;             // my side is the global L side
+    std::array<int64_t, 3> key;   // global L side (block, element, flux point)
+    double nrm[3], magL, magR;
+};
+}  // namespace
 
 static thread_local std::string g_setup_err;
 
@@ -241,10 +263,137 @@ void upload_device(fr_ctx* c) {
     CK(cudaDeviceSynchronize());
 }
 
+// Keep the elements of partition `rank` (in increasing global order within
+// each block): interior pairs with both sides here stay pairs, pairs with one
+// side here become exchange pairs (global L/R orientation kept), boundary
+// faces here stay.  Every block must keep at least one element.
+void localize(fr_ctx* c, const int32_t* part, int nparts, int rank, std::vector<MpiPair>& mp) {
+    const int nb = (int)c->hblocks.size();
+    std::vector<int64_t> base(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) base[b + 1] = base[b] + c->hblocks[b].nelem;
+    for (int64_t i = 0; i < base[nb]; ++i)
+        if (part[i] < 0 || part[i] >= nparts) throw Fail{FR_ERR_ARG, "partition index out of range"};
+    std::vector<std::vector<int64_t>> g2l(nb);
+    const int d = c->ndims;
+    for (int b = 0; b < nb; ++b) {
+        fr::HostBlock& hb = c->hblocks[b];
+        g2l[b].assign(hb.nelem, -1);
+        std::vector<double> nodes;
+        int64_t k = 0;
+        const size_t per = (size_t)hb.nnodes * d;
+        for (int64_t e = 0; e < hb.nelem; ++e)
+            if (part[base[b] + e] == rank) {
+                g2l[b][e] = k++;
+                nodes.insert(nodes.end(), hb.nodes.begin() + e * per, hb.nodes.begin() + (e + 1) * per);
+            }
+        if (k == 0) throw Fail{FR_ERR_ARG, "every element block needs elements in every partition"};
+        hb.nodes.swap(nodes);
+        hb.nelem = k;
+    }
+    std::vector<fr::HostPair> keep;
+    for (const fr::HostPair& P : c->pairs) {
+        const int pL = part[base[P.bL] + P.nL], pR = part[base[P.bR] + P.nR];
+        if (pL == rank && pR == rank) {
+            fr::HostPair Q = P;
+            Q.nL = g2l[P.bL][P.nL];
+            Q.nR = g2l[P.bR][P.nR];
+            keep.push_back(Q);
+        } else if (pL == rank || pR == rank) {
+            MpiPair m;
+            m.mine_L = pL == rank;
+            m.q = m.mine_L ? pR : pL;
+            m.b = m.mine_L ? P.bL : P.bR;
+            m.f = m.mine_L ? P.fL : P.fR;
+            m.n = m.mine_L ? g2l[P.bL][P.nL] : g2l[P.bR][P.nR];
+            m.key = {P.bL, P.nL, P.fL};
+            for (int j = 0; j < 3; ++j) m.nrm[j] = P.nrm[j];
+            m.magL = P.magL;
+            m.magR = P.magR;
+            mp.push_back(m);
+        }
+    }
+    c->pairs.swap(keep);
+    std::vector<fr::HostBnd> bk;
+    for (const fr::HostBnd& B : c->bnds)
+        if (part[base[B.b] + B.n] == rank) {
+            fr::HostBnd C = B;
+            C.n = g2l[B.b][B.n];
+            bk.push_back(C);
+        }
+    c->bnds.swap(bk);
+    c->part_rank = rank;
+    c->part_n = nparts;
+}
+
+// Exchange slots and device tables of the partition pairs.  With each
+// neighbour q, slots hold first the pairs whose global L side lies on the
+// lower of the two ranks, then the others, each sorted by the global L key;
+// both ranks derive the same order from the global pairing.
+void upload_part(fr_ctx* c, std::vector<MpiPair>& mp) {
+    const int rank = c->part_rank, d = c->ndims, V = c->nvars;
+    const bool fp64 = c->prm.precision == FR_PREC_FP64;
+    const size_t rs = fp64 ? sizeof(double) : sizeof(float);
+    const bool ns = c->prm.system == FR_NAVIER_STOKES;
+    std::map<int, std::vector<int64_t>> byq;
+    for (int64_t k = 0; k < (int64_t)mp.size(); ++k) byq[mp[k].q].push_back(k);
+    fr::DevCtx& D = c->dev;
+    for (auto& kv : byq) {
+        const int q = kv.first;
+        std::vector<int64_t>& ids = kv.second;
+        const bool lower = rank < q;
+        std::stable_sort(ids.begin(), ids.end(), [&](int64_t x, int64_t y) {
+            const bool fx = mp[x].mine_L == lower, fy = mp[y].mine_L == lower;   // L side on the lower rank
+            if (fx != fy) return fx;
+            return mp[x].key < mp[y].key;
+        });
+        const int nbi = (int)D.nbrs.size();
+        fr::DevNeighbour nbr;
+        nbr.q = q;
+        nbr.nslots = (int64_t)ids.size();
+        c->nbr_q.push_back(q);
+        c->nbr_keys.emplace_back();
+        for (int64_t i : ids) c->nbr_keys.back().push_back(mp[i].key);
+        nbr.send_u = dalloc(c, (size_t)V * nbr.nslots * rs);
+        nbr.recv_u = dalloc(c, (size_t)V * nbr.nslots * rs);
+        // the Q receive buffer also takes the discarded remote-side common solution
+        nbr.recv_q = dalloc(c, (size_t)(ns ? d : 1) * V * nbr.nslots * rs);
+        nbr.send_q = ns ? dalloc(c, (size_t)d * V * nbr.nslots * rs) : nullptr;
+        D.nbrs.push_back(nbr);
+        // device groups by (my block, orientation)
+        std::map<std::pair<int, int>, std::vector<int64_t>> grp;     // -> slots
+        for (int64_t sl = 0; sl < (int64_t)ids.size(); ++sl) grp[{mp[ids[sl]].b, mp[ids[sl]].mine_L ? 1 : 0}].push_back(sl);
+        for (auto& gv : grp) {
+            fr::DevMpiGroup g;
+            g.nb = nbi;
+            g.b = gv.first.first;
+            g.mine_L = gv.first.second == 1;
+            g.n = (int64_t)gv.second.size();
+            const fr::DevBlock& B = D.blocks[g.b];
+            std::vector<uint32_t> off(g.n), slot(g.n);
+            std::vector<double> nrm((size_t)d * g.n), mL(g.n), mR(g.n);
+            for (int64_t i = 0; i < g.n; ++i) {
+                const MpiPair& m = mp[ids[gv.second[i]]];
+                off[i] = (uint32_t)((int64_t)m.f * V * B.ld + m.n);
+                slot[i] = (uint32_t)gv.second[i];
+                for (int j = 0; j < d; ++j) nrm[(size_t)j * g.n + i] = m.nrm[j];
+                mL[i] = m.magL;
+                mR[i] = m.magR;
+            }
+            g.off = (uint32_t*)upload(c, off);
+            g.slot = (uint32_t*)upload(c, slot);
+            g.nrm = upload_real(c, nrm, fp64);
+            g.magL = upload_real(c, mL, fp64);
+            g.magR = upload_real(c, mR, fp64);
+            D.mgroups.push_back(g);
+        }
+    }
+}
+
 }  // namespace
 
 namespace fr {
 DevCtx* ctx_dev(fr_ctx* c) { return c ? &c->dev : nullptr; }
+bool ctx_is_part(const fr_ctx* c) { return c && c->part_n > 0; }
 void ctx_set_error(fr_ctx* c, const char* msg) {
     if (c) c->err = msg;
 }
@@ -271,12 +420,16 @@ void fr_destroy(fr_ctx* ctx) {
         fr::prof_free(ctx->dev);
         if (ctx->rk_exec) cudaGraphExecDestroy(ctx->rk_exec);
         if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+        if (ctx->xstream) cudaStreamDestroy(ctx->xstream);
+        for (cudaEvent_t e : ctx->xev)
+            if (e) cudaEventDestroy(e);
         for (void* p : ctx->allocs) cudaFree(p);
     }
     delete ctx;
 }
 
-fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx** out) {
+static fr_status setup_impl(const fr_mesh* mesh, const fr_params* prm, int device, const int32_t* part, int nparts,
+                            int rank, fr_ctx** out) {
     if (out) *out = nullptr;
     if (!mesh || !prm || !out) return set_err(nullptr, FR_ERR_ARG, "NULL argument");
     if (prm->ndims != 2 && prm->ndims != 3) return set_err(nullptr, FR_ERR_ARG, "ndims must be 2 or 3");
@@ -325,6 +478,8 @@ fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx
         if (!fr::pair_mesh(prm->ndims, c->hblocks, mesh->bfaces, mesh->nbfaces, mesh->periodic, mesh->nperiodic,
                            c->pairs, c->bnds, err))
             throw Fail{FR_ERR_MESH, err};
+        std::vector<MpiPair> mp;
+        if (part) localize(c.get(), part, nparts, rank, mp);
         // locality order: group by block pair, then L flux point, then L element
         std::sort(c->pairs.begin(), c->pairs.end(), [](const fr::HostPair& a, const fr::HostPair& b) {
             if (a.bL != b.bL) return a.bL < b.bL;
@@ -357,10 +512,27 @@ fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx
         if (device >= 0) {
             c->dev.device = device;
             upload_device(c.get());
+            if (part) upload_part(c.get(), mp);
             if (prm->precision == FR_PREC_BF16X3 || prm->precision == FR_PREC_TF32X3) CK(fr::tc::prepare());
             // the host pair list is only kept for inspection of small meshes
             if (c->pairs.size() > (size_t)4000000) { c->pairs.clear(); c->pairs.shrink_to_fit(); }
         } else {
+            if (part) {                   // slot tables for inspection
+                c->dev.device = -1;
+                std::map<int, std::vector<MpiPair>> byq;
+                for (auto& m : mp) byq[m.q].push_back(m);
+                for (auto& kv : byq) {
+                    const bool lower = rank < kv.first;
+                    std::stable_sort(kv.second.begin(), kv.second.end(), [&](const MpiPair& x, const MpiPair& y) {
+                        const bool fx = x.mine_L == lower, fy = y.mine_L == lower;
+                        if (fx != fy) return fx;
+                        return x.key < y.key;
+                    });
+                    c->nbr_q.push_back(kv.first);
+                    c->nbr_keys.emplace_back();
+                    for (auto& m : kv.second) c->nbr_keys.back().push_back(m.key);
+                }
+            }
             // host-only: still check every Jacobian
             for (auto& hb : c->hblocks) {
                 std::vector<double> adj((size_t)hb.el->nupts * 9), det(hb.el->nupts);
@@ -379,6 +551,33 @@ fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx
         return set_err(nullptr, FR_ERR_OOM, "host allocation failed");
     }
     *out = c.release();
+    return FR_OK;
+}
+
+fr_status fr_setup(const fr_mesh* mesh, const fr_params* prm, int device, fr_ctx** out) {
+    return setup_impl(mesh, prm, device, nullptr, 0, 0, out);
+}
+
+fr_status fr_setup_part(const fr_mesh* mesh, const fr_params* prm, int device, const int32_t* part, int32_t nparts,
+                        int32_t rank, fr_ctx** out) {
+    if (out) *out = nullptr;
+    if (!part || nparts < 1 || rank < 0 || rank >= nparts) return set_err(nullptr, FR_ERR_ARG, "bad partition arguments");
+    return setup_impl(mesh, prm, device, part, nparts, rank, out);
+}
+
+fr_status fr_part_slots(const fr_ctx* ctx, int32_t* nnbr, int32_t* ranks, int64_t* nslots, int64_t* keys) {
+    if (!ctx || !nnbr) return FR_ERR_ARG;
+    *nnbr = (int32_t)ctx->nbr_q.size();
+    int64_t o = 0;
+    for (size_t k = 0; k < ctx->nbr_q.size(); ++k) {
+        if (ranks) ranks[k] = ctx->nbr_q[k];
+        if (nslots) nslots[k] = (int64_t)ctx->nbr_keys[k].size();
+        if (keys)
+            for (auto& key : ctx->nbr_keys[k]) {
+                keys[3 * o] = key[0]; keys[3 * o + 1] = key[1]; keys[3 * o + 2] = key[2];
+                ++o;
+            }
+    }
     return FR_OK;
 }
 
@@ -460,9 +659,88 @@ static bool ptrs_ok(const fr_ctx* ctx, const void* const* p) {
     return true;
 }
 
+// a partition's right-hand side needs its neighbours: only fr_rhs_parts runs it
+static fr_status whole_mesh(fr_ctx* ctx) {
+    if (ctx && ctx->part_n > 0)
+        return set_err(ctx, FR_ERR_UNSUPPORTED, "partitioned context: use fr_rhs_parts for its right-hand side");
+    return FR_OK;
+}
+
+fr_status fr_rhs_parts(fr_ctx* const* parts, int32_t nparts, void* const* const* u, void* const* const* r,
+                       void* stream) {
+    if (!parts || nparts < 1 || !u || !r) return FR_ERR_ARG;
+    for (int p = 0; p < nparts; ++p) {
+        fr_ctx* c = parts[p];
+        if (!c) return FR_ERR_ARG;
+        fr_status s = check_dev(c);
+        if (s != FR_OK) return s;
+        if (c->part_n != nparts || c->part_rank != p)
+            return set_err(c, FR_ERR_ARG, "parts[p] must be the context of rank p of this partition");
+        if (c->dev.device != parts[0]->dev.device || c->prm.precision != parts[0]->prm.precision ||
+            c->prm.system != parts[0]->prm.system)
+            return set_err(c, FR_ERR_ARG, "partitions differ in device, precision or system");
+        if (!ptrs_ok(c, u[p]) || !ptrs_ok(c, r[p])) return set_err(c, FR_ERR_ARG, "NULL state pointer");
+    }
+    fr_ctx* c0 = parts[0];
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!c0->xstream && (e = cudaStreamCreateWithFlags(&c0->xstream, cudaStreamNonBlocking)) != cudaSuccess)
+        return set_err(c0, FR_ERR_CUDA, cudaGetErrorString(e));
+    for (cudaEvent_t& ev : c0->xev)
+        if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return set_err(c0, FR_ERR_CUDA, cudaGetErrorString(e));
+    const bool ns = c0->prm.system == FR_NAVIER_STOKES;
+    const size_t rs = c0->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    auto phase = [&](int ph) -> cudaError_t {
+        for (int p = 0; p < nparts; ++p) {
+            cudaError_t er = fr::launch_rhs_phases(parts[p]->dev, u[p], r[p], ph, st);
+            if (er != cudaSuccess) return er;
+        }
+        return cudaSuccess;
+    };
+    // exchange: rank p's send buffer for q into rank q's receive buffer for p
+    // (device-to-device copies on the exchange stream)
+    auto exchange = [&](bool qbuf, cudaEvent_t after, cudaEvent_t done) -> cudaError_t {
+        cudaError_t er = cudaEventRecord(after, st);
+        if (er == cudaSuccess) er = cudaStreamWaitEvent(c0->xstream, after, 0);
+        for (int p = 0; p < nparts && er == cudaSuccess; ++p) {
+            fr::DevCtx& A = parts[p]->dev;
+            for (auto& nb : A.nbrs) {
+                fr::DevCtx& B = parts[nb.q]->dev;
+                const fr::DevNeighbour* back = nullptr;
+                for (auto& x : B.nbrs)
+                    if (x.q == p) back = &x;
+                if (!back || back->nslots != nb.nslots) return cudaErrorInvalidValue;
+                const size_t bytes = (size_t)(qbuf ? A.ndims : 1) * A.nvars * nb.nslots * rs;
+                er = cudaMemcpyAsync(qbuf ? back->recv_q : back->recv_u, qbuf ? nb.send_q : nb.send_u, bytes,
+                                     cudaMemcpyDeviceToDevice, c0->xstream);
+                if (er != cudaSuccess) break;
+            }
+        }
+        if (er == cudaSuccess) er = cudaEventRecord(done, c0->xstream);
+        return er;
+    };
+    // interior-pair work overlaps each exchange (Sec. 3.6: int kernels while the mpi data is in flight)
+    if ((e = phase(fr::PH_A)) != cudaSuccess || (e = exchange(false, c0->xev[0], c0->xev[1])) != cudaSuccess)
+        return set_err(c0, FR_ERR_CUDA, cudaGetErrorString(e));
+    if (ns) {
+        if ((e = phase(fr::PH_B1)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c0->xev[1], 0)) != cudaSuccess ||
+            (e = phase(fr::PH_B2)) != cudaSuccess || (e = exchange(true, c0->xev[2], c0->xev[3])) != cudaSuccess ||
+            (e = phase(fr::PH_C1)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c0->xev[3], 0)) != cudaSuccess ||
+            (e = phase(fr::PH_C2)) != cudaSuccess)
+            return set_err(c0, FR_ERR_CUDA, cudaGetErrorString(e));
+    } else {
+        if ((e = phase(fr::PH_C1)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c0->xev[1], 0)) != cudaSuccess ||
+            (e = phase(fr::PH_C2)) != cudaSuccess)
+            return set_err(c0, FR_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return FR_OK;
+}
+
 fr_status fr_rhs(fr_ctx* ctx, void* const* u, void* const* r, void* stream) {
     fr_status s = check_dev(ctx);
     if (s != FR_OK) return s;
+    if ((s = whole_mesh(ctx)) != FR_OK) return s;
     if (!ptrs_ok(ctx, u) || !ptrs_ok(ctx, r)) return set_err(ctx, FR_ERR_ARG, "NULL state pointer");
     cudaError_t e = fr::launch_rhs(ctx->dev, u, r, (cudaStream_t)stream);
     if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
@@ -472,6 +750,7 @@ fr_status fr_rhs(fr_ctx* ctx, void* const* u, void* const* r, void* stream) {
 fr_status fr_rhs_host(fr_ctx* ctx, const void* const* u, void* const* r, void* stream) {
     fr_status s = check_dev(ctx);
     if (s != FR_OK) return s;
+    if ((s = whole_mesh(ctx)) != FR_OK) return s;
     if (!ptrs_ok(ctx, (void* const*)u) || !ptrs_ok(ctx, r)) return set_err(ctx, FR_ERR_ARG, "NULL state pointer");
     cudaStream_t st = (cudaStream_t)stream;
     size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -500,6 +779,7 @@ fr_status fr_rhs_host(fr_ctx* ctx, const void* const* u, void* const* r, void* s
 fr_status fr_euler(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream) {
     fr_status s = check_dev(ctx);
     if (s != FR_OK) return s;
+    if ((s = whole_mesh(ctx)) != FR_OK) return s;
     if (!ptrs_ok(ctx, u) || nsteps < 0) return set_err(ctx, FR_ERR_ARG, "bad argument");
     const size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
     try {
@@ -516,6 +796,7 @@ fr_status fr_dopri5(fr_ctx* ctx, void* const* u, double dt, int nsteps, double a
                     void* stream) {
     fr_status s = check_dev(ctx);
     if (s != FR_OK) return s;
+    if ((s = whole_mesh(ctx)) != FR_OK) return s;
     if (!ptrs_ok(ctx, u) || nsteps < 0) return set_err(ctx, FR_ERR_ARG, "bad argument");
     if (err && !(atol > 0.0 && rtol >= 0.0)) return set_err(ctx, FR_ERR_ARG, "atol must be > 0 and rtol >= 0");
     const size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -535,6 +816,7 @@ fr_status fr_dopri5(fr_ctx* ctx, void* const* u, double dt, int nsteps, double a
 fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream) {
     fr_status s = check_dev(ctx);
     if (s != FR_OK) return s;
+    if ((s = whole_mesh(ctx)) != FR_OK) return s;
     if (!ptrs_ok(ctx, u) || nsteps < 0) return set_err(ctx, FR_ERR_ARG, "bad argument");
     size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
     try {
@@ -594,6 +876,7 @@ fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value) {
 static fr_status adjoint_ready(fr_ctx* ctx) {
     fr_status s = check_dev(ctx);
     if (s != FR_OK) return s;
+    if ((s = whole_mesh(ctx)) != FR_OK) return s;
     if (ctx->prm.system != FR_EULER) return set_err(ctx, FR_ERR_UNSUPPORTED, "the adjoint covers the Euler equations");
     size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
     try {

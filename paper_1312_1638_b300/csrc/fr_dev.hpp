@@ -58,6 +58,32 @@ struct DevPairGroup {          // interior pairs between block bL and block bR
     void* magR = nullptr;
 };
 
+// Cross-partition pairs (Sec. 3.6 "mpi" interfaces) with one neighbour rank,
+// one of my blocks and one orientation: my side is the global L side
+// (mine_L) or the R side; the other side's values arrive in the neighbour's
+// exchange buffers at the pairs' slots.
+struct DevMpiGroup {
+    int nb = 0;                // index into DevCtx::nbrs
+    int b = 0;                 // my block
+    bool mine_L = true;
+    int64_t n = 0;
+    uint32_t* off = nullptr;   // my flux-point offsets fpt*nvars*ld + elem
+    uint32_t* slot = nullptr;  // slot of each pair in the exchange buffers
+    void* nrm = nullptr;       // [ndims][n] unit normal of the global L side (T)
+    void* magL = nullptr;
+    void* magR = nullptr;
+};
+
+// exchange buffers with one neighbour rank: U^(f) [nvars][nslots], Q^(f) [ndims][nvars][nslots]
+struct DevNeighbour {
+    int q = 0;
+    int64_t nslots = 0;
+    void* send_u = nullptr;
+    void* recv_u = nullptr;
+    void* send_q = nullptr;
+    void* recv_q = nullptr;
+};
+
 struct DevBndGroup {           // boundary flux points of one block and one type
     int b = 0, bctype = 0;
     int64_t n = 0;
@@ -89,6 +115,8 @@ struct DevCtx {
     std::vector<DevBlock> blocks;
     std::vector<DevPairGroup> pgroups;
     std::vector<DevBndGroup> bgroups;
+    std::vector<DevNeighbour> nbrs;   // partitioned context: neighbour ranks
+    std::vector<DevMpiGroup> mgroups;
     int* flags = nullptr;          // [0] non-finite seen, [1] timeout
     double* partial = nullptr;     // reduction scratch
     int64_t npartial = 0;
@@ -114,6 +142,13 @@ cudaError_t launch_rk4_adjoint(DevCtx& c, void* const* u0, void* const* lam, dou
                                const std::vector<std::vector<void*>>& tmp, cudaStream_t st);
 // classical RK4, nsteps steps of dt, in place on u
 cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st);
+// RHS phases of a partitioned context (all of them for an ordinary one):
+// A = disu + pack U^(f); B1 = common solution, interior and boundary pairs;
+// B2 = common solution at partition pairs, gradients, pack Q^(f);
+// C1 = transformed flux, common flux at interior and boundary pairs;
+// C2 = common flux at partition pairs, divergence (+ energy-split correction)
+enum RhsPhase { PH_A = 1, PH_B1 = 2, PH_B2 = 4, PH_C1 = 8, PH_C2 = 16, PH_ALL = 31 };
+cudaError_t launch_rhs_phases(DevCtx& c, void* const* u, void* const* r, int phases, cudaStream_t st);
 cudaError_t launch_euler(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st);
 cudaError_t launch_dopri5(DevCtx& c, void* const* u, double dt, int nsteps, double atol, double rtol, double* err,
                           cudaStream_t st);
@@ -131,4 +166,5 @@ struct fr_ctx;
 namespace fr {
 DevCtx* ctx_dev(fr_ctx* c);
 void ctx_set_error(fr_ctx* c, const char* msg);
+bool ctx_is_part(const fr_ctx* c);   // built by fr_setup_part
 }  // namespace fr

@@ -28,17 +28,20 @@ template <typename T>
 struct Sub {
     T v[5];
 };
+// Row tile MB = 8 * RM (8 row groups of RM rows each): small operators (low
+// orders) take RM = 2 or 4 so that few padded rows are computed; this matters
+// most in FP64, where a B300 SM retires about 2 FMA per cycle.
 template <typename T> struct GemmCfg;
-template <> struct GemmCfg<float>  { static constexpr int TN = 128, RN = 4, MB = 64, RM = 8, KC = 16; };
-template <> struct GemmCfg<double> { static constexpr int TN = 64,  RN = 2, MB = 64, RM = 8, KC = 16; };
+template <> struct GemmCfg<float>  { static constexpr int TN = 128, RN = 4, KC = 16; };
+template <> struct GemmCfg<double> { static constexpr int TN = 64,  RN = 2, KC = 16; };
 
-template <typename T>
+template <typename T, int RM>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int K, int K1, const T* __restrict__ A, const T* __restrict__ B1,
             const T* __restrict__ B2, int64_t N, T* __restrict__ C, int epi,
             const T* __restrict__ rcp, int64_t ld, int ks0, int ks1, Sub<T> sub) {
     using G = GemmCfg<T>;
-    constexpr int TN = G::TN, RN = G::RN, MB = G::MB, RM = G::RM, KC = G::KC;
+    constexpr int TN = G::TN, RN = G::RN, MB = 8 * RM, KC = G::KC;
     __shared__ __align__(16) T As[KC][MB];
     __shared__ __align__(16) T Bs[KC][TN];
     const int tid = threadIdx.x;
@@ -104,8 +107,15 @@ static void gemm(int M, int K, int K1, const void* A, const void* B1, const void
                  Sub<T> sub = Sub<T>{}) {
     constexpr int TN = GemmCfg<T>::TN;
     dim3 grid((unsigned)((N + TN - 1) / TN));
-    gemm_kernel<T><<<grid, 256, 0, st>>>(M, K, K1, (const T*)A, (const T*)B1, (const T*)B2, N, (T*)C, epi,
-                                         (const T*)rcp, ld, ks0, ks1, sub);
+    if (M <= 16)
+        gemm_kernel<T, 2><<<grid, 256, 0, st>>>(M, K, K1, (const T*)A, (const T*)B1, (const T*)B2, N, (T*)C, epi,
+                                                (const T*)rcp, ld, ks0, ks1, sub);
+    else if (M <= 32)
+        gemm_kernel<T, 4><<<grid, 256, 0, st>>>(M, K, K1, (const T*)A, (const T*)B1, (const T*)B2, N, (T*)C, epi,
+                                                (const T*)rcp, ld, ks0, ks1, sub);
+    else
+        gemm_kernel<T, 8><<<grid, 256, 0, st>>>(M, K, K1, (const T*)A, (const T*)B1, (const T*)B2, N, (T*)C, epi,
+                                                (const T*)rcp, ld, ks0, ks1, sub);
 }
 
 // Operator product dispatch: CUDA-core GEMM for FP64 / FP32, tensor-core
@@ -641,13 +651,28 @@ static inline unsigned lin_grid(int64_t n, int bs) { return (unsigned)((n + bs -
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
+// Gather my side of the partition pairs into an exchange buffer:
+// buf[(j nvars + a) nslots + slot_k] = src[j qs + off_k + a ld], j < ncomp
+template <typename T>
+__global__ void pack_kernel(int64_t n, int nvars, int ncomp, const uint32_t* __restrict__ off,
+                            const uint32_t* __restrict__ slot, const T* __restrict__ src, int64_t ld, int64_t qs,
+                            T* __restrict__ buf, int64_t nslots) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t o = off[k], sl = slot[k];
+    for (int j = 0; j < ncomp; ++j)
+        for (int a = 0; a < nvars; ++a) buf[(int64_t)(j * nvars + a) * nslots + sl] = src[j * qs + o + a * ld];
+}
+
 template <typename T, int D>
-static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st, bool energy_fix = true) {
+static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st, bool energy_fix = true,
+                            int phases = PH_ALL) {
     constexpr int NV = D + 2;
     const bool ns = c.system == 1;
     Sub<T> sub{};
     sub.v[0] = T(c.prm.ref_rho);
     sub.v[NV - 1] = T(c.prm.ref_E);
+    if (!(phases & PH_A)) goto phase_b1;
     // 1. U'^(f) = M0 (U - u_ref)  (K1, disu)
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
@@ -656,7 +681,15 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
                    B.ld, st, 0, B.nupts, sub));
         prof_end(c, st);
     }
-    if (ns) {
+    // partition pairs: my side of U^(f) into the exchange buffers
+    for (auto& g : c.mgroups) {
+        DevBlock& B = c.blocks[g.b];
+        DevNeighbour& q = c.nbrs[g.nb];
+        pack_kernel<T><<<lin_grid(g.n, 128), 128, 0, st>>>(g.n, NV, 1, g.off, g.slot, (const T*)B.Uf, B.ld, 0,
+                                                           (T*)q.send_u, q.nslots);
+    }
+phase_b1:
+    if (ns && (phases & PH_B1)) {
         // 2. common solution into the Q^(f) storage (C^(f) aliases Q^(f), Sec. 3.6)
         for (auto& g : c.pgroups) {
             DevBlock &L = c.blocks[g.bL], &R = c.blocks[g.bR];
@@ -672,6 +705,25 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
             prof_begin(c, K_COMM_SOL_BC, st);
             comm_sol_bc_kernel<T, D><<<lin_grid(g.n, 128), 128, 0, st>>>(g.n, g.bctype, g.off, (const T*)B.Uf, B.ld,
                                                                           (T*)B.Qf, c.prm);
+            prof_end(c, st);
+        }
+    }
+    if (ns && (phases & PH_B2)) {
+        // partition pairs: the remote side comes from the received U^(f); the
+        // common solution written for it lands in the (not yet used) Q receive
+        // buffer and is discarded
+        for (auto& g : c.mgroups) {
+            DevBlock& B = c.blocks[g.b];
+            DevNeighbour& q = c.nbrs[g.nb];
+            prof_begin(c, K_COMM_SOL, st);
+            if (g.mine_L)
+                comm_sol_kernel<T, D><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                    g.n, g.off, g.slot, (const T*)B.Uf, (const T*)q.recv_u, B.ld, q.nslots, (T*)B.Qf, (T*)q.recv_q,
+                    T(c.prm.beta));
+            else
+                comm_sol_kernel<T, D><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                    g.n, g.slot, g.off, (const T*)q.recv_u, (const T*)B.Uf, q.nslots, B.ld, (T*)q.recv_q, (T*)B.Qf,
+                    T(c.prm.beta));
             prof_end(c, st);
         }
         for (size_t b = 0; b < c.blocks.size(); ++b) {
@@ -705,7 +757,15 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
                 prof_end(c, st);
             }
         }
+        // partition pairs: my side of Q^(f) into the exchange buffers
+        for (auto& g : c.mgroups) {
+            DevBlock& B = c.blocks[g.b];
+            DevNeighbour& q = c.nbrs[g.nb];
+            pack_kernel<T><<<lin_grid(g.n, 128), 128, 0, st>>>(g.n, NV, D, g.off, g.slot, (const T*)B.Qf, B.ld,
+                                                               (int64_t)B.nfpts * NV * B.ld, (T*)q.send_q, q.nslots);
+        }
     }
+    if (!(phases & PH_C1)) goto phase_c2;
     // 6. F~ = J J^{-1} f(U, Q)  (tdisf), in place over Q
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
@@ -747,6 +807,33 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
                 g.n, g.bctype, g.off, (T*)B.Uf, nullptr, B.ld, qs, (const T*)g.nrm, (const T*)g.mag, c.prm);
         prof_end(c, st);
     }
+phase_c2:
+    if (!(phases & PH_C2)) return cudaGetLastError();
+    // partition pairs: the remote side from the received U^(f) and Q^(f); the
+    // flux written for it lands in the receive buffer and is discarded
+    for (auto& g : c.mgroups) {
+        DevBlock& B = c.blocks[g.b];
+        DevNeighbour& q = c.nbrs[g.nb];
+        const int64_t qsB = (int64_t)B.nfpts * NV * B.ld, qsQ = (int64_t)NV * q.nslots;
+        T* UL = g.mine_L ? (T*)B.Uf : (T*)q.recv_u;
+        T* UR = g.mine_L ? (T*)q.recv_u : (T*)B.Uf;
+        const T* QL = ns ? (const T*)(g.mine_L ? B.Qf : q.recv_q) : nullptr;
+        const T* QR = ns ? (const T*)(g.mine_L ? q.recv_q : B.Qf) : nullptr;
+        const uint32_t* oL = g.mine_L ? g.off : g.slot;
+        const uint32_t* oR = g.mine_L ? g.slot : g.off;
+        const int64_t ldL = g.mine_L ? B.ld : q.nslots, ldR = g.mine_L ? q.nslots : B.ld;
+        const int64_t qsL = g.mine_L ? qsB : qsQ, qsR = g.mine_L ? qsQ : qsB;
+        prof_begin(c, K_COMM_FLUX, st);
+        if (ns)
+            comm_flux_kernel<T, D, true><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                g.n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL, qsR, (const T*)g.nrm, (const T*)g.magL, (const T*)g.magR,
+                c.prm);
+        else
+            comm_flux_kernel<T, D, false><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                g.n, oL, oR, UL, UR, nullptr, nullptr, ldL, ldR, qsL, qsR, (const T*)g.nrm, (const T*)g.magL,
+                (const T*)g.magR, c.prm);
+        prof_end(c, st);
+    }
     // 8. R = -J^{-1} [M3 D~ + (M1 - M3 M2) F~]  (tdivtpcorf + negdivconf)
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
@@ -784,6 +871,13 @@ cudaError_t adjoint_gemm(DevCtx& c, int which, int b, const void* B, void* C, cu
 cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
     if (c.precision == 0) return c.ndims == 2 ? rhs_impl<double, 2>(c, u, r, st) : rhs_impl<double, 3>(c, u, r, st);
     return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st) : rhs_impl<float, 3>(c, u, r, st);
+}
+
+cudaError_t launch_rhs_phases(DevCtx& c, void* const* u, void* const* r, int phases, cudaStream_t st) {
+    if (c.precision == 0)
+        return c.ndims == 2 ? rhs_impl<double, 2>(c, u, r, st, true, phases)
+                            : rhs_impl<double, 3>(c, u, r, st, true, phases);
+    return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st, true, phases) : rhs_impl<float, 3>(c, u, r, st, true, phases);
 }
 
 // RHS without the final energy-split correction (the RK4 stage kernels apply it)

@@ -115,6 +115,10 @@ extern "C" fr_status fr_rk4_noalloc(fr_ctx* ctx, void* const* u, double dt, int 
         fr::ctx_set_error(ctx, "host-only context has no device state");
         return FR_ERR_UNSUPPORTED;
     }
+    if (fr::ctx_is_part(ctx)) {
+        fr::ctx_set_error(ctx, "partitioned context: use fr_rhs_parts for its right-hand side");
+        return FR_ERR_UNSUPPORTED;
+    }
     if (c->blocks.size() > 16) {
         fr::ctx_set_error(ctx, "fr_rk4_noalloc supports at most 16 element blocks");
         return FR_ERR_ARG;

@@ -28,7 +28,7 @@ EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pai
            "fr_rhs_host", "fr_rk4", "fr_sum_weighted", "fr_sync_status", "fr_check_finite",
            "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read",
            "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint", "fr_set_option", "fr_fma_peak",
-           "fr_euler", "fr_dopri5"]
+           "fr_euler", "fr_dopri5", "fr_setup_part", "fr_part_slots", "fr_rhs_parts"]
 
 
 class FRError(RuntimeError):
@@ -163,6 +163,42 @@ def adaptive_dopri5(step, save, restore, t_end, dt0, safety=0.9, facmin=0.2, fac
     return dict(t=t, accepted=acc, rejected=rej)
 
 
+class PartitionedSolver:
+    """The mesh split into nparts partitions, one context per rank, all on
+    one device; rhs() runs fr_rhs_parts.  part: one partition index per element,
+    block-major.  Each rank keeps its elements of every block in increasing
+    global order (local_elements)."""
+
+    def __init__(self, mesh, part, nparts, order, system="euler", precision="fp64", device=0, **params):
+        self.mesh, self.nparts = mesh, nparts
+        self.part = np.ascontiguousarray(part, dtype=np.int32)
+        self.ranks = [Solver(mesh, order, system, precision, device, part=self.part, nparts=nparts, rank=r, **params)
+                      for r in range(nparts)]
+        self.lib = self.ranks[0].lib
+        base = np.cumsum([0] + [b.nodes.shape[0] for b in mesh.blocks])
+        self._local = [[np.nonzero(self.part[base[b]:base[b + 1]] == r)[0] for b in range(len(mesh.blocks))]
+                       for r in range(nparts)]
+
+    def local_elements(self, rank, b):
+        """Global element indices (within block b) held by `rank`, in local order."""
+        return self._local[rank][b]
+
+    def rhs(self, u, r, stream=None):
+        """u[p][b], r[p][b]: device state / result of rank p, block b."""
+        ctxs = (C.c_void_p * self.nparts)(*[s.ctx for s in self.ranks])
+        ua, ra = [_ptrs(x) for x in u], [_ptrs(x) for x in r]       # kept alive for the call
+        U = (C.POINTER(C.c_void_p) * self.nparts)(*[C.cast(a, C.POINTER(C.c_void_p)) for a in ua])
+        R = (C.POINTER(C.c_void_p) * self.nparts)(*[C.cast(a, C.POINTER(C.c_void_p)) for a in ra])
+        self._keep = (ua, ra, U, R)
+        st = self.lib.fr_rhs_parts(ctxs, self.nparts, U, R, _stream_ptr(stream))
+        if st != OK:
+            raise FRError(st, self.lib.fr_last_error(self.ranks[0].ctx).decode())
+
+    def close(self):
+        for s in self.ranks:
+            s.close()
+
+
 def fma_peak(device=0):
     """Measured (FP32, FP64) FMA throughput of the CUDA cores, TFLOP/s."""
     lib = load()
@@ -180,7 +216,8 @@ class Solver:
     inspection); any other value is the CUDA device ordinal.
     """
 
-    def __init__(self, mesh, order, system="euler", precision="fp64", device=0, **params):
+    def __init__(self, mesh, order, system="euler", precision="fp64", device=0, part=None, nparts=0, rank=0,
+                 **params):
         lib = load()
         self.lib = lib
         self.mesh = mesh
@@ -229,7 +266,12 @@ class Solver:
         m.nperiodic = per.shape[0]
         m.periodic = per.ctypes.data_as(C.POINTER(C.c_double))
         ctx = C.c_void_p()
-        st = lib.fr_setup(C.byref(m), C.byref(p), device, C.byref(ctx))
+        if part is None:
+            st = lib.fr_setup(C.byref(m), C.byref(p), device, C.byref(ctx))
+        else:
+            self.part = np.ascontiguousarray(part, dtype=np.int32)
+            st = lib.fr_setup_part(C.byref(m), C.byref(p), device, self.part.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   int(nparts), int(rank), C.byref(ctx))
         if st != OK:
             raise FRError(st, lib.fr_last_error(None).decode())
         self.ctx = ctx
@@ -238,6 +280,23 @@ class Solver:
     def _check(self, st):
         if st != OK:
             raise FRError(st, self.lib.fr_last_error(self.ctx).decode())
+
+    def part_slots(self):
+        """{neighbour rank: int64 [nslots, 3] global L (block, element, flux point) per slot}."""
+        nn = C.c_int32()
+        self._check(self.lib.fr_part_slots(self.ctx, C.byref(nn), None, None, None))
+        ranks = np.zeros(nn.value, np.int32)
+        ns = np.zeros(nn.value, np.int64)
+        self._check(self.lib.fr_part_slots(self.ctx, C.byref(nn), ranks.ctypes.data_as(C.POINTER(C.c_int32)),
+                                           ns.ctypes.data_as(C.POINTER(C.c_int64)), None))
+        keys = np.zeros((int(ns.sum()), 3), np.int64)
+        self._check(self.lib.fr_part_slots(self.ctx, C.byref(nn), None, None,
+                                           keys.ctypes.data_as(C.POINTER(C.c_int64))))
+        out, o = {}, 0
+        for q, n in zip(ranks, ns):
+            out[int(q)] = keys[o:o + n]
+            o += n
+        return out
 
     def close(self):
         if getattr(self, "ctx", None):

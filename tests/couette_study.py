@@ -11,7 +11,7 @@ the first t with sigma(t) / sigma(t + 0.1) <= 1.01.  The paper's mixed meshes
 are not published: ``channel_mixed`` (quads below, split triangles above,
 jittered interior nodes, periodic in x) stands in for them.
 
-    python -m tests.couette_study      # the full table (p = 1..4, four meshes)
+    python -m tests.couette_study [uniform]   # the full table (p = 1..4, four meshes each)
 """
 
 from __future__ import annotations
@@ -29,8 +29,15 @@ PRM = dict(gamma=G, mu=MU, prandtl=PR, ldg_beta=0.5, ldg_tau=0.1, wall_cpTw=CPTW
            wall_v=(0.0, 0.0, 0.0), wall2_v=(VW, 0.0, 0.0))
 
 
-def run(p, n, precision="fp64", cfl=0.3, t_max=5.0, jitter=0.1, seed=1):
-    """Steady Couette flow on channel_mixed(n, n); returns dict(sigma, t_inf, steps)."""
+def run(p, n, precision="fp64", cfl=0.5, t_max=5.0, jitter=0.1, seed=1, start="uniform", t_end=1.2):
+    """Steady Couette flow on channel_mixed(n, n); returns dict(sigma, t_inf, steps).
+
+    start = "uniform": the paper's constant initial state and stopping rule
+    sigma(t) / sigma(t + 0.1) <= 1.01 (within ~3 % of the converged error when
+    the slowest mode decays at nu pi^2 / H^2 ~ 3.5 per unit time).
+    start = "exact": the analytic state, integrated to the fixed time t_end
+    (1.2 = four e-folding times of that mode; the discrete steady state is the
+    same and the remaining transient is a percent of sigma or less)."""
     import torch
     from paper_1312_1638_b300 import fr
 
@@ -42,14 +49,15 @@ def run(p, n, precision="fp64", cfl=0.3, t_max=5.0, jitter=0.1, seed=1):
     for b in range(len(m.blocks)):
         L = s.layout(b)
         X = s.solution_points(b)                                   # [ndims, nupts, nelem]
-        U0 = fields.uniform(X, rho0, (VW, 0.0), PC, G)            # [V, nupts, nelem]
         Ue = fields.couette(X, G, PR, CPTW, VW, PC, H)
+        U0 = fields.uniform(X, rho0, (VW, 0.0), PC, G) if start == "uniform" else Ue   # [V, nupts, nelem]
         ub = torch.zeros((L["nupts"], L["nvars"], L["ld"]), dtype=dt_np, device="cuda")
         ub[:, :, :L["nelem"]] = torch.from_numpy(U0.transpose(1, 0, 2)).to(dt_np)
         u.append(ub)
         ex.append(torch.from_numpy(Ue[-1]).to(dt_np).cuda())      # exact total energy [nupts, nelem]
     h = H / n
     c = np.sqrt(G * PC / rho0)
+    # acoustic limit of RK4 with degree-p FR; the split triangles' inradius is ~0.3 h
     dt = cfl * h / ((c + VW) * (p + 1) ** 2)
     nper = int(np.ceil(0.1 / dt))
     dt = 0.1 / nper
@@ -71,7 +79,9 @@ def run(p, n, precision="fp64", cfl=0.3, t_max=5.0, jitter=0.1, seed=1):
         cur = sigma()
         if not np.isfinite(cur):
             raise FloatingPointError(f"Couette p={p} n={n}: non-finite state at t={t:.1f}")
-        if prev / cur <= 1.01:
+        if start == "uniform" and prev / cur <= 1.01:
+            break
+        if start != "uniform" and t >= t_end - 1e-9:
             break
         prev = cur
     s.check_finite(u)
@@ -91,13 +101,14 @@ def order(hs, sigmas):
     return float(coef[0]), float(se)
 
 
-def main(orders=(1, 2, 3, 4), meshes=(4, 6, 8, 12)):
+def main(orders=(1, 2, 3, 4), start="exact"):
+    print(f"start = {start}")
     print("| p | n x n cells | sigma(t_inf) | t_inf | RK4 steps |")
     print("|---|---|---|---|---|")
     for p in orders:
         hs, sg = [], []
-        for n in meshes:
-            r = run(p, n)
+        for n in ((4, 6, 8, 12) if p <= 2 else (3, 4, 6, 8)):
+            r = run(p, n, start=start)
             hs.append(r["h"])
             sg.append(r["sigma"])
             print(f"| {p} | {n} x {n} | {r['sigma']:.4e} | {r['t_inf']:.1f} | {r['steps']} |", flush=True)
@@ -106,4 +117,4 @@ def main(orders=(1, 2, 3, 4), meshes=(4, 6, 8, 12)):
 
 
 if __name__ == "__main__":
-    sys.exit(main())
+    sys.exit(main(start=sys.argv[1] if len(sys.argv) > 1 else "exact"))
