@@ -440,27 +440,45 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
     const Ref<T> rf = make_ref<T>(P);
     Gas<T, D>::rusanov(uL, uR, n, rf, gamma, F);
     if (NS) {
-        T qL[D][NV], qR[D][NV], fvL[D][NV], fvR[D][NV];
+        // LDG viscous part, one side at a time (the gradients and viscous flux
+        // of only one side are live at once)
+        T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
+        T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
+        T fvn[NV];
+        {
+            T q[D][NV], fv[D][NV];
 #pragma unroll
-        for (int j = 0; j < D; ++j)
+            for (int j = 0; j < D; ++j)
+#pragma unroll
+                for (int a = 0; a < NV; ++a) q[j][a] = QfL[j * qsL + oL + a * ldL];
+            Gas<T, D>::vis_flux(uL, q, rf, gm1, mu, kappa, fv);
 #pragma unroll
             for (int a = 0; a < NV; ++a) {
-                qL[j][a] = QfL[j * qsL + oL + a * ldL];
-                qR[j][a] = QfR[j * qsR + oR + a * ldR];
+                T acc = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) acc += n[i] * fv[i][a];
+                fvn[a] = wl * acc;
             }
-        T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
-        Gas<T, D>::vis_flux(uL, qL, rf, gm1, mu, kappa, fvL);
-        Gas<T, D>::vis_flux(uR, qR, rf, gm1, mu, kappa, fvR);
-        T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
+        }
+        {
+            T q[D][NV], fv[D][NV];
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+#pragma unroll
+                for (int a = 0; a < NV; ++a) q[j][a] = QfR[j * qsR + oR + a * ldR];
+            Gas<T, D>::vis_flux(uR, q, rf, gm1, mu, kappa, fv);
+#pragma unroll
+            for (int a = 0; a < NV; ++a) {
+                T acc = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) acc += n[i] * fv[i][a];
+                fvn[a] += wr * acc;
+            }
+        }
         T du[NV];
         Gas<T, D>::jump(uL, uR, rf, du);
 #pragma unroll
-        for (int a = 0; a < NV; ++a) {
-            T fv = T(0);
-#pragma unroll
-            for (int i = 0; i < D; ++i) fv += n[i] * (wl * fvL[i][a] + wr * fvR[i][a]);
-            F[a] = F[a] - fv + tau * du[a];
-        }
+        for (int a = 0; a < NV; ++a) F[a] = F[a] - fvn[a] + tau * du[a];
     }
     T mL = magL[k], mR = magR[k];
 #pragma unroll
