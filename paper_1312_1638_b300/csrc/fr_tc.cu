@@ -28,10 +28,11 @@
 //               state_lo op_hi, state_hi op_lo), committed to the stage's
 //               "empty" barrier and, after the last chunk of a work item, to
 //               its accumulator barrier;
-//   warps 2-5   converters: read the FP32 tile, subtract the perturbation
+//   next 4 or 8 warps
+//               converters: read the FP32 tile, subtract the perturbation
 //               reference where the rows are solution states, split into
 //               hi / lo and write the K-major core-matrix operand layout;
-//   warps 6-    epilogue: tcgen05.ld of the accumulators (TMEM lane quadrant
+//   the rest    epilogue: tcgen05.ld of the accumulators (TMEM lane quadrant
 //               = warp % 4; 12 warps interleave 16-row groups when the tile
 //               has one subtile, 4 warps when it has two), optional -1/J
 //               scaling, coalesced stores.  Direct global stores from four
@@ -101,7 +102,12 @@ __host__ __device__ constexpr int subtiles_for(int nrp) { return nrp <= 128 ? 2 
 constexpr int GX_EG = 4;                       // epilogue warp groups with the gradient transform
 constexpr int GX_PB = 2;                       // points whose metric terms are loaded together
 __host__ __device__ constexpr int epi_groups(int nt, int gd) { return gd ? GX_EG : nt == 2 ? 1 : 3; }
-__host__ __device__ constexpr int nthreads_for(int nt, int gd) { return 192 + 128 * epi_groups(nt, gd); }
+// converter warps (sets of 4, one warp per scheduler each): two sets split
+// each chunk's conversion, except beside the register-hungry gradient epilogue
+__host__ __device__ constexpr int conv_warps(int gd) { return gd ? 4 : 8; }
+__host__ __device__ constexpr int nthreads_for(int nt, int gd) {
+    return 64 + 32 * conv_warps(gd) + 128 * epi_groups(nt, gd);
+}
 
 struct Layout {
     int nrp;                      // rows per block (MMA N)
@@ -287,6 +293,7 @@ template <int KIND, int NT, int GD>
 __global__ void __launch_bounds__(nthreads_for(NT, GD), 1)
 tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2) {
     constexpr int EG = epi_groups(NT, GD);
+    constexpr int CONVW = conv_warps(GD);
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[MAX_NST], bar_conv[MAX_NST], bar_empty[MAX_NST];
     __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
@@ -306,7 +313,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
     if (tid == 0) {
         for (int s = 0; s < L.nst; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bar_conv[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_conv[s])), "r"(32 * CONVW));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[s])));
         }
         for (int b = 0; b < 2; ++b) {
@@ -396,9 +403,11 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
             }
             if (!ok) atomicOr(&a.flags[1], 1);
         }
-    } else if (warp < 6) {
+    } else if (warp < 2 + CONVW) {
         // ---------------------------------------------------------- converters
-        const int ct = tid - 64;                       // state column within a subtile = MMA A row
+        // CONVW / 4 sets of 128 threads share each chunk's (subtile, 16-byte K group) pieces
+        const int ct = (tid - 64) & 127;               // state column within a subtile = MMA A row
+        const int cset = (tid - 64) >> 7;
         constexpr int ncols = NT * BN;
         int it = 0;
         for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x) {
@@ -422,6 +431,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                     const int cc = t * BN + ct;
 #pragma unroll
                     for (int g = 0; g < ROWB / 16; ++g) {
+                        if ((t * (ROWB / 16) + g) % (CONVW / 4) != cset) continue;
                         constexpr int PER = 16 / ESZ;
                         float x[PER];
 #pragma unroll
@@ -457,11 +467,11 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                 mbar_arrive(smem_u32(&bar_conv[s]));
             }
         }
-        if (!ok && ct == 0) atomicOr(&a.flags[1], 1);
+        if (!ok && tid == 64) atomicOr(&a.flags[1], 1);
     } else {
         // ---------------------------------------------------------- epilogue
         const int q = warp & 3;                        // TMEM lane quadrant of this warp
-        const int grp = (warp - 6) >> 2;               // 16-row groups grp, grp + EG, ...
+        const int grp = (warp - 2 - CONVW) >> 2;       // 16-row groups grp, grp + EG, ...
         int wc = 0;
         for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x, ++wc) {
             const int tl = w / a.nrb, rb = w - tl * a.nrb;
@@ -518,7 +528,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(smem_u32(&bar_tempty[b]));
         }
-        if (!ok && tid == 192) atomicOr(&a.flags[1], 1);
+        if (!ok && tid == 64 + 32 * CONVW) atomicOr(&a.flags[1], 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
