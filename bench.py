@@ -182,6 +182,10 @@ def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False):
     if name == "gradfpts_gemm":
         return (nu + nf) * V * s * E, 2.0 * nf * nu * V * E
     if name == "tdivf_gemm":
+        if fused:
+            # RK4 stage combination in the epilogue: the stages read/write 3, 4, 4, 2
+            # values per entry (u, acc, tmp) instead of writing R
+            return ((nf + D * nu) * V + nu) * s * E + 13 * nu * V * s * E / 4, 2.0 * nu * (nf + D * nu) * V * E
         return ((nf + D * nu + nu) * V + nu) * s * E, 2.0 * nu * (nf + D * nu) * V * E
     if name == "gradcoru":
         return (2 * D * nu * V + D * D * nu + nu) * s * E, 0.0

@@ -104,8 +104,9 @@ typedef struct {
      * rows of M0 sum to one, rows of M4 to zero), pressure is formed as
      * p' = (gamma-1)(E' - rho|v|^2/2), the momentum flux carries p' and the
      * energy flux is v (E' + p' - h_ref rho') with h_ref = gamma E_ref / ref_rho,
-     * and the result is finished with R_E += h_ref R_rho.  The energy split is
-     * exact by linearity of R in the fluxes; dropping the constant pressure
+     * and h_ref times the mass flux is added back to every energy flux (point
+     * and common) before the divergence, so R_E comes out whole.  The energy
+     * split is exact by linearity of R in the fluxes; dropping the constant pressure
      * flux is exact wherever the mesh preserves a free stream (affine
      * elements, quadratic 2D and trilinear 3D elements at p >= 2).  Choosing
      * the mean density and pressure keeps FP32 / split-precision results

@@ -96,7 +96,7 @@ struct DevBndGroup {           // boundary flux points of one block and one type
 // kernel when profiling is enabled.
 enum KernelId {
     K_DISU = 0, K_COMM_SOL, K_COMM_SOL_BC, K_TGRADU, K_GRADCORU, K_GRADFPTS, K_TDISF, K_COMM_FLUX,
-    K_COMM_FLUX_BC, K_TDIVF, K_RK_STAGE, K_ENERGY_FIX, K_NKERNELS
+    K_COMM_FLUX_BC, K_TDIVF, K_RK_STAGE, K_NKERNELS
 };
 extern const char* const kKernelNames[K_NKERNELS];
 

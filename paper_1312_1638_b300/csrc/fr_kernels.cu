@@ -367,6 +367,10 @@ __global__ void tflux_kernel(int nupts, int64_t nelem, int64_t ld, const T* __re
 #pragma unroll
             for (int a = 0; a < NV; ++a) f[i][a] -= fv[i][a];
     }
+    // energy split undone here: (E - h_ref rho) flux + h_ref (rho flux); R is
+    // linear in the fluxes, so R_E comes out whole
+#pragma unroll
+    for (int i = 0; i < D; ++i) f[i][NV - 1] += rf.h * f[i][0];
     T adj[D][D];
 #pragma unroll
     for (int i = 0; i < D; ++i)
@@ -480,6 +484,7 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
 #pragma unroll
         for (int a = 0; a < NV; ++a) F[a] = F[a] - fvn[a] + tau * du[a];
     }
+    F[NV - 1] += rf.h * F[0];                            // energy split undone (see tflux_kernel)
     T mL = magL[k], mR = magR[k];
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
@@ -528,38 +533,27 @@ __global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __re
             F[a] = F[a] - fv + tau * du[a];
         }
     }
+    F[NV - 1] += rf.h * F[0];                            // energy split undone (see tflux_kernel)
     T m = mag[k];
 #pragma unroll
     for (int a = 0; a < NV; ++a) Uf[o + a * ld] = m * F[a];
 }
 
-// R_E += h_ref R_rho: undo the energy split of the perturbation form
-template <typename T>
-__global__ void energy_fix_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, T* __restrict__ R, T href) {
-    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int s = blockIdx.y;
-    if (n >= nelem) return;
-    T* r = R + (int64_t)s * nvars * ld + n;
-    r[(int64_t)(nvars - 1) * ld] += href * r[0];
-}
 
 // ============================================================ RK4 combine
-// RK4 stage combine per solution point, all variables at once, with the
-// energy-split correction k_E += h_ref k_rho applied to the stage RHS first
-// (k lives in tmp):
+// RK4 stage combine per solution point, all variables at once (k lives in tmp):
 //   mode 0 (first stage):  acc = u + a_acc k;  tmp = u + a_tmp k
 //   mode 1:                acc += a_acc k;     tmp = u + a_tmp k
 //   mode 2 (last stage):   u = acc + a_acc k
 template <typename T>
 __global__ void rk_point_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, T* __restrict__ acc,
-                                T* __restrict__ tmp, T* __restrict__ u, T a_acc, T a_tmp, T href, int mode) {
+                                T* __restrict__ tmp, T* __restrict__ u, T a_acc, T a_tmp, int mode) {
     int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s = blockIdx.y;
     if (n >= nelem) return;
     const int64_t base = (int64_t)s * nvars * ld + n;
     T k[5];
     for (int a = 0; a < nvars; ++a) k[a] = tmp[base + a * ld];
-    k[nvars - 1] += href * k[0];
     for (int a = 0; a < nvars; ++a) {
         const int64_t i = base + a * ld;
         if (mode == 2) {
@@ -608,7 +602,7 @@ __global__ void check_finite_kernel(int npts, int nvars, int64_t nelem, int64_t 
 // ============================================================ profiling
 const char* const kKernelNames[K_NKERNELS] = {"disu_gemm", "comm_sol", "comm_sol_bc", "tgradu_gemm",
                                               "gradcoru", "gradfpts_gemm", "tdisf", "comm_flux",
-                                              "comm_flux_bc", "tdivf_gemm", "rk_stage", "energy_fix"};
+                                              "comm_flux_bc", "tdivf_gemm", "rk_stage"};
 
 static cudaEvent_t prof_event(DevCtx& c) {
     if (!c.pool.empty()) {
@@ -682,9 +676,17 @@ __global__ void pack_kernel(int64_t n, int nvars, int ncomp, const uint32_t* __r
         for (int a = 0; a < nvars; ++a) buf[(int64_t)(j * nvars + a) * nslots + sl] = src[j * qs + o + a * ld];
 }
 
+// RK stage to fuse into the divergence GEMM's epilogue (tensor-core paths):
+// the stage's k is not stored; see tc::RkFuse
+struct RkStage {
+    int mode;
+    double a, b;
+    void* const* u;           // the step's state (per block)
+};
+
 template <typename T, int D>
-static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st, bool energy_fix = true,
-                            int phases = PH_ALL) {
+static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st, int phases = PH_ALL,
+                            const RkStage* rk = nullptr) {
     constexpr int NV = D + 2;
     const bool ns = c.system == 1;
     Sub<T> sub{};
@@ -856,15 +858,17 @@ phase_c2:
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
         prof_begin(c, K_TDIVF, st);
-        FR_TRY(op_gemm<T>(c, B.opR, B.tcR, B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.Uf, B.Q, (int64_t)NV * B.ld, r[b], 1,
-                   B.rcpdjac, B.ld, st, 0, 0, Sub<T>{}));
-        prof_end(c, st);
-        if (energy_fix && c.prm.ref_h != 0.0) {
-            prof_begin(c, K_ENERGY_FIX, st);
-            energy_fix_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(B.nupts, NV, B.nelem, B.ld, (T*)r[b],
-                                                                            T(c.prm.ref_h));
-            prof_end(c, st);
+        if (rk && c.precision >= 2) {
+            const tc::RkFuse f{rk->mode, (float)rk->a, (float)rk->b, (float*)rk->u[b], (float*)B.rk_acc,
+                               (float*)B.rk_tmp, B.nelem};
+            FR_TRY(tc::gemm(c.precision == 3 ? 0 : 1, B.nupts, B.nfpts, D * B.nupts, B.tcR, (const float*)B.Uf,
+                            (const float*)B.Q, (int64_t)NV * B.ld, nullptr, 1, (const float*)B.rcpdjac, B.ld, 0,
+                            tc::SubRef{}, c.flags, st, nullptr, &f));
+        } else {
+            FR_TRY(op_gemm<T>(c, B.opR, B.tcR, B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.Uf, B.Q, (int64_t)NV * B.ld,
+                              r[b], 1, B.rcpdjac, B.ld, st, 0, 0, Sub<T>{}));
         }
+        prof_end(c, st);
     }
     return cudaGetLastError();
 }
@@ -893,35 +897,38 @@ cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t s
 
 cudaError_t launch_rhs_phases(DevCtx& c, void* const* u, void* const* r, int phases, cudaStream_t st) {
     if (c.precision == 0)
-        return c.ndims == 2 ? rhs_impl<double, 2>(c, u, r, st, true, phases)
-                            : rhs_impl<double, 3>(c, u, r, st, true, phases);
-    return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st, true, phases) : rhs_impl<float, 3>(c, u, r, st, true, phases);
+        return c.ndims == 2 ? rhs_impl<double, 2>(c, u, r, st, phases) : rhs_impl<double, 3>(c, u, r, st, phases);
+    return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st, phases) : rhs_impl<float, 3>(c, u, r, st, phases);
 }
 
-// RHS without the final energy-split correction (the RK4 stage kernels apply it)
-static cudaError_t launch_rhs_nofix(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {
-    if (c.precision == 0)
-        return c.ndims == 2 ? rhs_impl<double, 2>(c, u, r, st, false) : rhs_impl<double, 3>(c, u, r, st, false);
-    return c.ndims == 2 ? rhs_impl<float, 2>(c, u, r, st, false) : rhs_impl<float, 3>(c, u, r, st, false);
-}
 
 template <typename T>
 static cudaError_t rk4_impl(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {
     std::vector<void*> tmp(c.blocks.size());
     for (size_t b = 0; b < c.blocks.size(); ++b) tmp[b] = c.blocks[b].rk_tmp;
+    bool fuse = c.precision >= 2;
+    for (auto& B : c.blocks) fuse = fuse && tc::rk_fusable(B.nupts);
     for (int step = 0; step < nsteps; ++step) {
         const double a_acc[4] = {dt / 6, dt / 3, dt / 3, dt / 6};
         const double a_tmp[3] = {dt / 2, dt / 2, dt};
         for (int s = 0; s < 4; ++s) {
             // stage 1 reads u directly; later stages read the stage state in tmp
-            cudaError_t e = launch_rhs_nofix(c, s == 0 ? u : tmp.data(), tmp.data(), st);
+            if (fuse) {
+                // tensor-core path: the stage combination runs in the divergence GEMM's epilogue
+                const RkStage rk{s == 0 ? 0 : (s == 3 ? 2 : 1), a_acc[s], s < 3 ? a_tmp[s] : 0.0, u};
+                cudaError_t e = c.ndims == 2 ? rhs_impl<T, 2>(c, s == 0 ? u : tmp.data(), tmp.data(), st, PH_ALL, &rk)
+                                             : rhs_impl<T, 3>(c, s == 0 ? u : tmp.data(), tmp.data(), st, PH_ALL, &rk);
+                if (e != cudaSuccess) return e;
+                continue;
+            }
+            cudaError_t e = launch_rhs(c, s == 0 ? u : tmp.data(), tmp.data(), st);
             if (e != cudaSuccess) return e;
             for (size_t b = 0; b < c.blocks.size(); ++b) {
                 DevBlock& B = c.blocks[b];
                 prof_begin(c, K_RK_STAGE, st);
                 rk_point_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
                     B.nupts, B.nvars, B.nelem, B.ld, (T*)B.rk_acc, (T*)B.rk_tmp, (T*)u[b], T(a_acc[s]),
-                    T(s < 3 ? a_tmp[s] : 0.0), T(c.prm.ref_h), s == 0 ? 0 : (s == 3 ? 2 : 1));
+                    T(s < 3 ? a_tmp[s] : 0.0), s == 0 ? 0 : (s == 3 ? 2 : 1));
                 prof_end(c, st);
             }
         }
@@ -934,17 +941,16 @@ cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStr
 }
 
 // ------------------------------------------------------------------ Euler / DOPRI5
-// forward Euler stage: u += dt k, with the energy-split correction k_E += h_ref k_rho
+// forward Euler stage: u += dt k
 template <typename T>
 __global__ void euler_point_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, const T* __restrict__ k,
-                                   T* __restrict__ u, T dt, T href) {
+                                   T* __restrict__ u, T dt) {
     int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s = blockIdx.y;
     if (n >= nelem) return;
     const int64_t base = (int64_t)s * nvars * ld + n;
     T kk[5];
     for (int a = 0; a < nvars; ++a) kk[a] = k[base + a * ld];
-    kk[nvars - 1] += href * kk[0];
     for (int a = 0; a < nvars; ++a) u[base + a * ld] += dt * kk[a];
 }
 
@@ -1002,13 +1008,13 @@ static cudaError_t euler_impl(DevCtx& c, void* const* u, double dt, int nsteps, 
     std::vector<void*> k(c.blocks.size());
     for (size_t b = 0; b < c.blocks.size(); ++b) k[b] = c.blocks[b].rk_tmp;
     for (int step = 0; step < nsteps; ++step) {
-        cudaError_t e = launch_rhs_nofix(c, u, k.data(), st);
+        cudaError_t e = launch_rhs(c, u, k.data(), st);
         if (e != cudaSuccess) return e;
         for (size_t b = 0; b < c.blocks.size(); ++b) {
             DevBlock& B = c.blocks[b];
             prof_begin(c, K_RK_STAGE, st);
             euler_point_kernel<T><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
-                B.nupts, B.nvars, B.nelem, B.ld, (const T*)k[b], (T*)u[b], T(dt), T(c.prm.ref_h));
+                B.nupts, B.nvars, B.nelem, B.ld, (const T*)k[b], (T*)u[b], T(dt));
             prof_end(c, st);
         }
     }

@@ -34,8 +34,8 @@
 //               hi / lo and write the K-major core-matrix operand layout;
 //   the rest    epilogue: tcgen05.ld of the accumulators (TMEM lane quadrant
 //               = warp % 4; 12 warps interleave 16-row groups when the tile
-//               has one subtile, 4 warps when it has two), optional -1/J
-//               scaling, coalesced stores.  Direct global stores from four
+//               has one subtile, 8 when it has two), optional -1/J
+//               scaling or the fused RK stage, coalesced stores.  Direct global stores from four
 //               warps could not drain a 160-row accumulator as fast as the
 //               MMAs fill the next one; twelve warps keep more stores in
 //               flight.
@@ -101,7 +101,7 @@ __host__ __device__ constexpr int subtiles_for(int nrp) { return nrp <= 128 ? 2 
 // (the gradient transform epilogue, gd > 0, holds more registers per thread)
 constexpr int GX_EG = 4;                       // epilogue warp groups with the gradient transform
 constexpr int GX_PB = 2;                       // points whose metric terms are loaded together
-__host__ __device__ constexpr int epi_groups(int nt, int gd) { return gd ? GX_EG : nt == 2 ? 1 : 3; }
+__host__ __device__ constexpr int epi_groups(int nt, int gd) { return gd ? GX_EG : nt == 2 ? 2 : 3; }
 // converter warps (sets of 4, one warp per scheduler each): two sets split
 // each chunk's conversion, except beside the register-hungry gradient epilogue
 __host__ __device__ constexpr int conv_warps(int gd) { return gd ? 4 : 8; }
@@ -222,6 +222,13 @@ struct TcArgs {
     const float* smat;
     int gD, gnu;
     int vinter;         // > 0: work order interleaves the vinter variables of one element range
+    // RK stage epilogue (epi = 3): k = -acc / J, then by rk_mode
+    //   0: rk_acc = u + rk_a k, rk_tmp = u + rk_b k;  1: rk_acc += rk_a k, rk_tmp = u + rk_b k;
+    //   2: u = rk_acc + rk_a k; only columns of real elements (col % ld < rk_nelem) are written
+    int rk_mode;
+    float rk_a, rk_b;
+    float *rk_u, *rk_acc, *rk_tmp;
+    int64_t rk_nelem;
 };
 
 // column tile of the tl-th tile in work order
@@ -484,15 +491,16 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 const int64_t col = (int64_t)tile * NT * BN + t * BN + q * 32 + lane;    // this thread's state column
-                const bool col_ok = col < a.N;
+                const bool col_ok = col < a.N && (a.epi != 3 || col % a.ld < a.rk_nelem);
                 const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT * L.nrp + t * L.nrp);
                 if constexpr (GD > 0) {
                     epi_grad<GD>(a, tcol, rbase / GD, mr / GD, 8 * grp, 8 * EG, col, col_ok);
                     continue;
                 }
                 const float* rcp_col =
-                    (a.epi == 1 && col_ok) ? a.rcp + (int64_t)rbase * a.ld + col % a.ld : nullptr;
+                    ((a.epi == 1 || a.epi == 3) && col_ok) ? a.rcp + (int64_t)rbase * a.ld + col % a.ld : nullptr;
                 float* c_col = a.C + (int64_t)rbase * a.N + col;
+                const int64_t i_col = (int64_t)rbase * a.N + col;     // index of (row rbase, col) in C / u / acc / tmp
 #pragma unroll 1
                 for (int r0 = 16 * grp; r0 < mr; r0 += 16 * EG) {
                     uint32_t r[16];
@@ -512,6 +520,36 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                             rc[j] = r0 + j < mr ? __ldg(rcp_col + (int64_t)(r0 + j) * a.ld) : 0.f;
                     }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if constexpr (NT == 2) {
+                      if (col_ok && a.epi == 3) {
+                        // fused RK stage: k never goes to memory.  All 16 rows of u / acc
+                        // are loaded before the first store (the stores may alias them
+                        // as far as the compiler knows).
+                        float uu[16], aa[16];
+                        const int64_t i0 = i_col + (int64_t)r0 * a.N;
+                        const bool need_u = a.rk_mode != 2, need_acc = a.rk_mode != 0;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const bool in = r0 + j < mr;
+                            uu[j] = (in && need_u) ? __ldg(a.rk_u + i0 + (int64_t)j * a.N) : 0.f;
+                            aa[j] = (in && need_acc) ? a.rk_acc[i0 + (int64_t)j * a.N] : 0.f;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (r0 + j < mr) {
+                                const float k = -__uint_as_float(r[j]) * rc[j];
+                                const int64_t i = i0 + (int64_t)j * a.N;
+                                if (a.rk_mode == 2) {
+                                    a.rk_u[i] = aa[j] + a.rk_a * k;
+                                } else {
+                                    a.rk_acc[i] = (a.rk_mode == 0 ? uu[j] : aa[j]) + a.rk_a * k;
+                                    a.rk_tmp[i] = uu[j] + a.rk_b * k;
+                                }
+                            }
+                        }
+                        continue;
+                      }
+                    }
                     if (col_ok) {
                         float* cp = c_col + (int64_t)r0 * a.N;
 #pragma unroll
@@ -639,6 +677,8 @@ static cudaError_t set_smem() {
     return cudaSuccess;
 }
 
+bool rk_fusable(int M) { return subtiles_for(row_blocks(M, 1).nrp) == 2; }
+
 cudaError_t prepare() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -675,7 +715,7 @@ static cudaError_t launch(const TcArgs& a, int nt, const CUtensorMap& m1, const 
 
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
-                 cudaStream_t st, const GradXform* gx) {
+                 cudaStream_t st, const GradXform* gx, const RkFuse* rk) {
     if (!g_nsm) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
@@ -713,6 +753,23 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
     a.gD = gx ? gx->ndims : 0;
     a.gnu = gx ? gx->nupts : 0;
     if (gx) a.epi = 2;
+    a.rk_mode = 0;
+    a.rk_a = a.rk_b = 0.f;
+    a.rk_u = a.rk_acc = a.rk_tmp = nullptr;
+    a.rk_nelem = 0;
+    if (rk) {
+        if (nt != 2) return cudaErrorInvalidValue;          // fused only into the two-subtile kernels
+        if (gx || !rcp || rk->mode < 0 || rk->mode > 2 || !rk->u || !rk->acc || (rk->mode < 2 && !rk->tmp))
+            return cudaErrorInvalidValue;
+        a.epi = 3;
+        a.rk_mode = rk->mode;
+        a.rk_a = rk->a;
+        a.rk_b = rk->b;
+        a.rk_u = rk->u;
+        a.rk_acc = rk->acc;
+        a.rk_tmp = rk->tmp;
+        a.rk_nelem = rk->nelem;
+    }
     // the variables of one element range share the metric terms through L2
     a.vinter = (gx && gx->nvars > 1 && ld % (nt * BN) == 0 && N == (int64_t)gx->nvars * ld) ? gx->nvars : 0;
     CUtensorMap m1, m2;

@@ -43,11 +43,27 @@ cudaError_t prepare();
 // r, column c by -rcp[r][c % ld] (-1/J).  Rows of segment `subseg` (1 or 2;
 // 0 = none) have sub.v[c / ld] subtracted (perturbation form).  flags[1] is
 // raised if a wait gives up.  gx (optional) selects the gradient transform
-// epilogue, with rcp = 1/J.  Host-side tensor-map encoding failures and
+// epilogue, with rcp = 1/J; rk (optional, epi = 1 semantics) the RK stage
+// epilogue (C unused).  Host-side tensor-map encoding failures and
 // inconsistent arguments return cudaErrorInvalidValue.
+// RK stage fused into the -1/J epilogue: with k = -acc / J (never stored),
+// mode 0: acc = u + a k, tmp = u + b k; mode 1: acc += a k, tmp = u + b k;
+// mode 2: u = acc + a k.  u, acc, tmp have the layout of C; only columns
+// c with c % ld < nelem (real elements) are written.
+struct RkFuse {
+    int mode;
+    float a, b;
+    float *u, *acc, *tmp;
+    int64_t nelem;
+};
+
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
-                 cudaStream_t st, const GradXform* gx = nullptr);
+                 cudaStream_t st, const GradXform* gx = nullptr, const RkFuse* rk = nullptr);
+
+// whether an M-row operator runs with two 128-column subtiles, the kernels
+// that carry the fused RK stage epilogue (M <= 128)
+bool rk_fusable(int M);
 
 }  // namespace tc
 }  // namespace fr
