@@ -100,7 +100,6 @@ __host__ __device__ constexpr int subtiles_for(int nrp) { return nrp <= 128 ? 2 
 // epilogue warp groups (4 warps each, one per TMEM lane quadrant)
 // (the gradient transform epilogue, gd > 0, holds more registers per thread)
 constexpr int GX_EG = 4;                       // epilogue warp groups with the gradient transform
-constexpr int GX_PB = 2;                       // points whose metric terms are loaded together
 __host__ __device__ constexpr int epi_groups(int nt, int gd) { return gd ? GX_EG : nt == 2 ? 2 : 3; }
 // converter warps (sets of 4, one warp per scheduler each): two sets split
 // each chunk's conversion, except beside the register-hungry gradient epilogue
@@ -238,7 +237,7 @@ __device__ __forceinline__ int col_tile(const TcArgs& a, int tl) {
     return (tl % a.vinter) * per + tl / a.vinter;
 }
 
-// Epilogue of the gradient transform: 8-point units of one row block,
+// Epilogue of the gradient transform: 4-point units of one row block,
 // q_i = acc(s, i) from tensor memory, Q_j(s) = rcp(s) sum_i adj_ij(s) q_i
 // (Q = J^-T Q~, with adj = J J^-1 and rcp = 1/J stored per point).
 template <int D>
@@ -251,41 +250,38 @@ __device__ __forceinline__ void epi_grad(const TcArgs& a, uint32_t tcol, int p0,
     const int64_t es = (int64_t)a.gnu * ld;           // stride between the D*D metric entries
 #pragma unroll 1
     for (int u0 = u_first; u0 < np; u0 += u_step) {
-        uint32_t r[8 * D];
+        uint32_t r[4 * D];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            const uint32_t ta = tcol + (uint32_t)(u0 * D + 8 * k);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(r[8 * k + 0]), "=r"(r[8 * k + 1]), "=r"(r[8 * k + 2]), "=r"(r[8 * k + 3]),
-                  "=r"(r[8 * k + 4]), "=r"(r[8 * k + 5]), "=r"(r[8 * k + 6]), "=r"(r[8 * k + 7])
-                : "r"(ta));
+            const uint32_t ta = tcol + (uint32_t)(u0 * D + 4 * k);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r[4 * k + 0]), "=r"(r[4 * k + 1]), "=r"(r[4 * k + 2]), "=r"(r[4 * k + 3])
+                         : "r"(ta));
         }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (!col_ok) continue;
+        // the metric terms of the unit's 4 points are loaded while the tensor-memory load is in flight
+        float m[4][D * D], rj[4];
+        if (col_ok) {
 #pragma unroll
-        for (int pg = 0; pg < 8; pg += GX_PB) {
-            // the metric terms of GX_PB points are loaded before any of them is used
-            float m[GX_PB][D * D], rj[GX_PB];
-#pragma unroll
-            for (int k = 0; k < GX_PB; ++k) {
-                const int s = min(p0 + u0 + pg + k, p0 + np - 1);       // clamped: rows past np are not stored
+            for (int k = 0; k < 4; ++k) {
+                const int s = min(p0 + u0 + k, p0 + np - 1);          // clamped: rows past np are not stored
                 const float* ps = sm + (int64_t)s * ld;
 #pragma unroll
                 for (int e = 0; e < D * D; ++e) m[k][e] = __ldg(ps + e * es);
                 rj[k] = __ldg(rc + (int64_t)s * ld);
             }
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!col_ok) continue;
 #pragma unroll
-            for (int k = 0; k < GX_PB; ++k) {
-                const int s = p0 + u0 + pg + k;
-                if (u0 + pg + k < np) {
+        for (int k = 0; k < 4; ++k) {
+            const int s = p0 + u0 + k;
+            if (u0 + k < np) {
 #pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        float acc = 0.f;
+                for (int j = 0; j < D; ++j) {
+                    float acc = 0.f;
 #pragma unroll
-                        for (int i = 0; i < D; ++i) acc += m[k][i * D + j] * __uint_as_float(r[(pg + k) * D + i]);
-                        cc[((int64_t)j * a.gnu + s) * N] = acc * rj[k];
-                    }
+                    for (int i = 0; i < D; ++i) acc += m[k][i * D + j] * __uint_as_float(r[k * D + i]);
+                    cc[((int64_t)j * a.gnu + s) * N] = acc * rj[k];
                 }
             }
         }
@@ -494,7 +490,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                 const bool col_ok = col < a.N && (a.epi != 3 || col % a.ld < a.rk_nelem);
                 const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT * L.nrp + t * L.nrp);
                 if constexpr (GD > 0) {
-                    epi_grad<GD>(a, tcol, rbase / GD, mr / GD, 8 * grp, 8 * EG, col, col_ok);
+                    epi_grad<GD>(a, tcol, rbase / GD, mr / GD, 4 * grp, 4 * EG, col, col_ok);
                     continue;
                 }
                 const float* rcp_col =
