@@ -443,6 +443,9 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
     T gamma = T(P.gamma);
     const Ref<T> rf = make_ref<T>(P);
     Gas<T, D>::rusanov(uL, uR, n, rf, gamma, F);
+    // the energy split is undone on each part of the flux as it is formed
+    // (h_ref times the mass component; see tflux_kernel)
+    F[NV - 1] += rf.h * F[0];
     if (NS) {
         // LDG viscous part, one side at a time (the gradients and viscous flux
         // of only one side are live at once)
@@ -481,10 +484,11 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
         }
         T du[NV];
         Gas<T, D>::jump(uL, uR, rf, du);
+        fvn[NV - 1] += rf.h * fvn[0];
+        du[NV - 1] += rf.h * du[0];
 #pragma unroll
         for (int a = 0; a < NV; ++a) F[a] = F[a] - fvn[a] + tau * du[a];
     }
-    F[NV - 1] += rf.h * F[0];                            // energy split undone (see tflux_kernel)
     T mL = magL[k], mR = magR[k];
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
@@ -510,6 +514,7 @@ __global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __re
     bool grad_is_qL = Gas<T, D>::ghosts(bctype, uL, P, rf, gi, gl);
     T gamma = T(P.gamma);
     Gas<T, D>::rusanov(uL, gi, n, rf, gamma, F);
+    F[NV - 1] += rf.h * F[0];                            // energy split undone, part by part
     if (NS) {
         T qL[D][NV], fvL[D][NV], fvR[D][NV], qg[D][NV];
 #pragma unroll
@@ -523,17 +528,20 @@ __global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __re
         Gas<T, D>::vis_flux(uL, qL, rf, gm1, mu, kappa, fvL);
         Gas<T, D>::vis_flux(gl, qg, rf, gm1, mu, kappa, fvR);
         T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
-        T du[NV];
+        T du[NV], fvn[NV];
         Gas<T, D>::jump(uL, gl, rf, du);
 #pragma unroll
         for (int a = 0; a < NV; ++a) {
             T fv = T(0);
 #pragma unroll
             for (int i = 0; i < D; ++i) fv += n[i] * (wl * fvL[i][a] + wr * fvR[i][a]);
-            F[a] = F[a] - fv + tau * du[a];
+            fvn[a] = fv;
         }
+        fvn[NV - 1] += rf.h * fvn[0];
+        du[NV - 1] += rf.h * du[0];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) F[a] = F[a] - fvn[a] + tau * du[a];
     }
-    F[NV - 1] += rf.h * F[0];                            // energy split undone (see tflux_kernel)
     T m = mag[k];
 #pragma unroll
     for (int a = 0; a < NV; ++a) Uf[o + a * ld] = m * F[a];
