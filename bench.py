@@ -52,6 +52,7 @@ def _args():
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16x3 tensor-core comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed quad/triangle annulus leg")
     return ap.parse_args()
 
 
@@ -451,6 +452,51 @@ def main():
     s.close()
     del u
     torch.cuda.empty_cache()
+    # mixed-mesh workload: 2D NS on the annulus (100k quads + 60k triangles, p = 4, Re 100, M 0.2)
+    mixed = None
+    if not a.no_mixed:
+        from fr_inputs import annulus_mixed
+        p_inf = 1.0 / (1.4 * 0.2 ** 2)
+        mprm = dict(gamma=1.4, mu=0.01, prandtl=0.72, ldg_beta=0.5, ldg_tau=0.1, bc_rho=1.0, bc_v=(1.0, 0.0, 0.0),
+                    bc_p=p_inf, outflow_p=p_inf, wall_cpTw=1.4 / 0.4 * p_inf, ref_rho=1.0, ref_p=p_inf)
+        mm = annulus_mixed()
+        mixed = dict(workload="2D NS annulus r in [0.5, 20], 100,000 quads (curved wall ring) + 60,000 triangles, "
+                              "p=4, Re 100, M 0.2, free-stream state plus a seeded smooth perturbation")
+        for prec, nrep in ((a.precision, 20), ("fp64", 3)):
+            sm = fr.Solver(mm, 4, "ns", prec, device=local, **mprm)
+            dtp = torch.float64 if prec == "fp64" else torch.float32
+            um, mdof = [], 0
+            for b in range(len(mm.blocks)):
+                X = sm.solution_points(b)
+                Ub = fields.smooth_random(X, seed=3, amp=0.1, vel0=(1.0, 0.0), p0=p_inf).transpose(1, 0, 2)
+                um.append(torch.from_numpy(sm.pack(b, Ub)).to(dtp).cuda())
+                mdof += Ub.size
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if prec == "fp64":
+                rm = [torch.empty_like(x) for x in um]
+                sm.rhs(um, rm, stream)
+                e0.record(stream)
+                for _ in range(nrep):
+                    sm.rhs(um, rm, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                mixed["fp64_gdofs_per_rhs"] = mdof * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
+            else:
+                # dt well inside the viscous limit of the wall ring (h ~ 0.006, p = 4, mu = 0.01)
+                sm.rk4(um, 2e-6, 3, stream)
+                e0.record(stream)
+                sm.rk4(um, 2e-6, nrep, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                mixed[f"{prec}_gdofs_per_rk_stage"] = mdof * 4 * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
+                mixed["ms_per_rk4_step"] = e0.elapsed_time(e1) / nrep
+            sm.check_finite(um)
+            st_m = sm.sync_status()
+            mixed[f"{prec}_status"] = "ok" if st_m == fr.OK else fr.STATUS_NAMES[st_m]
+            mixed["dof"] = mdof
+            sm.close()
+            del um
+            torch.cuda.empty_cache()
     fp32 = rhs_leg("fp32", 3) if (not a.no_fp32 and a.precision != "fp32") else None
     fp64 = rhs_leg("fp64", 2) if (not a.no_fp64 and a.precision != "fp64") else None
     bf16 = rhs_leg("bf16x3", 3) if (not a.no_bf16 and a.precision != "bf16x3") else None
@@ -468,7 +514,7 @@ def main():
                     l2="inputs larger than L2 (state alone is %.1f GB)" % (u_init.numel() * u_init.element_size() / 1e9),
                     parallelism=f"replicas x{world}", setup_s=round(t_setup, 1)),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
-        clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16,
+        clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed,
         alu_peaks=alu_peaks, finite=finite_ok,
     )
     print(json.dumps(line))
