@@ -107,75 +107,20 @@ def test_autograd_gradcheck_tiny(torch):
     assert torch.autograd.gradcheck(f, (x0,), eps=1e-6, atol=1e-8, rtol=1e-6)
 
 
-def _kinetic_energy(w, u, nelem):
-    u = u[:, :, :nelem]
-    m2 = (u[:, 1:4] ** 2).sum(1)
-    return float((w * 0.5 * m2 / u[:, 0]).sum())
-
-
-def _kinetic_energy_grad(w, u, nelem):
-    g = np.zeros_like(u)
-    uu = u[:, :, :nelem]
-    m2 = (uu[:, 1:4] ** 2).sum(1)
-    g[:, 0, :nelem] = -0.5 * w * m2 / uu[:, 0] ** 2
-    for i in range(3):
-        g[:, 1 + i, :nelem] = w * uu[:, 1 + i] / uu[:, 0]
-    return g
-
-
-def _replicated(box, copies, L):
-    """`copies` disjoint copies of a periodic box in one element block, spaced
-    10 L apart along x; the box's own translations keep each copy periodic in
-    itself, so one RHS evaluates `copies` independent states."""
-    from fr_inputs import Mesh, Block
-    nodes = box.blocks[0].nodes
-    allnodes = np.concatenate([nodes + np.array([10.0 * L * c, 0.0, 0.0]) for c in range(copies)])
-    return Mesh(3, [Block("hex", allnodes)], box.bfaces, box.periodic)
-
-
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
 def test_rk4_adjoint_against_fp64_finite_differences(torch, prec):
     """c4 in miniature: 3D Euler, periodic 4^3 hexes, p=4, Taylor-Green + seeded
     perturbation, 50 RK4 steps dt=1e-3, checkpoints every 10; gradient of the
     volume-integrated kinetic energy vs FP64 central differences on 200
-    directions d ~ N(0, I) scaled per variable by its RMS (default_rng(4242)).
-    The FP64 trajectories run 8 directions at a time on 8 disjoint copies of
-    the box."""
-    from paper_1312_1638_b300 import fr
-    L = 2 * np.pi
-    m = periodic_box("hex", 4, 0.0, L)
-    o = FRSystem(m, 4, "euler")
-    w = o.quadrature_weights(0)
-    U = fields.perturbed_taylor_green(o.solution_coords(0), M=0.1).transpose(1, 0, 2).copy()
-    U = U.astype(np.float32).astype(np.float64)
-    n, dt, every, ndir, batch = 50, 1e-3, 10, 200, 8
-    s1 = fr.Solver(m, 4, "euler", prec, device=0)
-    ne = m.nelem
-    u0 = torch.from_numpy(s1.pack(0, U)).cuda()
-    uN = u0.clone()
-    s1.rk4([uN], dt, n)
-    lam = torch.from_numpy(_kinetic_energy_grad(w, uN.cpu().numpy().astype(np.float64), ne).astype(np.float32)).cuda()
-    s1.rk4_adjoint([u0], [lam], dt, n, every)
-    g = lam.cpu().numpy().astype(np.float64)[:, :, :ne]
-    rng = np.random.default_rng(4242)
-    rms = np.sqrt((U ** 2).mean(axis=(0, 2)))
-    dirs = [rng.standard_normal(U.shape) * rms[None, :, None] for _ in range(ndir)]
-    mr = _replicated(m, batch, L)
-    s64 = fr.Solver(mr, 4, "euler", "fp64", device=0)
-    bad = []
-    for k0 in range(0, ndir, batch):
-        ds = dirs[k0:k0 + batch]
-        eps = [1e-6 * np.sqrt((U ** 2).mean()) / np.sqrt((d ** 2).mean()) for d in ds]
-        res = []
-        for sign in (1.0, -1.0):
-            Ub = np.concatenate([U + sign * e * d for e, d in zip(eps, ds)], axis=2)
-            ub = torch.from_numpy(s64.pack(0, Ub)).cuda()
-            s64.rk4([ub], dt, n)
-            uh = ub.cpu().numpy()
-            res.append([_kinetic_energy(w, uh[:, :, c * ne:(c + 1) * ne], ne) for c in range(len(ds))])
-        for c, (d, e) in enumerate(zip(ds, eps)):
-            fd = (res[0][c] - res[1][c]) / (2 * e)
-            gd = float(np.sum(g * d))
-            if abs(gd - fd) > 1e-4 * (abs(fd) + 1e-3 * np.linalg.norm(g) * np.linalg.norm(d)):
-                bad.append((k0 + c, gd, fd))
-    assert not bad, bad[:5]
+    directions (tests/adjoint_fd_study.py)."""
+    from tests.adjoint_fd_study import fd_check
+    r = fd_check(4, 200, prec)
+    assert not r["bad"], r["bad"][:5]
+
+
+def test_rk4_adjoint_full_size_c4(torch):
+    """c4 at full size (16^3 hexes, 2.56 M DOF), FP32 adjoint, 16 of the 200
+    directions (the full set is the study's default run)."""
+    from tests.adjoint_fd_study import fd_check
+    r = fd_check(16, 16, "fp32")
+    assert not r["bad"], r["bad"][:5]
