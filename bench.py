@@ -497,6 +497,38 @@ def main():
             sm.close()
             del um
             torch.cuda.empty_cache()
+    # Taylor-Green workload at p = 3: 32^3 hex box (10.5 M DOF), split precision vs the FP64 GPU path
+    tgv32 = None
+    if not a.no_mixed:
+        mt = periodic_box("hex", 32, 0.0, 2 * np.pi)
+        tgv32 = dict(workload="3D NS Taylor-Green, periodic 32^3 hex box, p=3, Re 1600, M 0.1")
+        for prec, nrep in (("bf16x3", 20), (a.precision, 20), ("fp64", 3)):
+            st_ = fr.Solver(mt, 3, "ns", prec, device=local, **PRM, **REF)
+            dtp = torch.float64 if prec == "fp64" else torch.float32
+            Ut = fields.taylor_green(st_.solution_points(0), M=0.1)          # [V, nupts, nelem], host
+            ut = torch.from_numpy(st_.pack(0, Ut.transpose(1, 0, 2))).to(dtp).cuda()
+            tdof = Ut.size
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if prec == "fp64":
+                rt = [torch.empty_like(ut)]
+                st_.rhs([ut], rt, stream)
+                e0.record(stream)
+                for _ in range(nrep):
+                    st_.rhs([ut], rt, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tgv32["fp64_gdofs_per_rhs"] = tdof * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
+            else:
+                st_.rk4([ut], 2e-4, 3, stream)
+                e0.record(stream)
+                st_.rk4([ut], 2e-4, nrep, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tgv32[f"{prec}_gdofs_per_rk_stage"] = tdof * 4 * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
+            tgv32["dof"] = tdof
+            st_.close()
+            del ut, Ut
+            torch.cuda.empty_cache()
     fp32 = rhs_leg("fp32", 3) if (not a.no_fp32 and a.precision != "fp32") else None
     fp64 = rhs_leg("fp64", 2) if (not a.no_fp64 and a.precision != "fp64") else None
     bf16 = rhs_leg("bf16x3", 3) if (not a.no_bf16 and a.precision != "bf16x3") else None
@@ -514,7 +546,7 @@ def main():
                     l2="inputs larger than L2 (state alone is %.1f GB)" % (u_init.numel() * u_init.element_size() / 1e9),
                     parallelism=f"replicas x{world}", setup_s=round(t_setup, 1)),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
-        clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed,
+        clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed, tgv32_p3=tgv32,
         alu_peaks=alu_peaks, finite=finite_ok,
     )
     print(json.dumps(line))

@@ -1,0 +1,87 @@
+"""Full-size Taylor-Green workload: 3D Navier-Stokes on a periodic 32^3 hex
+box on [0, 2 pi]^3, p = 3 (64 points, 10.5 M DOF), Re 1600, Mach 0.1,
+Pr 0.71, LDG beta 1/2, tau 0.1 (perturbation form about the mean state).
+The RHS at t = 0 is compared with the oracle on every element in FP64, FP32,
+TF32x3 and BF16x3.  On this mesh the FP64 result moves by more than 1e-13 S
+under rounding-level changes of the DG correction operator (the oracle's
+exact-mass lift and its Radau closed form agree to 5e-14 but give RHS values
+about 1e-12 S apart in density and energy, growing like n^2), so the FP64
+bound is 1e-13 S plus twice that per-variable spread of the oracle's two
+constructions. after 10 RK4 steps of dt = 2e-4 the split-precision
+states are compared with the FP64 GPU path from the same initial state,
+componentwise within the RHS bound integrated over the interval plus the FP32
+rounding of the stage states."""
+
+import numpy as np
+import pytest
+
+from fr_inputs import periodic_box, fields
+from oracle.system import FRSystem
+from tests.libutil import ensure_built
+from tests.test_gpu_parity import TOL_C
+
+pytestmark = pytest.mark.gpu
+
+PRM = dict(gamma=1.4, mu=1.0 / 1600.0, prandtl=0.71, ldg_beta=0.5, ldg_tau=0.1)
+REF = dict(ref_rho=1.0, ref_p=1.0 / (1.4 * 0.1 ** 2))
+
+
+@pytest.fixture(scope="module")
+def case():
+    m = periodic_box("hex", 32, 0.0, 2 * np.pi)
+    o = FRSystem(m, 3, "ns", **PRM)
+    U = fields.taylor_green(o.solution_coords(0), M=0.1).transpose(1, 0, 2).copy()
+    U32 = U.astype(np.float32).astype(np.float64)
+    R64, S64 = o.rhs([U], scale=True)
+    R32, S32 = o.rhs([U32], scale=True)
+    # the same operator by the Radau closed form (DG member of the tensor construction)
+    el = o.eles[0]
+    el.M3 = el._vcjh_M3()
+    el.M6 = (el.fnorm.T[:, None, :] * el.M3[None, :, :]).reshape(el.ndims * el.nupts, el.nfpts)
+    Rr = o.rhs([U])[0]
+    spread = np.abs(Rr - R64[0]).max(axis=(0, 2))                  # per variable
+    return m, U, U32, (R64[0], S64[0]), (R32[0], S32[0]), spread
+
+
+def _solver(m, prec):
+    from paper_1312_1638_b300 import fr
+    return fr.Solver(m, 3, "ns", prec, device=0, **PRM, **REF)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
+def test_c2_rhs_full_size(case, prec):
+    import torch
+    ensure_built()
+    from paper_1312_1638_b300 import fr
+    m, U64, U32, (R64, S64), (R32, S32), spread = case
+    U, R, S = (U64, R64, S64) if prec == "fp64" else (U32, R32, S32)
+    s = _solver(m, prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = [torch.from_numpy(s.pack(0, U)).to(dt).cuda()]
+    r = [torch.full_like(u[0], float("nan"))]
+    s.rhs(u, r)
+    g = r[0][:, :, :U.shape[2]].double().cpu().numpy()
+    bound = TOL_C[prec] * S + (2 * spread[None, :, None] if prec == "fp64" else 0.0)
+    assert np.all(np.abs(g - R) <= bound), float(np.max(np.abs(g - R) / bound))
+    assert s.sync_status() == fr.OK
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_c2_ten_rk4_steps_vs_fp64_gpu(case, prec):
+    import torch
+    ensure_built()
+    m, U64, U32, _, (R32, S32), _ = case
+    dt, n = 2e-4, 10
+    ref = _solver(m, "fp64")
+    a = [torch.from_numpy(ref.pack(0, U32)).cuda()]
+    ref.rk4(a, dt, n)
+    A = a[0][:, :, :U32.shape[2]].cpu().numpy()
+    s = _solver(m, prec)
+    b = [torch.from_numpy(s.pack(0, U32)).float().cuda()]
+    s.rk4(b, dt, n)
+    B = b[0][:, :, :U32.shape[2]].double().cpu().numpy()
+    bound = TOL_C[prec] * 2 * S32 * n * dt + 16 * np.finfo(np.float32).eps * np.abs(A) * n
+    assert np.all(np.abs(A - B) <= bound), float(np.max(np.abs(A - B) / bound))
+    ref.close()
+    s.close()
