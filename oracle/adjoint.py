@@ -1,20 +1,32 @@
-"""Discrete adjoint of the Euler right-hand side and of classical RK4 (FP64).
+"""Discrete adjoint of the FR right-hand side (Euler and Navier-Stokes) and of
+classical RK4 (FP64).  Test infrastructure: only the tests, the smoke check
+and the benchmark's CPU baseline use it.
 
 Not in the paper: the transpose (dR/dU)^T lambda of the FR operator of
-Sec. 2 / App. A for the Euler equations, assembled by running the RHS steps
-backwards:
+Sec. 2 / App. A, assembled by running the RHS steps backwards.  Forward map:
 
-    R = -J^-1 [M3 D~ + (M1 - M3 M2) F~],   F~ = adj(J) f(U),
-    D~_L = |n|_L F(uL, uR, n),  D~_R = -|n|_R F(uL, uR, n),   uf = M0 U
+    uf = M0 U
+    (NS)  C = LDG common solution of uf (Sec. 4.3; boundary ghosts, App. C)
+          qt = M6 (C - uf) + M4 U,  Q = J^-T qt,  Qf = M0 Q (per direction)
+    F~ = adj(J) (f_inv(U) - f_vis(U, Q))
+    D~_L = |n|_L F(uL, uR, qL, qR, n),  D~_R = -|n|_R F(...)
+    R = -J^-1 [M3 D~ + (M1 - M3 M2) F~]
+
+Transpose:
 
     mu   = -J^-1 lambda
     g_D  = M3^T mu,  g_F = (M1 - M3 M2)^T mu  (= M1^T mu - M2^T g_D)
-    per pair:  a = |n|_L g_D,L - |n|_R g_D,R;  a_uL = (dF/duL)^T a,  a_uR = (dF/duR)^T a
-    boundary:  a_ub = (d F(ub, ghost(ub)) / dub)^T (|n| g_D)
-    out  = M0^T a_uf + (d f / dU)^T (adj(J)^T g_F)   (point-wise)
+    per pair:  a = |n|_L g_D,L - |n|_R g_D,R;  a_uL, a_uR, a_qL, a_qR = (dF/d.)^T a
+    boundary:  a_ub, a_qb = (d F(ub, ghosts(ub, qb)) / d.)^T (|n| g_D)
+    point-wise: G = adj(J)^T g_F;  a_U = (df/dU)^T G,  a_Q = (df/dQ)^T G
+    (NS)  a_Q += M0^T a_Qf;  a_qt = J^-1 a_Q (per point: adj(J) a_Q / det J)
+          a_C = M6^T a_qt;  a_uf -= a_C;  a_U += M4^T a_qt
+          a_uf += (dC/d uf)^T a_C   (both sides of a pair share C)
+    a_U += M0^T a_uf
 
-The local Jacobians (flux, Rusanov with its ghost states) are taken exactly
-by the complex-step method on the oracle's own complex-safe physics.
+The local Jacobians (fluxes, the Rusanov / LDG common flux with its ghost
+states, the boundary common solution) are taken exactly by the complex-step
+method on the oracle's own complex-safe physics.
 
 RK4 adjoint (u_{n+1} = u_n + dt/6 (k1 + 2 k2 + 2 k3 + k4), k_i = R(y_i)):
     w4 = J4^T (dt/6 l);  nu3 = dt/3 l + dt w4;    w3 = J3^T nu3
@@ -31,7 +43,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import physics as ph
-from .system import FRSystem, EULER
+from .system import FRSystem, NAVIER_STOKES
 
 H_CS = 1e-30          # complex-step size
 
@@ -49,12 +61,18 @@ def _local_jac_T(fun, u, a, nin):
     return out
 
 
-class EulerAdjoint:
-    """Adjoint of ``FRSystem.rhs`` (Euler only) and of ``FRSystem.rk4``."""
+def _scatter_grad(s, arrs, b, f, n, vals):
+    """Write gradient values [d, V, np] at flux points (b, f, n) into per-block
+    [d, nf, V, nel] arrays."""
+    for bb in np.unique(b):
+        m = b == bb
+        arrs[bb][:, f[m], :, n[m]] = vals[:, :, m].transpose(2, 0, 1)
+
+
+class FRAdjoint:
+    """Adjoint of ``FRSystem.rhs`` and of ``FRSystem.rk4``."""
 
     def __init__(self, sysm: FRSystem):
-        if sysm.system != EULER:
-            raise ValueError("the adjoint covers the Euler equations")
         self.s = sysm
 
     # ----------------------------------------------------------- RHS
@@ -62,48 +80,120 @@ class EulerAdjoint:
         """(dR/dU)^T lam for per-block arrays [nupts, nvars, nelem]."""
         s = self.s
         prm = s.prm
-        gamma = prm["gamma"]
+        gamma, beta, tau = prm["gamma"], prm["ldg_beta"], prm["ldg_tau"]
+        mu, pr = prm["mu"], prm["prandtl"]
+        ns = s.system == NAVIER_STOKES
         d, V = s.ndims, s.nvars
         P, B = s.pairs, s.bpairs
-        mu = [-l / g["det"].T[:, None, :] for l, g in zip(lam, s.geo)]
-        gD = [np.einsum("uf,uvn->fvn", el.M3, m) for el, m in zip(s.eles, mu)]
+        Uf, Q, Qf = s.gradients(U)
+        mu_ = [-l / g["det"].T[:, None, :] for l, g in zip(lam, s.geo)]
+        gD = [np.einsum("uf,uvn->fvn", el.M3, m) for el, m in zip(s.eles, mu_)]
         gF = [np.einsum("ua,uvn->avn", el.M1, m) - np.einsum("fa,fvn->avn", el.M2, gd)
-              for el, m, gd in zip(s.eles, mu, gD)]
-        # point-wise transformed flux: F~_i = sum_j adj_ij f_j(u)
-        out = []
+              for el, m, gd in zip(s.eles, mu_, gD)]
+
+        def vflux(w, q):
+            return ph.viscous_flux(w, q, gamma, mu, pr)
+
+        # point-wise transformed flux: F~_i = sum_j adj_ij f_j(u, q)
+        out, aQ = [], []
         for b, (el, g, u, gf) in enumerate(zip(s.eles, s.geo, U, gF)):
             nu = el.nupts
             gfi = gf.reshape(d, nu, V, -1)                              # [i, sigma, alpha, n]
             G = np.einsum("nuij,iuvn->juvn", g["adj"], gfi)             # adj^T g: [j, sigma, alpha, n]
             ua = u.transpose(1, 0, 2).reshape(V, -1)                    # [V, nu*nel]
             Ga = G.transpose(0, 2, 1, 3).reshape(d * V, -1)             # [(j, alpha), nu*nel]
-            flux = lambda w: ph.inviscid_flux(w, gamma).reshape(d * V, -1)
-            au = _local_jac_T(flux, ua, Ga, V).reshape(V, nu, -1).transpose(1, 0, 2)
-            out.append(au)
+            if ns:
+                qa = Q[b].transpose(0, 2, 1, 3).reshape(d * V, -1)      # [(j, alpha), nu*nel]
+
+                def flux(w, q):
+                    f = ph.inviscid_flux(w, gamma) - vflux(w, q.reshape(d, V, -1))
+                    return f.reshape(d * V, -1)
+                au = _local_jac_T(lambda w: flux(w, qa), ua, Ga, V)
+                aq = _local_jac_T(lambda w: flux(ua, w), qa, Ga, d * V)
+                aQ.append(aq.reshape(d, V, nu, -1).transpose(0, 2, 1, 3))     # [j, sigma, alpha, n]
+            else:
+                au = _local_jac_T(lambda w: ph.inviscid_flux(w, gamma).reshape(d * V, -1), ua, Ga, V)
+            out.append(au.reshape(V, nu, -1).transpose(1, 0, 2))
         # interface pairs
-        uf = [np.einsum("fu,uvn->fvn", el.M0, u) for el, u in zip(s.eles, U)]
-        auf = [np.zeros_like(x) for x in uf]
-        uL = s._gather(uf, P["bL"], P["fL"], P["nL"])
-        uR = s._gather(uf, P["bR"], P["fR"], P["nR"])
+        auf = [np.zeros_like(x) for x in Uf]
+        aQf = [np.zeros_like(x) for x in Qf] if ns else None
+        uL = s._gather(Uf, P["bL"], P["fL"], P["nL"])
+        uR = s._gather(Uf, P["bR"], P["fR"], P["nR"])
         a = P["magL"] * s._gather(gD, P["bL"], P["fL"], P["nL"]) - P["magR"] * s._gather(gD, P["bR"], P["fR"], P["nR"])
         n = P["nrm"]
-        aL = _local_jac_T(lambda w: ph.rusanov(w, uR, n, gamma), uL, a, V)
-        aR = _local_jac_T(lambda w: ph.rusanov(uL, w, n, gamma), uR, a, V)
+        if ns:
+            qL = s._gather_grad(Qf, P["bL"], P["fL"], P["nL"])
+            qR = s._gather_grad(Qf, P["bR"], P["fR"], P["nR"])
+
+            def Fp(wL, wR, zL, zR):
+                return (ph.rusanov(wL, wR, n, gamma)
+                        - ph.ldg_viscous_normal(vflux(wL, zL), vflux(wR, zR), n, beta) + tau * (wL - wR))
+            aL = _local_jac_T(lambda w: Fp(w, uR, qL, qR), uL, a, V)
+            aR = _local_jac_T(lambda w: Fp(uL, w, qL, qR), uR, a, V)
+            aqL = _local_jac_T(lambda w: Fp(uL, uR, w.reshape(d, V, -1), qR), qL.reshape(d * V, -1), a, d * V)
+            aqR = _local_jac_T(lambda w: Fp(uL, uR, qL, w.reshape(d, V, -1)), qR.reshape(d * V, -1), a, d * V)
+            _scatter_grad(s, aQf, P["bL"], P["fL"], P["nL"], aqL.reshape(d, V, -1))
+            _scatter_grad(s, aQf, P["bR"], P["fR"], P["nR"], aqR.reshape(d, V, -1))
+        else:
+            aL = _local_jac_T(lambda w: ph.rusanov(w, uR, n, gamma), uL, a, V)
+            aR = _local_jac_T(lambda w: ph.rusanov(uL, w, n, gamma), uR, a, V)
         s._scatter(auf, P["bL"], P["fL"], P["nL"], aL)
         s._scatter(auf, P["bR"], P["fR"], P["nR"], aR)
         if len(B["b"]):
-            ub = s._gather(uf, B["b"], B["f"], B["n"])
+            ub = s._gather(Uf, B["b"], B["f"], B["n"])
+            qb = s._gather_grad(Qf, B["b"], B["f"], B["n"]) if ns else None
             ab = B["mag"] * s._gather(gD, B["b"], B["f"], B["n"])
             res = np.zeros_like(ub)
+            resq = np.zeros((d, V, ub.shape[1])) if ns else None
             for t in np.unique(B["t"]):
                 m = B["t"] == t
                 nb = B["nrm"][:, m]
 
-                def fb(w, t=int(t), nb=nb):
-                    gi, _, _ = ph.ghost_states(t, w, None, prm)
-                    return ph.rusanov(w, gi, nb, gamma)
-                res[:, m] = _local_jac_T(fb, ub[:, m], ab[:, m], V)
+                def fb(w, z, t=int(t), nb=nb):
+                    gi, gl, qg = ph.ghost_states(t, w, z, prm)
+                    F = ph.rusanov(w, gi, nb, gamma)
+                    if ns:
+                        F = F - ph.ldg_viscous_normal(vflux(w, z), vflux(gl, qg), nb, beta) + tau * (w - gl)
+                    return F
+                qm = qb[:, :, m] if ns else None
+                res[:, m] = _local_jac_T(lambda w: fb(w, qm), ub[:, m], ab[:, m], V)
+                if ns:
+                    resq[:, :, m] = _local_jac_T(lambda w: fb(ub[:, m], w.reshape(d, V, -1)),
+                                                 qm.reshape(d * V, -1), ab[:, m], d * V).reshape(d, V, -1)
             s._scatter(auf, B["b"], B["f"], B["n"], res)
+            if ns:
+                _scatter_grad(s, aQf, B["b"], B["f"], B["n"], resq)
+        if ns:
+            # gradient chain: Qf = M0 Q, Q = J^-T qt, qt = M6 (C - uf) + M4 U
+            aC = []
+            for b, (el, g) in enumerate(zip(s.eles, s.geo)):
+                aq = aQ[b] + np.einsum("fu,jfvn->juvn", el.M0, aQf[b])          # [j, sigma, alpha, n]
+                aqt = np.einsum("nuij,juvn->iuvn", g["adj"], aq) / g["det"].T[None, :, None, :]
+                aqt = aqt.reshape(d * el.nupts, V, -1)
+                ac = np.einsum("af,avn->fvn", el.M6, aqt)
+                out[b] = out[b] + np.einsum("au,avn->uvn", el.M4, aqt)
+                auf[b] = auf[b] - ac
+                aC.append(ac)
+            # common solution: both sides of a pair hold the same C
+            acp = s._gather(aC, P["bL"], P["fL"], P["nL"]) + s._gather(aC, P["bR"], P["fR"], P["nR"])
+            addL = [np.zeros_like(x) for x in Uf]
+            addR = [np.zeros_like(x) for x in Uf]
+            s._scatter(addL, P["bL"], P["fL"], P["nL"], (0.5 - beta) * acp)
+            s._scatter(addR, P["bR"], P["fR"], P["nR"], (0.5 + beta) * acp)
+            auf = [x + y + z for x, y, z in zip(auf, addL, addR)]
+            if len(B["b"]):
+                acb = s._gather(aC, B["b"], B["f"], B["n"])
+                resc = np.zeros_like(ub)
+                for t in np.unique(B["t"]):
+                    m = B["t"] == t
+
+                    def cb(w, t=int(t)):
+                        _, gl, _ = ph.ghost_states(t, w, None, prm)
+                        return ph.ldg_common_solution(w, gl, beta)
+                    resc[:, m] = _local_jac_T(cb, ub[:, m], acb[:, m], V)
+                addB = [np.zeros_like(x) for x in Uf]
+                s._scatter(addB, B["b"], B["f"], B["n"], resc)
+                auf = [x + y for x, y in zip(auf, addB)]
         for b, el in enumerate(s.eles):
             out[b] = out[b] + np.einsum("fu,fvn->uvn", el.M0, auf[b])
         return out

@@ -163,6 +163,44 @@ class FRSystem:
             arrs[bb][f[m], :, n[m]] = vals[:, m].T
 
     # ------------------------------------------------------------ RHS
+    def gradients(self, U):
+        """Steps 1-2: U^(f) per block ([nfpts, V, nelem]) and, for
+        Navier-Stokes, the physical gradient Q at solution points
+        ([d, nupts, V, nelem]) and Q^(f) at flux points ([d, nfpts, V, nelem]);
+        Q and Q^(f) are None for the Euler equations."""
+        beta = self.prm["ldg_beta"]
+        d, V = self.ndims, self.nvars
+        P, B = self.pairs, self.bpairs
+        # 1. interpolate to flux points
+        Uf = [np.einsum("fu,uvn->fvn", el.M0, u) for el, u in zip(self.eles, U)]
+        if self.system != NAVIER_STOKES:
+            return Uf, None, None
+        uL = self._gather(Uf, P["bL"], P["fL"], P["nL"])
+        uR = self._gather(Uf, P["bR"], P["fR"], P["nR"])
+        ub = self._gather(Uf, B["b"], B["f"], B["n"])
+        # 2a. common solution (each pair visited once, both sides get it)
+        C = [np.empty_like(u) for u in Uf]
+        c = ph.ldg_common_solution(uL, uR, beta)
+        self._scatter(C, P["bL"], P["fL"], P["nL"], c)
+        self._scatter(C, P["bR"], P["fR"], P["nR"], c)
+        cb = np.empty_like(ub)
+        for t in np.unique(B["t"]):
+            m = B["t"] == t
+            _, gl, _ = ph.ghost_states(int(t), ub[:, m], None, self.prm)
+            cb[:, m] = ph.ldg_common_solution(ub[:, m], gl, beta)
+        self._scatter(C, B["b"], B["f"], B["n"], cb)
+        # 2b. corrected transformed gradient, physical gradient, to flux points
+        Q, Qf = [], []
+        for el, g, u, uf, cf in zip(self.eles, self.geo, U, Uf, C):
+            nu = el.nupts
+            qt = (np.einsum("af,fvn->avn", el.M6, cf - uf)
+                  + np.einsum("au,uvn->avn", el.M4, u)).reshape(d, nu, V, -1)
+            # q_j = sum_i (J^{-1})_{ij} qt_i with J^{-1} = adj / det
+            q = np.einsum("nuij,iuvn->juvn", g["adj"], qt) / g["det"].T[None, :, None, :]
+            Q.append(q)
+            Qf.append(np.einsum("fu,juvn->jfvn", el.M0, q))
+        return Uf, Q, Qf
+
     def rhs(self, U, scale=False):
         """R(U) for a list of per-block states U_b[nupts, nvars, nelem].
 
@@ -178,36 +216,11 @@ class FRSystem:
         ns = self.system == NAVIER_STOKES
         d, V = self.ndims, self.nvars
         P, B = self.pairs, self.bpairs
-        # 1. interpolate to flux points
-        Uf = [np.einsum("fu,uvn->fvn", el.M0, u) for el, u in zip(self.eles, U)]
+        # 1.-2. flux-point values and (Navier-Stokes) gradients
+        Uf, Q, Qf = self.gradients(U)
         uL = self._gather(Uf, P["bL"], P["fL"], P["nL"])
         uR = self._gather(Uf, P["bR"], P["fR"], P["nR"])
         ub = self._gather(Uf, B["b"], B["f"], B["n"])
-        ghost = {}
-        for t in np.unique(B["t"]):
-            m = B["t"] == t
-            ghost[t] = (m, ph.ghost_states(int(t), ub[:, m], None, prm))
-        Q = Qf = None
-        if ns:
-            # 2a. common solution (each pair visited once, both sides get it)
-            C = [np.empty_like(u) for u in Uf]
-            c = ph.ldg_common_solution(uL, uR, beta)
-            self._scatter(C, P["bL"], P["fL"], P["nL"], c)
-            self._scatter(C, P["bR"], P["fR"], P["nR"], c)
-            cb = np.empty_like(ub)
-            for t, (m, (_, gl, _)) in ghost.items():
-                cb[:, m] = ph.ldg_common_solution(ub[:, m], gl, beta)
-            self._scatter(C, B["b"], B["f"], B["n"], cb)
-            # 2b. corrected transformed gradient, physical gradient, to flux points
-            Q, Qf = [], []
-            for el, g, u, uf, cf in zip(self.eles, self.geo, U, Uf, C):
-                nu = el.nupts
-                qt = (np.einsum("af,fvn->avn", el.M6, cf - uf)
-                      + np.einsum("au,uvn->avn", el.M4, u)).reshape(d, nu, V, -1)
-                # q_j = sum_i (J^{-1})_{ij} qt_i with J^{-1} = adj / det
-                q = np.einsum("nuij,iuvn->juvn", g["adj"], qt) / g["det"].T[None, :, None, :]
-                Q.append(q)
-                Qf.append(np.einsum("fu,juvn->jfvn", el.M0, q))
         # 3. transformed flux at solution points
         Ft = []
         for b, (el, g, u) in enumerate(zip(self.eles, self.geo, U)):
@@ -233,7 +246,8 @@ class FRSystem:
         if len(B["b"]):
             Fb = np.empty_like(ub)
             qb = self._gather_grad(Qf, B["b"], B["f"], B["n"]) if ns else None
-            for t, (m, _) in ghost.items():
+            for t in np.unique(B["t"]):
+                m = B["t"] == t
                 gi, gl, qg = ph.ghost_states(int(t), ub[:, m], None if qb is None else qb[:, :, m], prm)
                 nb = B["nrm"][:, m]
                 Fm = ph.rusanov(ub[:, m], gi, nb, gamma)

@@ -14,7 +14,7 @@ import pytest
 
 from fr_inputs import periodic_box, annulus_mixed, fields
 from oracle.system import FRSystem
-from oracle.adjoint import EulerAdjoint
+from oracle.adjoint import FRAdjoint
 from tests.libutil import ensure_built, rel_l2_per_var
 
 pytestmark = pytest.mark.gpu
@@ -58,7 +58,7 @@ def test_adjoint_rhs_matches_oracle(torch, kind, prec, tol):
     lam = [rng.standard_normal(u.shape) for u in U]
     if prec != "fp64":
         lam = [l.astype(np.float32).astype(np.float64) for l in lam]
-    ref = EulerAdjoint(o).rhs_vjp(U, lam)
+    ref = FRAdjoint(o).rhs_vjp(U, lam)
     s = fr.Solver(m, p, "euler", prec, device=0, **prm)
     tu = [torch.from_numpy(s.pack(b, U[b])).cuda() for b in range(len(U))]
     tl = [torch.from_numpy(s.pack(b, lam[b])).cuda() for b in range(len(U))]
@@ -75,7 +75,7 @@ def test_rk4_adjoint_matches_oracle(torch):
     from paper_1312_1638_b300 import fr
     m = periodic_box("hex", 2, 0.0, 2 * np.pi, jitter=0.1, seed=1)
     o = FRSystem(m, 3, "euler")
-    A = EulerAdjoint(o)
+    A = FRAdjoint(o)
     U = [fields.smooth_random(o.solution_coords(0), seed=2, amp=0.2, vel0=(0.5, 0.1, 0.0),
                               p0=2.0).transpose(1, 0, 2).copy()]
     dt, n, every = 2e-3, 7, 3
