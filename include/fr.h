@@ -240,9 +240,14 @@ fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value);
  * fr_adjoint_rhs -- out = (dR/du)^T lambda, the discrete adjoint of fr_rhs
  * at state u (not in the paper; the transpose of the operator chain of
  * Eq. negdivconf / App. A with the Rusanov flux of App. B and the ghost
- * states of App. C).  Euler contexts only (FR_ERR_UNSUPPORTED otherwise).
+ * states of App. C; for Navier-Stokes also the LDG common solution and
+ * viscous flux of Sec. 4.3 and the corrected-gradient chain of
+ * Eq. tquptsm / gradufpts).  Euler and Navier-Stokes contexts on a whole
+ * mesh (FR_ERR_UNSUPPORTED for a partitioned context).
  * u, lambda, out: device buffers laid out like fr_rhs's; out may not alias
- * u or lambda.  Uses context scratch allocated on the first adjoint call.
+ * u or lambda.  Uses context scratch allocated on the first adjoint call
+ * (Navier-Stokes: two more gradient-sized arrays per block).  The
+ * Navier-Stokes adjoint overwrites the context's RHS scratch, as fr_rhs does.
  * Stream-ordered.
  */
 fr_status fr_adjoint_rhs(fr_ctx* ctx, void* const* u, void* const* lambda, void* const* out, void* stream);
@@ -254,7 +259,8 @@ fr_status fr_adjoint_rhs(fr_ctx* ctx, void* const* u, void* const* lambda, void*
  * recomputed from checkpoints of the state stored every `every` steps
  * (ceil(nsteps/every) checkpoints plus `every` states of the current block
  * and 8 work states, allocated for the call and freed before returning).
- * u0 is not modified.  Euler contexts only.  Synchronises `stream`.
+ * u0 is not modified.  Euler and Navier-Stokes contexts on a whole mesh.
+ * Synchronises `stream`.
  */
 fr_status fr_rk4_adjoint(fr_ctx* ctx, void* const* u0, void* const* lambda, double dt, int nsteps, int every,
                          void* stream);

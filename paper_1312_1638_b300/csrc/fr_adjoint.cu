@@ -1,16 +1,26 @@
-// Discrete adjoint of the Euler right-hand side and of classical RK4.
+// Discrete adjoint of the Euler and Navier-Stokes right-hand sides and of
+// classical RK4.
 //
 // Not in the paper.  The transpose of R = -J^-1 [M3 D~ + (M1 - M3 M2) F~]
 // (App. A) is applied by running the RHS steps backwards:
 //   mu  = -J^-1 lambda                           (adj_scale)
 //   g_D = M3^T mu,  g_F = (M1 - M3 M2)^T mu      (operator products)
 //   per pair: a = |n|_L g_D,L - |n|_R g_D,R,  a_uL = (dF/duL)^T a,
-//             a_uR = (dF/duR)^T a  with F the Rusanov flux (App. B);
-//   per boundary point the ghost state's dependence on u_L is included (App. C)
-//   out = M0^T a_uf + (df/du)^T adj(J)^T g_F     (point-wise, accumulated)
+//             a_uR = (dF/duR)^T a  with F the Rusanov flux (App. B), plus for
+//             Navier-Stokes the LDG viscous part and tau penalty (Sec. 4.3):
+//             a_qL, a_qR = (dF/dqL)^T a, (dF/dqR)^T a
+//   per boundary point the ghost states' dependence on u_L (and q_L) is
+//   included (App. C)
+//   point-wise: a_u += (df/du)^T adj(J)^T g_F, and for Navier-Stokes
+//             a_q = (df/dq)^T adj(J)^T g_F + M0^T a_qf, a_q~ = J^-1 a_q
+//   Navier-Stokes gradient chain (Q~ = M6 C + (M4 - M6 M0) U):
+//             a_C = M6^T a_q~, a_uf += (dC/duf)^T a_C (LDG common solution)
+//   out = M0^T a_uf [+ (M4 - M6 M0)^T a_q~] + point-wise terms
 // The local transposed Jacobians are written out analytically from the
-// Euler flux (Eq. eulerflux, idealgas), in plain (not perturbation) variables.
-// The RK4 adjoint recomputes stage inputs from checkpoints.
+// fluxes (Eq. eulerflux, idealgas, visflux), in plain (not perturbation)
+// variables.  The Navier-Stokes adjoint recomputes U^(f), Q and Q^(f) at u
+// with the forward kernels first.  The RK4 adjoint recomputes stage inputs
+// from checkpoints.
 #include <cmath>
 #include <vector>
 
@@ -175,6 +185,128 @@ struct EulerAdj {
     }
 };
 
+template <typename T, int D>
+struct NsAdj {
+    static constexpr int NV = D + 2;
+
+    // Viscous flux (Eq. visflux, constant mu, kappa = mu gamma / (Pr (gamma-1))
+    // multiplying grad(p/rho)) in plain variables, differentiated in reverse:
+    // au += (d f_vis / du)^T W and aq += (d f_vis / dq)^T W, where W[i][a]
+    // weights f_vis[i][a].
+    __device__ static __forceinline__ void vis_vjp(const T* u, const T q[D][NV], const T W[D][NV], T gm1, T mu,
+                                                   T kappa, T* au, T aq[D][NV]) {
+        const T rho = u[0], rinv = T(1) / rho;
+        T v[D], v2 = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { v[i] = u[1 + i] * rinv; v2 += v[i] * v[i]; }
+        const T p = gm1 * (u[D + 1] - T(0.5) * rho * v2), pr = p * rinv;
+        // forward: dv[i][j] = d v_i / d x_j, dpr[j] = d (p/rho) / d x_j, stress tau
+        T dv[D][D], dpr[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const T drho = q[j][0];
+            T vdm = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) { dv[i][j] = (q[j][1 + i] - v[i] * drho) * rinv; vdm += v[i] * q[j][1 + i]; }
+            const T dp = gm1 * (q[j][D + 1] - vdm + T(0.5) * v2 * drho);
+            dpr[j] = (dp - pr * drho) * rinv;
+        }
+        T div = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) div += dv[i][i];
+        // reverse: adjoints of tau (Wt), of v (av), of grad(p/rho) (Wdpr)
+        T Wt[D][D], av[D], trW = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) Wt[i][j] = W[i][1 + j] + v[i] * W[j][D + 1];
+            trW += Wt[i][i];
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const T tji = mu * (dv[i][j] + dv[j][i]) - (i == j ? T(2) / T(3) * mu * div : T(0));
+                acc += W[i][D + 1] * tji;
+            }
+            av[j] = acc;
+        }
+        T arinv = T(0), apr = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            // dv[k][j] = (q[j][1+k] - v_k q[j][0]) / rho
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T w = mu * (Wt[j][k] + Wt[k][j]) - (k == j ? T(2) / T(3) * mu * trW : T(0));   // adjoint of dv[k][j]
+                aq[j][1 + k] += w * rinv;
+                aq[j][0] -= w * v[k] * rinv;
+                av[k] -= w * q[j][0] * rinv;
+                arinv += w * dv[k][j] * rho;
+            }
+            // dpr[j] = (dp_j - (p/rho) q[j][0]) / rho,
+            // dp_j = gm1 (q[j][E] - v . q[j][m] + |v|^2 q[j][0] / 2)
+            const T wpr = kappa * W[j][D + 1];
+            const T wdp = wpr * rinv;
+            aq[j][0] += -wpr * pr * rinv + gm1 * wdp * T(0.5) * v2;
+            apr -= wpr * q[j][0] * rinv;
+            arinv += wpr * dpr[j] * rho;
+            aq[j][D + 1] += gm1 * wdp;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                aq[j][1 + k] -= gm1 * wdp * v[k];
+                av[k] += gm1 * wdp * (v[k] * q[j][0] - q[j][1 + k]);
+            }
+        }
+        // p/rho = p * (1/rho)
+        const T ap = apr * rinv;
+        arinv += apr * p;
+        // to conserved variables: p = gm1 (E - |m|^2 / (2 rho)), v = m / rho, 1/rho
+        T avv = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            au[1 + k] += -gm1 * v[k] * ap + av[k] * rinv;
+            avv += av[k] * v[k];
+        }
+        au[D + 1] += gm1 * ap;
+        au[0] += gm1 * T(0.5) * v2 * ap - avv * rinv - arinv * rinv * rinv;
+    }
+
+    // LDG ghost state (App. C) in plain variables: the inviscid ghost for
+    // free-stream and outflow faces; at isothermal walls the wall velocity
+    // and temperature with the interior density
+    __device__ static __forceinline__ void ldg_ghost(int bctype, const T* uL, const DevParams& P, T* g) {
+        if (bctype <= 1) { EulerAdj<T, D>::ghost(bctype, uL, P, g); return; }
+        const double* wv = bctype == 3 ? P.wall2_v : P.wall_v;
+        const T rho = uL[0];
+        T k2 = T(0);
+        g[0] = rho;
+#pragma unroll
+        for (int i = 0; i < D; ++i) { g[1 + i] = rho * T(wv[i]); k2 += T(wv[i]) * T(wv[i]); }
+        g[D + 1] = rho * (T(P.wall_cpTw) / T(P.gamma) + T(0.5) * k2);
+    }
+
+    // c += (d ldg_ghost / d uL)^T b
+    __device__ static __forceinline__ void ldg_ghost_vjp(int bctype, const T* uL, const DevParams& P, const T* b,
+                                                         T* c) {
+        if (bctype <= 1) { EulerAdj<T, D>::ghost_vjp(bctype, uL, P, b, c); return; }
+        const double* wv = bctype == 3 ? P.wall2_v : P.wall_v;
+        T k2 = T(0), bm = T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { k2 += T(wv[i]) * T(wv[i]); bm += T(wv[i]) * b[1 + i]; }
+        c[0] += b[0] + bm + (T(P.wall_cpTw) / T(P.gamma) + T(0.5) * k2) * b[D + 1];
+    }
+
+    // weights of the viscous part of the common flux on one side:
+    // W[i][a] = -w n_i a_a (F contains -n . w f_vis)
+    __device__ static __forceinline__ void side_weights(const T* n, const T* a, T w, T W[D][NV]) {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) W[i][k] = -w * n[i] * a[k];
+    }
+};
+
 // mu = -lambda / J
 template <typename T>
 __global__ void adj_scale_kernel(int nupts, int nvars, int64_t nelem, int64_t ld, const T* __restrict__ lam,
@@ -272,8 +404,216 @@ __global__ void adj_flux_kernel(int nupts, int64_t nelem, int64_t ld, const T* _
     for (int q = 0; q < NV; ++q) out[((int64_t)s * NV + q) * ld + n] += a[q];
 }
 
+// Navier-Stokes pairs: the common flux F = Rusanov - n.{(1/2+b) fv_L +
+// (1/2-b) fv_R} + tau (u_L - u_R) transposed; a_u in place of g_D, a_q in
+// place of Q^(f)
+template <typename T, int D>
+__global__ void ns_adj_pair_kernel(int64_t npairs, const uint32_t* __restrict__ offL,
+                                   const uint32_t* __restrict__ offR, const T* __restrict__ ufL,
+                                   const T* __restrict__ ufR, T* gL, T* gR, T* qfL, T* qfR, int64_t ldL, int64_t ldR,
+                                   int64_t qsL, int64_t qsR, const T* __restrict__ nrm, const T* __restrict__ magL,
+                                   const T* __restrict__ magR, DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    const int64_t oL = offL[k], oR = offR[k];
+    const T gamma = T(P.gamma), gm1 = gamma - T(1), mu = T(P.mu), tau = T(P.tau), beta = T(P.beta);
+    const T kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
+    T uL[NV], uR[NV], a[NV], n[D], aL[NV], aR[NV];
+    const T mL = magL[k], mR = magR[k];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        uL[q] = ufL[oL + q * ldL];
+        uR[q] = ufR[oR + q * ldR];
+        a[q] = mL * gL[oL + q * ldL] - mR * gR[oR + q * ldR];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) n[i] = nrm[i * npairs + k];
+    EulerAdj<T, D>::rusanov_vjp(uL, uR, n, gamma, a, aL, aR);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { aL[q] += tau * a[q]; aR[q] -= tau * a[q]; }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const T* u = side == 0 ? uL : uR;
+        T* au = side == 0 ? aL : aR;
+        T* qf = side == 0 ? qfL : qfR;
+        const int64_t o = side == 0 ? oL : oR, ld = side == 0 ? ldL : ldR, qs = side == 0 ? qsL : qsR;
+        T q[D][NV], W[D][NV], aq[D][NV];
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) { q[j][v] = qf[j * qs + o + v * ld]; aq[j][v] = T(0); }
+        NsAdj<T, D>::side_weights(n, a, side == 0 ? T(0.5) + beta : T(0.5) - beta, W);
+        NsAdj<T, D>::vis_vjp(u, q, W, gm1, mu, kappa, au, aq);
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) qf[j * qs + o + v * ld] = aq[j][v];
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        gL[oL + q * ldL] = aL[q];
+        gR[oR + q * ldR] = aR[q];
+    }
+}
+
+// Navier-Stokes boundary points: Rusanov with the inviscid ghost, the LDG
+// viscous part and tau penalty with the LDG ghost and ghost gradient (q_L at
+// walls, zero otherwise), all transposed onto u_L and q_L
+template <typename T, int D>
+__global__ void ns_adj_bc_kernel(int64_t nb, int bctype, const uint32_t* __restrict__ off, const T* __restrict__ uf,
+                                 T* g, T* qf, int64_t ld, int64_t qs, const T* __restrict__ nrm,
+                                 const T* __restrict__ mag, DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const int64_t o = off[k];
+    const T gamma = T(P.gamma), gm1 = gamma - T(1), mu = T(P.mu), tau = T(P.tau), beta = T(P.beta);
+    const T kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
+    T uL[NV], gs[NV], gl[NV], a[NV], n[D], aL[NV], aR[NV], agl[NV];
+    const T m = mag[k];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        uL[q] = uf[o + q * ld];
+        a[q] = m * g[o + q * ld];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) n[i] = nrm[i * nb + k];
+    EulerAdj<T, D>::ghost(bctype, uL, P, gs);
+    EulerAdj<T, D>::rusanov_vjp(uL, gs, n, gamma, a, aL, aR);
+    EulerAdj<T, D>::ghost_vjp(bctype, uL, P, aR, aL);
+    NsAdj<T, D>::ldg_ghost(bctype, uL, P, gl);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { aL[q] += tau * a[q]; agl[q] = -tau * a[q]; }
+    const bool wall = bctype >= 2;
+    T q[D][NV], W[D][NV], aq[D][NV];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { q[j][v] = qf[j * qs + o + v * ld]; aq[j][v] = T(0); }
+    NsAdj<T, D>::side_weights(n, a, T(0.5) + beta, W);
+    NsAdj<T, D>::vis_vjp(uL, q, W, gm1, mu, kappa, aL, aq);
+    {
+        // ghost side: gradient q_L at walls (its adjoint joins a_q), zero otherwise
+        T qg[D][NV], aqg[D][NV];
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) { qg[j][v] = wall ? q[j][v] : T(0); aqg[j][v] = T(0); }
+        NsAdj<T, D>::side_weights(n, a, T(0.5) - beta, W);
+        NsAdj<T, D>::vis_vjp(gl, qg, W, gm1, mu, kappa, agl, aqg);
+        if (wall)
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) aq[j][v] += aqg[j][v];
+    }
+    NsAdj<T, D>::ldg_ghost_vjp(bctype, uL, P, agl, aL);
+#pragma unroll
+    for (int q2 = 0; q2 < NV; ++q2) g[o + q2 * ld] = aL[q2];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) qf[j * qs + o + v * ld] = aq[j][v];
+}
+
+// Navier-Stokes solution points: G = adj(J)^T g_F;  a_u = (df_inv/du)^T G -
+// (df_vis/du)^T G into au;  a_q = -(df_vis/dq)^T G + X (X = M0^T a_qf);
+// a_q~ = adj(J) a_q / det J in place of Q
+template <typename T, int D>
+__global__ void ns_adj_point_kernel(int nupts, int64_t nelem, int64_t ld, const T* __restrict__ U, T* Q,
+                                    const T* __restrict__ gF, const T* __restrict__ X, const T* __restrict__ smat,
+                                    const T* __restrict__ rcp, T* __restrict__ au, DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y;
+    if (n >= nelem) return;
+    const T gamma = T(P.gamma), gm1 = gamma - T(1), mu = T(P.mu);
+    const T kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
+    T u[NV], G[D][NV], adj[D][D], a[NV], q[D][NV], aq[D][NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        u[v] = U[((int64_t)s * NV + v) * ld + n];
+        a[v] = T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) adj[i][j] = smat[((int64_t)(i * D + j) * nupts + s) * ld + n];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc += adj[i][j] * gF[((int64_t)(i * nupts + s) * NV + v) * ld + n];
+            G[j][v] = acc;
+            q[j][v] = Q[((int64_t)(j * nupts + s) * NV + v) * ld + n];
+            aq[j][v] = X[((int64_t)(j * nupts + s) * NV + v) * ld + n];
+        }
+    EulerAdj<T, D>::flux_vjp(u, G, gamma, a);
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) G[j][v] = -G[j][v];
+    NsAdj<T, D>::vis_vjp(u, q, G, gm1, mu, kappa, a, aq);
+    const T r = rcp[(int64_t)s * ld + n];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < D; ++j) acc += adj[i][j] * aq[j][v];
+            Q[((int64_t)(i * nupts + s) * NV + v) * ld + n] = acc * r;
+        }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) au[((int64_t)s * NV + v) * ld + n] = a[v];
+}
+
+// LDG common solution transposed (Sec. 4.3): both sides of a pair hold
+// C = (1/2-b) u_L + (1/2+b) u_R, so a = a_C,L + a_C,R feeds both sides
+template <typename T, int D>
+__global__ void ns_adj_csol_kernel(int64_t npairs, const uint32_t* __restrict__ offL,
+                                   const uint32_t* __restrict__ offR, const T* __restrict__ cL,
+                                   const T* __restrict__ cR, T* aL, T* aR, int64_t ldL, int64_t ldR, T beta) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    const int64_t oL = offL[k], oR = offR[k];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const T ac = cL[oL + v * ldL] + cR[oR + v * ldR];
+        aL[oL + v * ldL] += (T(0.5) - beta) * ac;
+        aR[oR + v * ldR] += (T(0.5) + beta) * ac;
+    }
+}
+
+// boundary: C = (1/2-b) u_L + (1/2+b) B_ldg(u_L)
+template <typename T, int D>
+__global__ void ns_adj_csol_bc_kernel(int64_t nb, int bctype, const uint32_t* __restrict__ off,
+                                      const T* __restrict__ uf, const T* __restrict__ c, T* a, int64_t ld,
+                                      DevParams P) {
+    constexpr int NV = D + 2;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const int64_t o = off[k];
+    const T beta = T(P.beta);
+    T uL[NV], gb[NV], res[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        uL[v] = uf[o + v * ld];
+        const T cv = c[o + v * ld];
+        res[v] = (T(0.5) - beta) * cv;
+        gb[v] = (T(0.5) + beta) * cv;
+    }
+    NsAdj<T, D>::ldg_ghost_vjp(bctype, uL, P, gb, res);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a[o + v * ld] += res[v];
+}
+
 template <typename T>
-__global__ void lincomb_kernel(int64_t n, T* __restrict__ out, T a, const T* __restrict__ x, T b,
+__global__ void lincomb_kernel(int64_t n, T* out, T a, const T* x, T b,
                                const T* __restrict__ y) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -320,7 +660,82 @@ static cudaError_t adjoint_impl(DevCtx& c, void* const* u, void* const* lam, voi
     return cudaGetLastError();
 }
 
+template <typename T, int D>
+static cudaError_t ns_adjoint_impl(DevCtx& c, void* const* u, void* const* lam, void* const* out, cudaStream_t st) {
+    constexpr int NV = D + 2;
+    cudaError_t e;
+    // forward values at u: plain U^(f) (adj_uf); Q (B.Q) and Q^(f) (B.Qf) by
+    // the forward kernels (their U^(f) in B.Uf is not used)
+    for (size_t b = 0; b < c.blocks.size(); ++b)
+        if ((e = adjoint_gemm(c, 0, (int)b, u[b], c.blocks[b].adj_uf, st)) != cudaSuccess) return e;
+    if ((e = launch_rhs_phases(c, u, nullptr, PH_A | PH_B1 | PH_B2, st)) != cudaSuccess) return e;
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        dim3 g((unsigned)((B.nelem + 127) / 128), (unsigned)B.nupts);
+        adj_scale_kernel<T><<<g, 128, 0, st>>>(B.nupts, B.nvars, B.nelem, B.ld, (const T*)lam[b],
+                                               (const T*)B.rcpdjac, (T*)B.adj_mu);
+        if ((e = adjoint_gemm(c, 1, (int)b, B.adj_mu, B.Uf, st)) != cudaSuccess) return e;     // g_D
+        if ((e = adjoint_gemm(c, 2, (int)b, B.adj_mu, B.adj_g, st)) != cudaSuccess) return e;  // g_F
+    }
+    for (auto& g : c.pgroups) {
+        if (!g.n) continue;
+        DevBlock &L = c.blocks[g.bL], &R = c.blocks[g.bR];
+        const int64_t qsL = (int64_t)L.nfpts * NV * L.ld, qsR = (int64_t)R.nfpts * NV * R.ld;
+        ns_adj_pair_kernel<T, D><<<lgrid(g.n, 128), 128, 0, st>>>(
+            g.n, g.offL, g.offR, (const T*)L.adj_uf, (const T*)R.adj_uf, (T*)L.Uf, (T*)R.Uf, (T*)L.Qf, (T*)R.Qf,
+            L.ld, R.ld, qsL, qsR, (const T*)g.nrm, (const T*)g.magL, (const T*)g.magR, c.prm);
+    }
+    for (auto& g : c.bgroups) {
+        if (!g.n) continue;
+        DevBlock& B = c.blocks[g.b];
+        ns_adj_bc_kernel<T, D><<<lgrid(g.n, 128), 128, 0, st>>>(g.n, g.bctype, g.off, (const T*)B.adj_uf, (T*)B.Uf,
+                                                                (T*)B.Qf, B.ld, (int64_t)B.nfpts * NV * B.ld,
+                                                                (const T*)g.nrm, (const T*)g.mag, c.prm);
+    }
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        const int64_t N = (int64_t)NV * B.ld;
+        for (int j = 0; j < D; ++j)   // M0^T per direction of the flux-point gradient adjoint
+            if ((e = adjoint_gemm(c, 3, (int)b, (const T*)B.Qf + (int64_t)j * B.nfpts * N,
+                                  (T*)B.adj_x + (int64_t)j * B.nupts * N, st)) != cudaSuccess)
+                return e;
+        dim3 g((unsigned)((B.nelem + 127) / 128), (unsigned)B.nupts);
+        ns_adj_point_kernel<T, D><<<g, 128, 0, st>>>(B.nupts, B.nelem, B.ld, (const T*)u[b], (T*)B.Q,
+                                                     (const T*)B.adj_g, (const T*)B.adj_x, (const T*)B.smat,
+                                                     (const T*)B.rcpdjac, (T*)B.adj_mu, c.prm);
+        if ((e = adjoint_gemm(c, 4, (int)b, B.Q, B.Qf, st)) != cudaSuccess) return e;          // a_C = M6^T a_q~
+    }
+    for (auto& g : c.pgroups) {
+        if (!g.n) continue;
+        DevBlock &L = c.blocks[g.bL], &R = c.blocks[g.bR];
+        ns_adj_csol_kernel<T, D><<<lgrid(g.n, 128), 128, 0, st>>>(g.n, g.offL, g.offR, (const T*)L.Qf,
+                                                                  (const T*)R.Qf, (T*)L.Uf, (T*)R.Uf, L.ld, R.ld,
+                                                                  T(c.prm.beta));
+    }
+    for (auto& g : c.bgroups) {
+        if (!g.n) continue;
+        DevBlock& B = c.blocks[g.b];
+        ns_adj_csol_bc_kernel<T, D><<<lgrid(g.n, 128), 128, 0, st>>>(g.n, g.bctype, g.off, (const T*)B.adj_uf,
+                                                                     (const T*)B.Qf, (T*)B.Uf, B.ld, c.prm);
+    }
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        // out = M0^T a_uf + (M4 - M6 M0)^T a_q~, then the point-wise terms
+        if ((e = adjoint_gemm(c, 5, (int)b, B.Uf, out[b], st, B.Q)) != cudaSuccess) return e;
+        const int64_t n = (int64_t)B.nupts * NV * B.ld;
+        lincomb_kernel<T><<<lgrid(n, 256), 256, 0, st>>>(n, (T*)out[b], T(1), (const T*)out[b], T(1),
+                                                         (const T*)B.adj_mu);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_rhs(DevCtx& c, void* const* u, void* const* lam, void* const* out, cudaStream_t st) {
+    if (c.system == 1) {
+        if (c.precision == 0) return c.ndims == 2 ? ns_adjoint_impl<double, 2>(c, u, lam, out, st)
+                                                  : ns_adjoint_impl<double, 3>(c, u, lam, out, st);
+        return c.ndims == 2 ? ns_adjoint_impl<float, 2>(c, u, lam, out, st)
+                            : ns_adjoint_impl<float, 3>(c, u, lam, out, st);
+    }
     if (c.precision == 0) return c.ndims == 2 ? adjoint_impl<double, 2>(c, u, lam, out, st)
                                               : adjoint_impl<double, 3>(c, u, lam, out, st);
     return c.ndims == 2 ? adjoint_impl<float, 2>(c, u, lam, out, st) : adjoint_impl<float, 3>(c, u, lam, out, st);

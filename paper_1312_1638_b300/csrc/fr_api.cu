@@ -173,7 +173,7 @@ void upload_device(fr_ctx* c) {
         B.opM0 = upload_real(c, el.M0, fp64);
         B.opQ = upload_real(c, hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu), fp64);
         B.opR = upload_real(c, hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu), fp64);
-        if (c->prm.system == FR_EULER) {
+        {
             // transposed operators of the discrete adjoint
             auto transpose = [](const std::vector<double>& A, int r, int cl) {
                 std::vector<double> t((size_t)r * cl);
@@ -186,11 +186,23 @@ void upload_device(fr_ctx* c) {
             B.opM3T = upload_real(c, M3T, fp64);
             B.opM132T = upload_real(c, M132T, fp64);
             B.opM0T = upload_real(c, M0T, fp64);
+            std::vector<double> M6T, OutT;
+            if (ns) {
+                // gradient chain: C and U enter Q~ through M6 and M4 - M6 M0
+                M6T = transpose(el.M6, d * (int)nu, (int)nf);
+                OutT = hcat(M0T, (int)nf, transpose(el.M46, d * (int)nu, (int)nu), d * (int)nu, (int)nu);
+                B.opM6T = upload_real(c, M6T, fp64);
+                B.opOutT = upload_real(c, OutT, fp64);
+            }
             if (c->prm.precision == FR_PREC_BF16X3 || c->prm.precision == FR_PREC_TF32X3) {
                 const int kind = c->prm.precision == FR_PREC_TF32X3 ? 0 : 1;
                 B.tcM3T = upload(c, fr::tc::pack_operator(kind, M3T, (int)nf, (int)nu, 0));
                 B.tcM132T = upload(c, fr::tc::pack_operator(kind, M132T, d * (int)nu, (int)nu, 0));
                 B.tcM0T = upload(c, fr::tc::pack_operator(kind, M0T, (int)nu, (int)nf, 0));
+                if (ns) {
+                    B.tcM6T = upload(c, fr::tc::pack_operator(kind, M6T, (int)nf, d * (int)nu, 0));
+                    B.tcOutT = upload(c, fr::tc::pack_operator(kind, OutT, (int)nu, (int)nf, d * (int)nu));
+                }
             }
         }
         if (c->prm.precision == FR_PREC_BF16X3 || c->prm.precision == FR_PREC_TF32X3) {
@@ -877,12 +889,15 @@ static fr_status adjoint_ready(fr_ctx* ctx) {
     fr_status s = check_dev(ctx);
     if (s != FR_OK) return s;
     if ((s = whole_mesh(ctx)) != FR_OK) return s;
-    if (ctx->prm.system != FR_EULER) return set_err(ctx, FR_ERR_UNSUPPORTED, "the adjoint covers the Euler equations");
     size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const bool ns = ctx->prm.system == FR_NAVIER_STOKES;
+    const size_t d = (size_t)ctx->dev.ndims;
     try {
         for (auto& B : ctx->dev.blocks) {
             if (!B.adj_mu) B.adj_mu = dalloc(ctx, (size_t)B.nupts * B.nvars * B.ld * rs);
             if (!B.adj_uf) B.adj_uf = dalloc(ctx, (size_t)B.nfpts * B.nvars * B.ld * rs);
+            if (ns && !B.adj_g) B.adj_g = dalloc(ctx, d * B.nupts * B.nvars * B.ld * rs);
+            if (ns && !B.adj_x) B.adj_x = dalloc(ctx, d * B.nupts * B.nvars * B.ld * rs);
             if (!B.rk_acc) B.rk_acc = dalloc(ctx, (size_t)B.nupts * B.nvars * B.ld * rs);
             if (!B.rk_tmp) B.rk_tmp = dalloc(ctx, (size_t)B.nupts * B.nvars * B.ld * rs);
         }

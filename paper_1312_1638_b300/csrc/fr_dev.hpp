@@ -32,15 +32,21 @@ struct DevBlock {
     void* tcM0 = nullptr;      // the same three operators packed for the tensor-core GEMM
     void* tcQ = nullptr;       // (split-precision modes only)
     void* tcR = nullptr;
-    // adjoint (Euler): transposed operators and scratch
+    // adjoint: transposed operators and scratch
     void* opM3T = nullptr;     // M3^T: nfpts x nupts
     void* opM132T = nullptr;   // (M1 - M3 M2)^T: ndims*nupts x nupts
     void* opM0T = nullptr;     // M0^T: nupts x nfpts
+    void* opM6T = nullptr;     // (NS) M6^T: nfpts x ndims*nupts
+    void* opOutT = nullptr;    // (NS) [M0^T | (M4 - M6 M0)^T]: nupts x (nfpts + ndims*nupts)
     void* tcM3T = nullptr;
     void* tcM132T = nullptr;
     void* tcM0T = nullptr;
+    void* tcM6T = nullptr;
+    void* tcOutT = nullptr;
     void* adj_mu = nullptr;    // [nupts][nvars][ld]
     void* adj_uf = nullptr;    // [nfpts][nvars][ld]
+    void* adj_g = nullptr;     // (NS) [ndims*nupts][nvars][ld]: g_F
+    void* adj_x = nullptr;     // (NS) [ndims*nupts][nvars][ld]: M0^T applied to the flux-point gradient adjoint
     void* stage = nullptr;     // device staging for fr_rhs_host: [nupts][nvars][ld]
     void* rk_acc = nullptr;    // RK4 registers
     void* rk_tmp = nullptr;
@@ -131,10 +137,12 @@ void prof_free(DevCtx& c);
 
 // RHS r = R(u) for every block (precision and dimension dispatched inside).
 cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t st);
-// out = (dR/du)^T lam (Euler); scratch must be allocated (adj_mu, adj_uf)
+// out = (dR/du)^T lam; scratch must be allocated (adj_mu, adj_uf; NS also adj_g, adj_x)
 cudaError_t launch_adjoint_rhs(DevCtx& c, void* const* u, void* const* lam, void* const* out, cudaStream_t st);
-// operator product used by the adjoint: which = 0: M0 u (plain), 1: M3^T x, 2: (M1-M3M2)^T x, 3: M0^T x
-cudaError_t adjoint_gemm(DevCtx& c, int which, int b, const void* B, void* C, cudaStream_t st);
+// operator product used by the adjoint: which = 0: M0 u (plain), 1: M3^T x, 2: (M1-M3M2)^T x, 3: M0^T x,
+// (NS) 4: M6^T x, 5: M0^T x + (M4 - M6 M0)^T y with y = B2
+cudaError_t adjoint_gemm(DevCtx& c, int which, int b, const void* B, void* C, cudaStream_t st,
+                         const void* B2 = nullptr);
 // RK4 adjoint: lam (dK/du_N on entry) becomes dK/du_0; ck: ceil(nsteps/every)
 // state slots, blk: `every` slots, tmp: 8 slots (each [block] -> device buffer)
 cudaError_t launch_rk4_adjoint(DevCtx& c, void* const* u0, void* const* lam, double dt, int nsteps, int every,

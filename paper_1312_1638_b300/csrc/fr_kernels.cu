@@ -881,21 +881,25 @@ phase_c2:
     return cudaGetLastError();
 }
 
-cudaError_t adjoint_gemm(DevCtx& c, int which, int b, const void* B, void* C, cudaStream_t st) {
+cudaError_t adjoint_gemm(DevCtx& c, int which, int b, const void* B, void* C, cudaStream_t st, const void* B2) {
     DevBlock& Bk = c.blocks[b];
     const int D = c.ndims, nu = Bk.nupts, nf = Bk.nfpts;
     const int64_t N = (int64_t)c.nvars * Bk.ld;
     const void *op = nullptr, *tcop = nullptr;
-    int M = 0, K = 0;
+    int M = 0, K = 0, K1 = 0;
     switch (which) {
         case 0: op = Bk.opM0; tcop = Bk.tcM0; M = nf; K = nu; break;
         case 1: op = Bk.opM3T; tcop = Bk.tcM3T; M = nf; K = nu; break;
         case 2: op = Bk.opM132T; tcop = Bk.tcM132T; M = D * nu; K = nu; break;
-        default: op = Bk.opM0T; tcop = Bk.tcM0T; M = nu; K = nf; break;
+        case 3: op = Bk.opM0T; tcop = Bk.tcM0T; M = nu; K = nf; break;
+        case 4: op = Bk.opM6T; tcop = Bk.tcM6T; M = nf; K = D * nu; break;
+        default: op = Bk.opOutT; tcop = Bk.tcOutT; M = nu; K = nf + D * nu; K1 = nf; break;
     }
+    if (!K1) K1 = K;
+    if (!op || (K1 < K && !B2)) return cudaErrorInvalidValue;
     if (c.precision == 0)
-        return op_gemm<double>(c, op, tcop, M, K, K, B, nullptr, N, C, 0, nullptr, Bk.ld, st, 0, 0, Sub<double>{});
-    return op_gemm<float>(c, op, tcop, M, K, K, B, nullptr, N, C, 0, nullptr, Bk.ld, st, 0, 0, Sub<float>{});
+        return op_gemm<double>(c, op, tcop, M, K, K1, B, B2, N, C, 0, nullptr, Bk.ld, st, 0, 0, Sub<double>{});
+    return op_gemm<float>(c, op, tcop, M, K, K1, B, B2, N, C, 0, nullptr, Bk.ld, st, 0, 0, Sub<float>{});
 }
 
 cudaError_t launch_rhs(DevCtx& c, void* const* u, void* const* r, cudaStream_t st) {

@@ -7,7 +7,7 @@ directions d ~ N(0, I) scaled per variable by its RMS (default_rng(4242)):
 |g.d - FD| <= 1e-4 (|FD| + 1e-3 |g| |d|).  The FP64 trajectories run
 `batch` directions at a time on disjoint copies of the box.
 
-    python -m tests.adjoint_fd_study [n] [ndir]     # default: the full c4 (16, 200)
+    python -m tests.adjoint_fd_study [n] [ndir] [euler|ns]   # default: the full c4 (16, 200, euler)
 """
 
 from __future__ import annotations
@@ -45,18 +45,26 @@ def replicated(box, copies, L):
     return Mesh(3, [Block("hex", allnodes)], box.bfaces, box.periodic)
 
 
-def fd_check(n_box, ndir, prec="fp32", batch=8, nsteps=50, dt=1e-3, every=10):
+# Navier-Stokes variant: the Taylor-Green constants (mu = 1/1600, Pr = 0.71,
+# LDG beta = 1/2, tau = 0.1), single precision in perturbation form about the
+# mean state (rho 1, p 1/(gamma M^2), M = 0.1)
+NS_PRM = dict(mu=1.0 / 1600.0, prandtl=0.71, ldg_beta=0.5, ldg_tau=0.1)
+NS_REF = dict(ref_rho=1.0, ref_p=1.0 / (1.4 * 0.01))
+
+
+def fd_check(n_box, ndir, prec="fp32", batch=8, nsteps=50, dt=1e-3, every=10, system="euler"):
     """Returns dict(bad=[(k, g.d, FD)], worst relative deviation, directions)."""
     import torch
     from oracle.system import FRSystem
     from paper_1312_1638_b300 import fr
     L = 2 * np.pi
     m = periodic_box("hex", n_box, 0.0, L)
-    o = FRSystem(m, 4, "euler")
+    prm = NS_PRM if system == "ns" else {}
+    o = FRSystem(m, 4, system, **prm)
     w = o.quadrature_weights(0)
     U = fields.perturbed_taylor_green(o.solution_coords(0), M=0.1).transpose(1, 0, 2).copy()
     U = U.astype(np.float32).astype(np.float64)
-    s1 = fr.Solver(m, 4, "euler", prec, device=0)
+    s1 = fr.Solver(m, 4, system, prec, device=0, **prm, **(NS_REF if system == "ns" else {}))
     ne = m.nelem
     u0 = torch.from_numpy(s1.pack(0, U)).cuda()
     uN = u0.clone()
@@ -69,7 +77,7 @@ def fd_check(n_box, ndir, prec="fp32", batch=8, nsteps=50, dt=1e-3, every=10):
     rng = np.random.default_rng(4242)
     rms = np.sqrt((U ** 2).mean(axis=(0, 2)))
     dirs = [rng.standard_normal(U.shape) * rms[None, :, None] for _ in range(ndir)]
-    s64 = fr.Solver(replicated(m, batch, L), 4, "euler", "fp64", device=0)
+    s64 = fr.Solver(replicated(m, batch, L), 4, system, "fp64", device=0, **prm)
     bad, worst = [], 0.0
     for k0 in range(0, ndir, batch):
         ds = dirs[k0:k0 + batch]
@@ -90,14 +98,15 @@ def fd_check(n_box, ndir, prec="fp32", batch=8, nsteps=50, dt=1e-3, every=10):
             if abs(gd - fd) > tol:
                 bad.append((k0 + c, gd, fd))
     s64.close()
-    return dict(bad=bad, worst=worst, ndir=ndir, n_box=n_box, prec=prec)
+    return dict(bad=bad, worst=worst, ndir=ndir, n_box=n_box, prec=prec, system=system)
 
 
 if __name__ == "__main__":
     n = int(sys.argv[1]) if len(sys.argv) > 1 else 16
     nd = int(sys.argv[2]) if len(sys.argv) > 2 else 200
+    sysname = sys.argv[3] if len(sys.argv) > 3 else "euler"
     t0 = time.time()
-    r = fd_check(n, nd)
-    print(f"c4 adjoint vs FP64 central FD: {n}^3 hexes, p=4, {nd} directions, FP32 adjoint: "
+    r = fd_check(n, nd, system=sysname)
+    print(f"{sysname} adjoint vs FP64 central FD: {n}^3 hexes, p=4, {nd} directions, FP32 adjoint: "
           f"{len(r['bad'])} outside the bound; largest |g.d - FD| / (|FD| + 1e-3 |g||d|) = {r['worst']:.2e} "
           f"(bound 1e-4); {time.time() - t0:.0f} s")
