@@ -53,6 +53,7 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed quad/triangle annulus leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (16^3 hex box) leg")
     return ap.parse_args()
 
 
@@ -529,6 +530,52 @@ def main():
             st_.close()
             del ut, Ut
             torch.cuda.empty_cache()
+    # adjoint workload: 16^3 hex box, p = 4, Taylor-Green + seeded perturbation (M 0.1); the adjoint RHS
+    # against the forward RHS on the same state, and the adjoint of 50 RK4 steps (dt 1e-3, checkpoints
+    # every 10), Euler and Navier-Stokes
+    adjoint = None
+    if not a.no_adjoint:
+        ma = periodic_box("hex", 16, 0.0, 2 * np.pi)
+        adjoint = dict(workload="periodic 16^3 hex box, p=4, Taylor-Green + seeded perturbation, M 0.1; "
+                                "Euler and NS (Re 1600); adjoint of one RHS and of 50 RK4 steps (dt 1e-3, "
+                                "checkpoints every 10, checkpoint allocation included)")
+        rng_a = np.random.default_rng(4242)
+        for sysname in ("euler", "ns"):
+            for prec in ("fp32", a.precision):
+                kw = dict(PRM, **REF) if sysname == "ns" else dict(gamma=1.4, **REF)
+                sa = fr.Solver(ma, 4, sysname, prec, device=local, **kw)
+                Ua = fields.perturbed_taylor_green(sa.solution_points(0), M=0.1).transpose(1, 0, 2)
+                ua = torch.from_numpy(sa.pack(0, Ua)).float().cuda()
+                la = torch.from_numpy(sa.pack(0, rng_a.standard_normal(Ua.shape))).float().cuda()
+                ra, oa = torch.empty_like(ua), torch.empty_like(ua)
+                sa.rhs([ua], [ra], stream)
+                sa.adjoint_rhs([ua], [la], [oa], stream)
+                torch.cuda.synchronize()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+                nrep = 20
+                ev[0].record(stream)
+                for _ in range(nrep):
+                    sa.rhs([ua], [ra], stream)
+                ev[1].record(stream)
+                for _ in range(nrep):
+                    sa.adjoint_rhs([ua], [la], [oa], stream)
+                ev[2].record(stream)
+                ev[3].record(stream)
+                sa.rk4_adjoint([ua], [la], 1e-3, 50, 10, stream)
+                ev[4].record(stream)
+                torch.cuda.synchronize()
+                t_f, t_a = ev[0].elapsed_time(ev[1]) / nrep, ev[1].elapsed_time(ev[2]) / nrep
+                t_rk = ev[3].elapsed_time(ev[4])
+                sa.check_finite([la])
+                st_a = sa.sync_status()
+                adjoint[f"{sysname}_{prec}"] = dict(
+                    ms_rhs=round(t_f, 4), ms_adjoint_rhs=round(t_a, 4), adjoint_over_rhs=round(t_a / t_f, 2),
+                    adjoint_gdofs=round(Ua.size / (t_a / 1e3) / 1e9, 2), ms_rk4_adjoint_50_steps=round(t_rk, 2),
+                    status="ok" if st_a == fr.OK else fr.STATUS_NAMES[st_a])
+                adjoint["dof"] = Ua.size
+                sa.close()
+                del ua, la, ra, oa
+                torch.cuda.empty_cache()
     fp32 = rhs_leg("fp32", 3) if (not a.no_fp32 and a.precision != "fp32") else None
     fp64 = rhs_leg("fp64", 2) if (not a.no_fp64 and a.precision != "fp64") else None
     bf16 = rhs_leg("bf16x3", 3) if (not a.no_bf16 and a.precision != "bf16x3") else None
@@ -547,6 +594,7 @@ def main():
                     parallelism=f"replicas x{world}", setup_s=round(t_setup, 1)),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
         clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed, tgv32_p3=tgv32,
+        adjoint_16cube_p4=adjoint,
         alu_peaks=alu_peaks, finite=finite_ok,
     )
     print(json.dumps(line))

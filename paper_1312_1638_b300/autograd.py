@@ -3,7 +3,7 @@
 ``FRStep.apply(u0, solver, dt, nsteps, every)`` returns u_N after `nsteps`
 classical RK4 steps (fr_rk4); its backward pass runs fr_rk4_adjoint with
 checkpoints every `every` steps.  Argument marshalling only: both passes run
-in the library's kernels.  Single-block Euler solvers.
+in the library's kernels.  Single-block solvers (Euler or Navier-Stokes).
 """
 
 from __future__ import annotations

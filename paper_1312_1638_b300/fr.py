@@ -403,11 +403,11 @@ class Solver:
         return adaptive_dopri5(step, save, restore, t_end, dt0, **ctl)
 
     def adjoint_rhs(self, u, lam, out, stream=None):
-        """out = (dR/du)^T lam (Euler)."""
+        """out = (dR/du)^T lam (Euler or Navier-Stokes; whole-mesh contexts)."""
         self._check(self.lib.fr_adjoint_rhs(self.ctx, _ptrs(u), _ptrs(lam), _ptrs(out), _stream_ptr(stream)))
 
     def rk4_adjoint(self, u0, lam, dt, nsteps, every=10, stream=None):
-        """lam: dK/du_N on entry, dK/du0 on return (Euler)."""
+        """lam: dK/du_N on entry, dK/du0 on return (Euler or Navier-Stokes)."""
         self._check(self.lib.fr_rk4_adjoint(self.ctx, _ptrs(u0), _ptrs(lam), C.c_double(dt), nsteps, every,
                                             _stream_ptr(stream)))
 
