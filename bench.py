@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -122,7 +123,9 @@ class ClockSampler:
     def __init__(self, uuid):
         self.uuid = uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: FR_BENCH_CLOCKS_DIR if set (to keep them), else a temporary directory
+        cdir = os.environ.get("FR_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(cdir, f"fr_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
