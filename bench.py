@@ -85,6 +85,17 @@ def _oracle_sample(order, n_sample, reps):
                        f"median of {reps} RHS evaluations ({dof} DOF, {t:.2f} s each)"), t
 
 
+def workload_config(a, world):
+    """The benchmark workload (both arms report it): the periodic n^3 hex box at
+    order p, 3D NS (5 variables), (p+1)^3 solution points per element."""
+    nelem = a.n ** 3
+    dof = nelem * (a.order + 1) ** 3 * 5
+    return dict(workload=f"3D Navier-Stokes Taylor-Green (+seeded perturbation), periodic {a.n}^3 hex box, "
+                         f"p={a.order}, {dof} DOF, precision {a.precision}",
+                elements=nelem, order=a.order, dof=dof, step="one RK4 step (4 RHS + stage combines)",
+                parallelism=f"replicas x{world}")
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -106,8 +117,9 @@ def run_reference(a):
     line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=a.gpus, steps=a.steps,
                 warmup=a.warmup, ms_per_step=dt / a.steps * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=f"NS TGV periodic hex box, p={a.order}; reference arm = CPU oracle on a "
-                                     f"bounded 8^3 sample (one RHS per step)"),
+                config=dict(workload_config(a, 1),
+                            reference="FP64 CPU oracle; each step is one oracle RHS on a bounded sample of the "
+                                      "workload (periodic 8^3 hexes, same order, physics and state), rated per DOF"),
                 cpu_baseline=dict(cb, value=val, sample="periodic 8^3 hexes, one oracle RHS per step, 1 thread"),
                 e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
@@ -590,11 +602,9 @@ def main():
         ms_per_step=ms / a.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype={"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3+f32", "bf16x3": "bf16x3+f32"}[a.precision],
         data="synthetic",
-        config=dict(workload=f"3D Navier-Stokes Taylor-Green (+seeded perturbation), periodic {a.n}^3 hex box, "
-                             f"p={a.order}, {dof} DOF, precision {a.precision}",
-                    elements=nelem, order=a.order, dof=dof, step="one RK4 step (4 RHS + stage combines)",
+        config=dict(workload_config(a, world),
                     l2="inputs larger than L2 (state alone is %.1f GB)" % (u_init.numel() * u_init.element_size() / 1e9),
-                    parallelism=f"replicas x{world}", setup_s=round(t_setup, 1)),
+                    setup_s=round(t_setup, 1)),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
         clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed, tgv32_p3=tgv32,
         adjoint_16cube_p4=adjoint,
