@@ -233,7 +233,12 @@ fr_status fr_dopri5(fr_ctx* ctx, void* const* u, double dt, int nsteps, double a
 fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
 
 /* Context options: "graphs" (default 1) enables the RK4-step CUDA graph of
- * fr_rk4.  FR_ERR_ARG for an unknown name. */
+ * fr_rk4.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
+ * the SM clock cycles after which a bounded wait inside the tensor-core
+ * operator GEMMs gives up: the kernel then drains its own copies and MMAs,
+ * returns, and fr_sync_status reports FR_ERR_TIMEOUT; the context stays
+ * usable (a small value forces this path in tests; setting the option drops
+ * the captured RK4 graph).  FR_ERR_ARG for an unknown name or a bad value. */
 fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value);
 
 /*

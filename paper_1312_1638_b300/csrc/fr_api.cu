@@ -882,6 +882,15 @@ fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value) {
         ctx->use_graphs = value != 0;
         return FR_OK;
     }
+    if (std::string(name) == "tc_wait_limit") {
+        if (value < 0) return set_err(ctx, FR_ERR_ARG, "tc_wait_limit must be >= 0");
+        ctx->dev.tc_wait_limit = value;
+        if (ctx->rk_exec) {                    // a captured RK4 step holds the old limit
+            cudaGraphExecDestroy(ctx->rk_exec);
+            ctx->rk_exec = nullptr;
+        }
+        return FR_OK;
+    }
     return set_err(ctx, FR_ERR_ARG, std::string("unknown option ") + name);
 }
 

@@ -124,6 +124,7 @@ struct DevCtx {
     std::vector<DevNeighbour> nbrs;   // partitioned context: neighbour ranks
     std::vector<DevMpiGroup> mgroups;
     int* flags = nullptr;          // [0] non-finite seen, [1] timeout
+    long long tc_wait_limit = 0;   // tensor-core GEMM wait limit in SM cycles (0: about two seconds)
     double* partial = nullptr;     // reduction scratch
     int64_t npartial = 0;
 };

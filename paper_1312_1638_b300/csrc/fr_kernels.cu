@@ -130,7 +130,8 @@ static cudaError_t op_gemm(DevCtx& c, const void* opA, const void* tcA, int M, i
         // state rows needing the reference subtracted form exactly one segment here
         const int subseg = ks1 > ks0 ? (ks0 == 0 ? 1 : 2) : 0;
         return tc::gemm(c.precision == 3 ? 0 : 1, M, K1, K - K1, tcA, (const float*)B1, (const float*)B2, N,
-                        (float*)C, epi, (const float*)rcp, ld, subseg, sr, c.flags, st);
+                        (float*)C, epi, (const float*)rcp, ld, subseg, sr, c.flags, st, nullptr, nullptr,
+                        c.tc_wait_limit);
     }
     gemm<T>(M, K, K1, opA, B1, B2, N, C, epi, rcp, ld, st, ks0, ks1, sub);
     return cudaGetLastError();
@@ -774,7 +775,7 @@ phase_b1:
                 const tc::GradXform gx{(const float*)B.smat, D, B.nupts, NV};
                 FR_TRY(tc::gemm(c.precision == 3 ? 0 : 1, D * B.nupts, B.nfpts, B.nupts, B.tcQ, (const float*)B.Qf,
                                 (const float*)u[b], N, (float*)B.Q, 0, (const float*)B.rcpdjac, B.ld, 2, sr, c.flags,
-                                st, &gx));
+                                st, &gx, nullptr, c.tc_wait_limit));
                 prof_end(c, st);
             } else {
                 FR_TRY(op_gemm<T>(c, B.opQ, B.tcQ, D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.Qf, u[b], N, B.Q, 0,
@@ -879,7 +880,7 @@ phase_c2:
                                (float*)B.rk_tmp, B.nelem};
             FR_TRY(tc::gemm(c.precision == 3 ? 0 : 1, B.nupts, B.nfpts, D * B.nupts, B.tcR, (const float*)B.Uf,
                             (const float*)B.Q, (int64_t)NV * B.ld, nullptr, 1, (const float*)B.rcpdjac, B.ld, 0,
-                            tc::SubRef{}, c.flags, st, nullptr, &f));
+                            tc::SubRef{}, c.flags, st, nullptr, &f, c.tc_wait_limit));
         } else {
             FR_TRY(op_gemm<T>(c, B.opR, B.tcR, B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.Uf, B.Q, (int64_t)NV * B.ld,
                               r[b], 1, B.rcpdjac, B.ld, st, 0, 0, Sub<T>{}));

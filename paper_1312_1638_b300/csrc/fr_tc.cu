@@ -40,8 +40,11 @@
 //               MMAs fill the next one; twelve warps keep more stores in
 //               flight.
 // Shared-memory stages form a ring; accumulators are double-buffered in
-// tensor memory whenever two fit.  Every mbarrier wait gives up after about
-// two seconds of clock cycles and raises the context's timeout flag.
+// tensor memory whenever two fit.  Every mbarrier wait gives up after a
+// cycle limit (about two seconds unless the caller sets a shorter one) and
+// raises the context's timeout flag; a CTA then still waits, with its own
+// ~2 s limit, for the bulk copies it armed and the MMAs it issued to finish
+// before it frees tensor memory and exits.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -63,6 +66,7 @@ constexpr int ROWB = 32 * KSTEPS;              // bytes of K per operand row per
 constexpr int SPART = BN * ROWB;               // one part (hi or lo) of the state operand per chunk
 constexpr int MAX_NST = 6;
 constexpr int MAX_RB = 256;                    // operator rows per block (MMA N limit)
+constexpr long long DRAIN_LIMIT = 4000000000LL;  // cycles (~2 s) for the end-of-kernel drains, whatever a.limit is
 
 // Byte offset of (row r, K byte kb) inside one operand part: core matrices of
 // 8 rows x 16 bytes, 2*KSTEPS of them along K, then the next 8-row group.
@@ -299,7 +303,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
     constexpr int CONVW = conv_warps(GD);
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[MAX_NST], bar_conv[MAX_NST], bar_empty[MAX_NST];
-    __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
+    __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
     __shared__ uint32_t tmem_holder;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -323,6 +327,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_tfull[b])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_tempty[b])), "r"(128 * EG));
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_drain)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -363,6 +368,10 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                         : "memory");
                 }
             }
+            // copies possibly still in flight (after any role gave up): wait for the
+            // last chunk armed on every stage before the CTA may exit
+            for (int i = it > L.nst ? it - L.nst : 0; i < it; ++i)
+                if (!mbar_wait(smem_u32(&bar_full[i % L.nst]), (i / L.nst) & 1, DRAIN_LIMIT)) ok = false;
             if (!ok) atomicOr(&a.flags[1], 1);
         }
     } else if (warp == 1) {
@@ -404,6 +413,12 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                                  smem_u32(&bar_tfull[b]))
                              : "memory");
             }
+            // MMAs possibly still in flight: one more commit, waited for, before
+            // tensor memory is freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar_drain))
+                         : "memory");
+            if (!mbar_wait(smem_u32(&bar_drain), 0, DRAIN_LIMIT)) ok = false;
             if (!ok) atomicOr(&a.flags[1], 1);
         }
     } else if (warp < 2 + CONVW) {
@@ -711,7 +726,7 @@ static cudaError_t launch(const TcArgs& a, int nt, const CUtensorMap& m1, const 
 
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
-                 cudaStream_t st, const GradXform* gx, const RkFuse* rk) {
+                 cudaStream_t st, const GradXform* gx, const RkFuse* rk, long long wait_limit) {
     if (!g_nsm) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
@@ -742,7 +757,7 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
     a.sub3 = sub.v[3];
     a.sub4 = sub.v[4];
     a.flags = flags;
-    a.limit = 4000000000LL;                  // ~2 s of SM clock cycles per wait
+    a.limit = wait_limit > 0 ? wait_limit : 4000000000LL;   // SM clock cycles per wait (default ~2 s)
     a.ntiles = (int)((N + nt * BN - 1) / (nt * BN));
     a.nwork = a.ntiles * a.nrb;
     a.smat = gx ? gx->smat : nullptr;

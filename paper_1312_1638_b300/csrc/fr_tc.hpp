@@ -57,9 +57,12 @@ struct RkFuse {
     int64_t nelem;
 };
 
+// wait_limit: SM clock cycles after which a bounded wait gives up and sets
+// flags[1] (0: about two seconds)
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
-                 cudaStream_t st, const GradXform* gx = nullptr, const RkFuse* rk = nullptr);
+                 cudaStream_t st, const GradXform* gx = nullptr, const RkFuse* rk = nullptr,
+                 long long wait_limit = 0);
 
 // whether an M-row operator runs with two 128-column subtiles, the kernels
 // that carry the fused RK stage epilogue (M <= 128)

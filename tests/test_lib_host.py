@@ -124,3 +124,17 @@ def test_bad_arguments(fr):
     s = fr.Solver(m, 1, device=-1)
     assert s.lib.fr_rhs(s.ctx, None, None, None) in (fr.ERR_ARG, fr.ERR_UNSUPPORTED)
     assert s.lib.fr_layout(s.ctx, 5, None, None, None, None, None) == fr.ERR_ARG
+
+
+def test_context_options_are_validated(fr):
+    m = periodic_box("quad", 2, 0.0, 1.0)
+    s = fr.Solver(m, 1, "euler", "tf32x3", device=-1)
+    s.set_option("graphs", 0)
+    s.set_option("tc_wait_limit", 1000)
+    s.set_option("tc_wait_limit", 0)                     # back to the default limit
+    with pytest.raises(fr.FRError) as e:
+        s.set_option("tc_wait_limit", -1)
+    assert e.value.status == fr.ERR_ARG
+    with pytest.raises(fr.FRError) as e:
+        s.set_option("no_such_option", 1)
+    assert e.value.status == fr.ERR_ARG
