@@ -191,7 +191,7 @@ fr_status fr_pairs(const fr_ctx* ctx, int64_t* npairs, int64_t* out);
 fr_status fr_rhs(fr_ctx* ctx, void* const* u, void* const* r, void* stream);
 
 /*
- * fr_rhs_host -- as fr_rhs, but u and r are HOST buffers (any host memory;
+ * fr_rhs_host -- as fr_rhs (Eq. negdivconf, App. A), but u and r are HOST buffers (any host memory;
  * pinned memory makes the copies asynchronous).  The library copies u to a
  * device staging buffer it owns, evaluates R, copies r back and synchronises
  * `stream` before returning.  u and r may alias.
@@ -232,7 +232,7 @@ fr_status fr_dopri5(fr_ctx* ctx, void* const* u, double dt, int nsteps, double a
  */
 fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
 
-/* Context options: "graphs" (default 1) enables the RK4-step CUDA graph of
+/* Context options (not in the paper): "graphs" (default 1) enables the RK4-step CUDA graph of
  * fr_rk4.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
  * operator GEMMs gives up: the kernel then drains its own copies and MMAs,
@@ -279,7 +279,7 @@ fr_status fr_rk4_adjoint(fr_ctx* ctx, void* const* u0, void* const* lambda, doub
 fr_status fr_sum_weighted(fr_ctx* ctx, void* const* u, double* out, void* stream);
 
 /*
- * fr_rk4_noalloc -- the same RK4 step as fr_rk4, for callers that cannot let
+ * fr_rk4_noalloc -- the same RK4 step as fr_rk4 (end of Sec. 2), for callers that cannot let
  * a library allocate device memory at call time.  The paper has no
  * counterpart; it exists for applications whose framework owns all device
  * memory through its own pool (a cudaMalloc behind its back fails or
@@ -306,15 +306,16 @@ fr_status fr_sum_weighted(fr_ctx* ctx, void* const* u, double* out, void* stream
 fr_status fr_rk4_noalloc(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
 
 /* Reads and clears the device error flags (non-finite values seen by
- * fr_check_finite, timeouts).  Synchronises the device. */
+ * fr_check_finite, timeouts); not in the paper.  Synchronises the device. */
 fr_status fr_sync_status(fr_ctx* ctx);
 
-/* Scans u for NaN/Inf on the device; the result is reported by the next
- * fr_sync_status() as FR_ERR_NONFINITE.  Stream-ordered. */
+/* Scans u for NaN/Inf on the device (not in the paper); the result is
+ * reported by the next fr_sync_status() as FR_ERR_NONFINITE.  Stream-ordered. */
 fr_status fr_check_finite(fr_ctx* ctx, void* const* u, void* stream);
 
 /*
- * Kernel-level timing.  fr_profile_enable(ctx, 1) makes every later kernel
+ * Kernel-level timing (not in the paper; its kernel names follow the kernel
+ * flow of Sec. 3.6 / App. A).  fr_profile_enable(ctx, 1) makes every later kernel
  * launch of fr_rhs / fr_rk4 record a CUDA event pair on its launch stream.
  * fr_profile_read synchronises on those events and returns, per kernel, the
  * number of launches and the total event-measured milliseconds since the
@@ -326,14 +327,16 @@ fr_status fr_check_finite(fr_ctx* ctx, void* const* u, void* stream);
 fr_status fr_profile_enable(fr_ctx* ctx, int enable);
 fr_status fr_profile_read(fr_ctx* ctx, int32_t* nkernels, char* names, int64_t* launches, double* ms);
 
-/* Message for the last failure on ctx (ctx == NULL: last fr_setup failure). */
+/* Message for the last failure on ctx (ctx == NULL: last fr_setup failure);
+ * not in the paper. */
 const char* fr_last_error(const fr_ctx* ctx);
 
-/* Frees everything the context owns.  Synchronises its device. */
+/* Frees everything the context owns (not in the paper).  Synchronises its device. */
 void fr_destroy(fr_ctx* ctx);
 
 /*
- * Measured FMA throughput of the CUDA cores of device cuda_device, in TFLOP/s
+ * Measured FMA throughput (not in the paper; the paper's Sec. 6 rates its
+ * kernels against the device peaks) of the CUDA cores of device cuda_device, in TFLOP/s
  * (2 flop per FMA): eight independent FP32 (resp. FP64) FMA chains per thread
  * over 8 blocks of 256 threads per SM, best of three timed launches.  Used as
  * the ALU roofline of the plain FP32 and FP64 paths.  Synchronous; sets the
@@ -367,7 +370,7 @@ fr_status fr_setup_part(const fr_mesh* mesh, const fr_params* prm, int cuda_devi
                         int32_t nparts, int32_t rank, fr_ctx** out);
 
 /*
- * Exchange slots of a partitioned context: *nnbr neighbour ranks (ascending)
+ * Exchange slots of a partitioned context (Sec. 3.6 "mpi" interfaces): *nnbr neighbour ranks (ascending)
  * in ranks[], their slot counts in nslots[], and for every slot, neighbour by
  * neighbour, the global L side (block, element, flux point) as 3 int64 in
  * keys[].  Arrays may be NULL (sizes only).  Host-only contexts work too.
@@ -375,7 +378,8 @@ fr_status fr_setup_part(const fr_mesh* mesh, const fr_params* prm, int cuda_devi
 fr_status fr_part_slots(const fr_ctx* ctx, int32_t* nnbr, int32_t* ranks, int64_t* nslots, int64_t* keys);
 
 /*
- * One right-hand side of every partition, all on the calling device:
+ * One right-hand side of every partition (Sec. 3.6: the kernel flow split
+ * into interior ("int") and partition ("mpi") interfaces), all on the calling device:
  * parts[p] is the context of rank p, u[p] / r[p] its per-block state and
  * result pointers (layout of fr_layout on parts[p]).  Per partition and stage:
  * interpolation and packing of the shared flux-point values; exchange of the
@@ -389,7 +393,7 @@ fr_status fr_part_slots(const fr_ctx* ctx, int32_t* nnbr, int32_t* ranks, int64_
 fr_status fr_rhs_parts(fr_ctx* const* parts, int32_t nparts, void* const* const* u, void* const* const* r,
                        void* stream);
 
-/* ABI version (increments on any signature change). */
+/* ABI version (increments on any signature change); not in the paper. */
 int32_t fr_version(void);   /* 4 */
 
 #ifdef __cplusplus

@@ -3,6 +3,7 @@ in include/fr.h, and its host-side set-up (operators, solution points,
 interface pairs, error statuses) agrees with the oracle.  No compute calls
 are made (no GPU here)."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -138,3 +139,28 @@ def test_context_options_are_validated(fr):
     with pytest.raises(fr.FRError) as e:
         s.set_option("no_such_option", 1)
     assert e.value.status == fr.ERR_ARG
+
+
+def test_every_abi_declaration_cites_its_passage():
+    """Each entry point of include/fr.h is preceded by a comment that cites the
+    paper passage defining it (Sec., Eq., App.) or says it is not in the paper."""
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fr.h")).read()
+    decls = list(re.finditer(r"^(?:fr_status|int32_t|const char\*|void)\s+(fr_\w+)\(", src, re.M))
+    assert len(decls) >= 20
+    bad = []
+    for m in decls:
+        # skip #defines and the declarations of a group that shares one comment
+        lines = src[:m.start()].rstrip().split("\n")
+        while lines and (not lines[-1].strip() or lines[-1].startswith("#define")
+                         or re.match(r"^(fr_status|int32_t|const char\*|void)\s+fr_\w+\(", lines[-1])
+                         or (lines[-1].startswith("    ") and lines[-1].rstrip().endswith(");"))):
+            lines.pop()
+        before = "\n".join(lines)
+        if not before.rstrip().endswith("*/"):
+            bad.append((m.group(1), "no comment"))
+            continue
+        c = before[before.rfind("/*"):]
+        if not re.search(r"Sec\.|Eq\.|App\.|not in the paper", c):
+            bad.append((m.group(1), "no citation"))
+    assert not bad, bad
