@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed quad/triangle annulus leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (16^3 hex box) leg")
+    ap.add_argument("--extra-legs", action="store_true",
+                    help="also time the SD / HU correction functions and the Euler / DOPRI5 steppers (64^3 box)")
     return ap.parse_args()
 
 
@@ -591,6 +593,52 @@ def main():
                 sa.close()
                 del ua, la, ra, oa
                 torch.cuda.empty_cache()
+    # rows without a leg of their own in the default run: the SD / HU correction functions (the DG
+    # kernels with other operator values) and the forward Euler / DOPRI5 steppers, on a 64^3 box
+    extra = None
+    if a.extra_legs:
+        mx = periodic_box("hex", 64, 0.0, 2 * np.pi)
+        extra = dict(workload=f"periodic 64^3 hex box, p={a.order}, NS Taylor-Green + seeded perturbation, "
+                              f"precision {a.precision}")
+        dtx = torch.float64 if a.precision == "fp64" else torch.float32
+        for corr in ("dg", "sd", "hu"):
+            sx = fr.Solver(mx, a.order, "ns", a.precision, device=local, correction=corr, **PRM, **REF)
+            Ux = fields.perturbed_taylor_green(sx.solution_points(0), M=0.1).transpose(1, 0, 2)
+            ux = torch.from_numpy(sx.pack(0, Ux)).to(dtx).cuda()
+            rx = torch.empty_like(ux)
+            sx.rhs([ux], [rx], stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(10):
+                sx.rhs([ux], [rx], stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extra[f"{corr}_gdofs_per_rhs"] = round(Ux.size * 10 / (e0.elapsed_time(e1) / 1e3) / 1e9, 2)
+            if corr == "dg":
+                # 5 steps of each stepper after one warm-up step; DOPRI5 evaluates 7 RHS on a call's
+                # first step and 6 on the others (first stage reused)
+                n = 5
+                for name, fn, nrhs in (("rk4", lambda k: sx.rk4([ux], 1e-4, k, stream), 4.0),
+                                       ("euler", lambda k: sx.euler([ux], 1e-5, k, stream), 1.0),
+                                       ("dopri5", lambda k: sx.dopri5([ux], 1e-4, k, stream=stream),
+                                        (7.0 + 6.0 * (n - 1)) / n)):
+                    fn(1)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    fn(n)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms_s = e0.elapsed_time(e1) / n
+                    extra[f"{name}_ms_per_step"] = round(ms_s, 3)
+                    extra[f"{name}_gdofs_per_rhs"] = round(Ux.size * nrhs / (ms_s / 1e3) / 1e9, 2)
+            sx.check_finite([ux])
+            stx = sx.sync_status()
+            extra[f"{corr}_status"] = "ok" if stx == fr.OK else fr.STATUS_NAMES[stx]
+            extra["dof"] = Ux.size
+            sx.close()
+            del ux, rx
+            torch.cuda.empty_cache()
     fp32 = rhs_leg("fp32", 3) if (not a.no_fp32 and a.precision != "fp32") else None
     fp64 = rhs_leg("fp64", 2) if (not a.no_fp64 and a.precision != "fp64") else None
     bf16 = rhs_leg("bf16x3", 3) if (not a.no_bf16 and a.precision != "bf16x3") else None
@@ -607,7 +655,7 @@ def main():
                     setup_s=round(t_setup, 1)),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
         clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed, tgv32_p3=tgv32,
-        adjoint_16cube_p4=adjoint,
+        adjoint_16cube_p4=adjoint, corrections_steppers_64cube=extra,
         alu_peaks=alu_peaks, finite=finite_ok,
     )
     print(json.dumps(line))
