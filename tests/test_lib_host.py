@@ -164,3 +164,35 @@ def test_every_abi_declaration_cites_its_passage():
         if not re.search(r"Sec\.|Eq\.|App\.|not in the paper", c):
             bad.append((m.group(1), "no citation"))
     assert not bad, bad
+
+
+@pytest.mark.parametrize("entry", [(1, 0, 0, 2), (0, 99, 0, 2), (0, 0, 7, 2), (0, 0, 0, 4), (0, 0, 0, -1)])
+def test_bad_boundary_entry_is_a_mesh_error(fr, entry):
+    # an unknown block, element, face or boundary type in the boundary list
+    m = periodic_box("quad", 3)
+    m.periodic = m.periodic[:1]                          # y faces become boundaries
+    import numpy as np
+    ny = [(0, e, f, 2) for e in range(9) for f in range(4) if (f == 0 and e < 3) or (f == 2 and e >= 6)]
+    fr.Solver(Mesh(2, m.blocks, np.array(ny, dtype=np.int64), m.periodic), 1, device=-1)   # the valid list
+    bf = np.array(ny + [entry], dtype=np.int64)
+    m2 = Mesh(2, m.blocks, bf, m.periodic)
+    with pytest.raises(fr.FRError) as e:
+        fr.Solver(m2, 1, device=-1)
+    assert e.value.status in (fr.ERR_MESH, fr.ERR_ARG)
+
+
+def test_paired_face_listed_as_boundary_is_a_mesh_error(fr):
+    import numpy as np
+    m = periodic_box("quad", 3)
+    m2 = Mesh(2, m.blocks, np.array([(0, 4, 1, 2)], dtype=np.int64), m.periodic)   # an interior face
+    with pytest.raises(fr.FRError) as e:
+        fr.Solver(m2, 1, device=-1)
+    assert e.value.status == fr.ERR_MESH
+
+
+def test_device_calls_on_a_host_only_context_are_refused(fr):
+    m = periodic_box("quad", 2)
+    s = fr.Solver(m, 1, "ns", "fp64", device=-1, mu=0.01)
+    assert s.lib.fr_adjoint_rhs(s.ctx, None, None, None, None) in (fr.ERR_ARG, fr.ERR_UNSUPPORTED)
+    assert s.lib.fr_rk4(s.ctx, None, 1e-3, 1, None) in (fr.ERR_ARG, fr.ERR_UNSUPPORTED)
+    assert s.lib.fr_sync_status(s.ctx) == fr.ERR_UNSUPPORTED
