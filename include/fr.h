@@ -293,13 +293,19 @@ fr_status fr_sum_weighted(fr_ctx* ctx, void* const* u, double* out, void* stream
  *   - Limit: the registers need 2 * nupts * nvars * ld * sizeof(real) bytes
  *     per block (each rounded up to 256); larger meshes are rejected with
  *     FR_ERR_ARG and a message naming both sizes, before anything runs.
- *   - Set-up: the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *   - Set-up: fr_setup looks up the array's device address on the context's
+ *     device (cudaGetSymbolAddress, with that device current).  That look-up
+ *     loads the part of the library that holds the array and so reserves its
+ *     FR_NOALLOC_MAX_BYTES there: set up the context before the caller's pool
+ *     takes the GPU's memory.  Should that look-up have failed, the first call
+ *     repeats it and reports the failure (FR_ERR_CUDA); such a first call
+ *     must not run inside a stream capture.
  *   - Sharing: every call, from any context or stream, uses the same array,
  *     which keeps the last call's contents (nothing needs clearing: each call
  *     writes every byte it reads).  Calls that overlap on the GPU race on it:
  *     serialise them.
+ *   - Kernel timing (fr_profile_enable) is suspended during the call, since
+ *     its CUDA events may allocate; the call's kernels are not timed.
  * u, dt, nsteps and stream as for fr_rk4; at most 16 element blocks.
  */
 #define FR_NOALLOC_MAX_BYTES (64u * 1024u * 1024u)

@@ -526,6 +526,7 @@ static fr_status setup_impl(const fr_mesh* mesh, const fr_params* prm, int devic
             upload_device(c.get());
             if (part) upload_part(c.get(), mp);
             if (prm->precision == FR_PREC_BF16X3 || prm->precision == FR_PREC_TF32X3) CK(fr::tc::prepare());
+            fr::noalloc_prepare(device);
             // the host pair list is only kept for inspection of small meshes
             if (c->pairs.size() > (size_t)4000000) { c->pairs.clear(); c->pairs.shrink_to_fit(); }
         } else {

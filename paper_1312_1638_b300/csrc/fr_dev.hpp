@@ -166,6 +166,9 @@ cudaError_t launch_sum_weighted(DevCtx& c, void* const* u, double* host_out, cud
 cudaError_t launch_check_finite(DevCtx& c, void* const* u, cudaStream_t st);
 // FP32 and FP64 FMA throughput of the current device (TFLOP/s), synchronous
 cudaError_t measure_fma(double* fp32_tflops, double* fp64_tflops);
+// look up the allocation-free RK4's fixed device array on `device` (current),
+// reserving it there; failures are left for fr_rk4_noalloc to report
+void noalloc_prepare(int device);
 
 }  // namespace fr
 

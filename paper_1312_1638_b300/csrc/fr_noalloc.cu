@@ -8,8 +8,11 @@
 // cudaMalloc/cudaFree because those calls can synchronise the whole device.
 // This entry point gives them the same RK4 step with the registers placed in
 // a fixed array compiled into the library (`fr_noalloc_scratch` below), so the
-// call itself allocates nothing.  The array costs every GPU that loads
-// libfr.so FR_NOALLOC_MAX_BYTES of device memory until the process exits.
+// call itself allocates nothing.  The array lives in this file's own module,
+// which the CUDA runtime loads on a device the first time its address is
+// looked up there; fr_setup does that look-up on the context's device, so the
+// array's FR_NOALLOC_MAX_BYTES are reserved when the context is set up (when
+// the library allocates anyway) and stay reserved until the process exits.
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -44,14 +47,16 @@ cudaError_t scratch_address(int device, void** out) {
     return cudaSuccess;
 }
 
+// stage combination, k in tmp: first stage acc = u + a_acc k, later stages
+// acc += a_acc k; then tmp = u + a_tmp k
 template <typename T>
 __global__ void stage_kernel(int64_t n, T* __restrict__ acc, T* __restrict__ tmp, const T* __restrict__ u,
-                             T a_acc, T a_tmp) {
+                             T a_acc, T a_tmp, int first) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    T k = tmp[i];
-    acc[i] += a_acc * k;
-    tmp[i] = u[i] + a_tmp * k;
+    const T k = tmp[i], ui = u[i];
+    acc[i] = (first ? ui : acc[i]) + a_acc * k;
+    tmp[i] = ui + a_tmp * k;
 }
 
 template <typename T>
@@ -80,15 +85,9 @@ cudaError_t rk4_static(fr::DevCtx& c, void* const* u, double dt, int nsteps, uns
     const double a_acc[4] = {dt / 6, dt / 3, dt / 3, dt / 6};
     const double a_tmp[3] = {dt / 2, dt / 2, dt};
     for (int step = 0; step < nsteps; ++step) {
-        for (size_t b = 0; b < nb; ++b) {
-            const fr::DevBlock& B = c.blocks[b];
-            size_t bytes = (size_t)B.nupts * B.nvars * B.ld * sizeof(T);
-            cudaError_t e = cudaMemcpyAsync(acc[b], u[b], bytes, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(tmp[b], u[b], bytes, cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return e;
-        }
         for (int s = 0; s < 4; ++s) {
-            cudaError_t e = fr::launch_rhs(c, tmp, tmp, st);
+            // the first stage reads u directly; later stages read the stage state in tmp
+            cudaError_t e = fr::launch_rhs(c, s == 0 ? u : tmp, tmp, st);
             if (e != cudaSuccess) return e;
             for (size_t b = 0; b < nb; ++b) {
                 const fr::DevBlock& B = c.blocks[b];
@@ -96,7 +95,7 @@ cudaError_t rk4_static(fr::DevCtx& c, void* const* u, double dt, int nsteps, uns
                 unsigned grid = (unsigned)((n + 255) / 256);
                 if (s < 3)
                     stage_kernel<T><<<grid, 256, 0, st>>>(n, (T*)acc[b], (T*)tmp[b], (const T*)u[b], T(a_acc[s]),
-                                                          T(a_tmp[s]));
+                                                          T(a_tmp[s]), s == 0);
                 else
                     final_kernel<T><<<grid, 256, 0, st>>>(n, (const T*)acc[b], (const T*)tmp[b], (T*)u[b],
                                                           T(a_acc[3]));
@@ -107,6 +106,18 @@ cudaError_t rk4_static(fr::DevCtx& c, void* const* u, double dt, int nsteps, uns
 }
 
 }  // namespace
+
+namespace fr {
+// Called by fr_setup with the context's device current: looks up (and so
+// reserves) the array on that device, so that fr_rk4_noalloc's calls find
+// its address cached.  A failure here is not an error of the set-up; the
+// entry point then tries again and reports it.
+void noalloc_prepare(int device) {
+    void* p = nullptr;
+    (void)scratch_address(device, &p);
+    (void)cudaGetLastError();
+}
+}  // namespace fr
 
 extern "C" fr_status fr_rk4_noalloc(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream) {
     fr::DevCtx* c = fr::ctx_dev(ctx);
@@ -143,8 +154,13 @@ extern "C" fr_status fr_rk4_noalloc(fr_ctx* ctx, void* const* u, double dt, int 
         return FR_ERR_CUDA;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // kernel timing records CUDA events, which the runtime may allocate: it is
+    // suspended for this call (its kernels are not timed)
+    const bool prof = c->prof;
+    c->prof = false;
     e = c->precision == FR_PREC_FP64 ? rk4_static<double>(*c, u, dt, nsteps, (unsigned char*)base, st)
                                      : rk4_static<float>(*c, u, dt, nsteps, (unsigned char*)base, st);
+    c->prof = prof;
     if (e != cudaSuccess) {
         fr::ctx_set_error(ctx, cudaGetErrorString(e));
         return FR_ERR_CUDA;

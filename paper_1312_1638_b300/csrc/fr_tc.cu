@@ -255,6 +255,7 @@ __device__ __forceinline__ void epi_grad(const TcArgs& a, uint32_t tcol, int p0,
 #pragma unroll 1
     for (int u0 = u_first; u0 < np; u0 += u_step) {
         uint32_t r[4 * D];
+        __syncwarp();                                  // reconverge after the lane-dependent stores
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             const uint32_t ta = tcol + (uint32_t)(u0 * D + 4 * k);
@@ -497,7 +498,10 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
             const int rbase = rb * a.rr;                          // first operator row of the block
             const int mr = min(a.rr, a.M - rbase);                // real rows in the block
             const int b = wc % L.tbuf;
-            if (!mbar_wait(smem_u32(&bar_tfull[b]), (wc / L.tbuf) & 1, a.limit)) { ok = false; break; }
+            // the give-up decision is taken by the whole warp: the tensor-memory loads
+            // below are .sync.aligned and must be executed by all 32 lanes or none
+            const bool got = mbar_wait(smem_u32(&bar_tfull[b]), (wc / L.tbuf) & 1, a.limit);
+            if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
@@ -516,6 +520,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                 for (int r0 = 16 * grp; r0 < mr; r0 += 16 * EG) {
                     uint32_t r[16];
                     const uint32_t taddr = tcol + (uint32_t)r0;
+                    __syncwarp();                          // reconverge after the lane-dependent stores
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
                         "%12, %13, %14, %15}, [%16];"

@@ -4,10 +4,15 @@ GPU's memory through its own pool; loops in which cudaMalloc/cudaFree, which
 may synchronise the device, must not run).  Its stage registers live in a
 fixed device array inside libfr.so instead of memory from cudaMalloc.
 
-The test calls it through the C ABI and checks it against fr_rk4 (same
-tolerance as the other FP64 / FP32 tests) on two calls in a row, and checks
-that a mesh whose registers exceed the fixed array is refused before
-anything runs.  It sits in a file of its own, collected last.
+The test calls it through the C ABI and checks it against fr_rk4 on two
+calls in a row, in every precision: FP64 and FP32 at the tolerances of the
+other FP64 / FP32 tests, and the split-precision paths (TF32x3, BF16x3), on
+which fr_rk4 runs the stage combination inside the divergence product while
+this entry point runs it as a separate kernel, at the split-precision bound
+2e-5.  Around the second call it checks that the device's free memory is
+unchanged, and it checks that a mesh whose registers exceed the fixed array
+is refused before anything runs.  It sits in a file of its own, collected
+last.
 """
 import ctypes as C
 
@@ -20,7 +25,7 @@ from tests.libutil import ensure_built, rel_l2_per_var
 pytestmark = pytest.mark.gpu
 
 PRM = dict(gamma=1.4, mu=0.02, prandtl=0.72, ldg_beta=0.5, ldg_tau=0.1)
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 2e-5, "bf16x3": 2e-5}
 
 
 def _ptrs(ts):
@@ -30,7 +35,7 @@ def _ptrs(ts):
     return arr
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_noalloc_rk4_matches_rk4_on_two_calls(prec):
     import torch
     assert torch.cuda.is_available()
@@ -46,9 +51,14 @@ def test_noalloc_rk4_matches_rk4_on_two_calls(prec):
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     for call in range(2):
         s.rk4([u_ref], 2e-3, 2)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = s.lib.fr_rk4_noalloc(s.ctx, _ptrs([u_new]), C.c_double(2e-3), 2, stream)
         assert st == fr.OK, s.lib.fr_last_error(s.ctx)
         torch.cuda.synchronize()
+        if call == 1:
+            # the second call finds every kernel loaded: nothing may take device memory
+            assert torch.cuda.mem_get_info()[0] == free0
         n = m.nelem
         a = u_ref[:, :, :n].cpu().numpy().astype(np.float64)
         b = u_new[:, :, :n].cpu().numpy().astype(np.float64)
