@@ -9,7 +9,12 @@ benchmark is a periodic hexahedral box at p = 2..4 (Sec. 6); its meshes are
 not published and this box stands in for them.
 
 One step = one classical RK4 step (4 right-hand sides + stage combines) via
-fr_rk4; the metric is N_V * sum_e N_e^(u) |Omega_e| * 4 * steps / time / 1e9.
+fr_rk4, replayed as a captured CUDA graph (the library's default); the metric
+is N_V * sum_e N_e^(u) |Omega_e| * 4 * steps / time / 1e9.  Per-kernel times
+come from a second pass over the same steps with kernel timing on (direct
+launches, CUDA events around every kernel).  The comparison legs (FP64, FP32,
+BF16x3) are timed per RK stage as well, and the error of each precision's
+RHS against the FP64 GPU RHS of the same state is stated per variable.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -61,30 +66,96 @@ def _args():
 
 
 # ---------------------------------------------------------------- CPU oracle leg
-def oracle_sample(order, n_sample=16, reps=3):
-    """Time the FP64 CPU oracle's RHS on a bounded sample of the workload
-    (periodic n_sample^3 hexes, same order and physics).  The oracle's
-    contractions are numpy einsum loops (no BLAS), i.e. one host thread."""
-    return _oracle_sample(order, n_sample, reps)
-
-
-def _oracle_sample(order, n_sample, reps):
+def _oracle_system(n_sample, order):
     from fr_inputs import periodic_box, fields
     from oracle.system import FRSystem
     m = periodic_box("hex", n_sample, 0.0, 2 * np.pi)
     o = FRSystem(m, order, "ns", **PRM)
     U = [fields.perturbed_taylor_green(o.solution_coords(0), M=0.1).transpose(1, 0, 2).copy()]
-    o.rhs(U)                                      # warm-up
-    ts = []
-    for _ in range(reps):
+    return o, U
+
+
+def _oracle_worker(n_sample, order, warmup, reps, barrier, queue):
+    """One oracle process: set up, warm up, wait for the others, time `reps` RHS."""
+    try:
+        o, U = _oracle_system(n_sample, order)
+        for _ in range(warmup):
+            o.rhs(U)
+        barrier.wait(timeout=900)
         t0 = time.perf_counter()
-        o.rhs(U)
-        ts.append(time.perf_counter() - t0)
-    t = statistics.median(ts)
-    dof = U[0].size
-    return dict(value=dof / t / 1e9, unit=UNIT, cores=1, kind="oracle",
-                sample=f"periodic {n_sample}^3 hexes, p={order}, NS, FP64 numpy oracle, "
-                       f"median of {reps} RHS evaluations ({dof} DOF, {t:.2f} s each)"), t
+        for _ in range(reps):
+            o.rhs(U)
+        queue.put((U[0].size, reps, time.perf_counter() - t0))
+    except Exception as e:                                    # reported, not hidden
+        queue.put(("error", repr(e), 0.0))
+
+
+def oracle_processes(n_sample, order, nproc, warmup, reps):
+    """Time the FP64 oracle's RHS in `nproc` independent processes at once
+    (spawned, one host thread each: numpy's einsum contractions are single-
+    threaded and the thread pools are pinned to one thread), each on its own
+    copy of the periodic n_sample^3 sample.  Returns (GDOF/s over all
+    processes, slowest process's seconds per RHS, processes)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        barrier, queue = ctx.Barrier(nproc), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker, args=(n_sample, order, warmup, reps, barrier, queue))
+                 for _ in range(nproc)]
+        for pr in procs:
+            pr.start()
+        res = [queue.get(timeout=1800) for _ in procs]
+        for pr in procs:
+            pr.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    bad = [r for r in res if r[0] == "error"]
+    if bad:
+        raise RuntimeError(f"oracle process failed: {bad[0][1]}")
+    tmax = max(r[2] for r in res)
+    return sum(r[0] * r[1] for r in res) / tmax / 1e9, tmax / reps, nproc
+
+
+def host_cores():
+    """Cores this process may run on, and how many oracle processes of
+    `per_proc_gb` fit in the available host memory."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    avail = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return n, avail
+
+
+def oracle_baseline(order, n_sample=16):
+    """The oracle on the host cores: one process alone (the 1-thread figure),
+    then one process per core at once (memory permitting), both on the
+    periodic n_sample^3 sample of the workload."""
+    n, avail = host_cores()
+    per_proc = 1.2e9 * (n_sample / 16.0) ** 3             # measured peak RSS ~0.8 GB at 16^3, p=4
+    nproc = max(1, min(n, int(0.7 * avail / per_proc) if avail else n))
+    one, t_one, _ = oracle_processes(n_sample, order, 1, 1, 2)
+    allc, t_all, used = oracle_processes(n_sample, order, nproc, 1, 2)
+    dof = n_sample ** 3 * (order + 1) ** 3 * 5
+    return dict(value=allc, unit=UNIT, cores=used, kind="oracle", host_cores=n,
+                single_thread_value=one,
+                sample=f"periodic {n_sample}^3 hexes, p={order}, NS, FP64 numpy oracle ({dof} DOF per copy); "
+                       f"{used} independent processes (one thread each) ran 2 RHS each at once after one "
+                       f"warm-up, {t_all:.2f} s per RHS in the slowest; alone: {t_one:.2f} s per RHS "
+                       f"(single_thread_value); rated per DOF per RHS")
 
 
 def workload_config(a, world):
@@ -99,30 +170,25 @@ def workload_config(a, world):
 
 
 def run_reference(a):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores;
+    each step is one oracle RHS in every process on its own bounded 8^3
+    sample of the workload (same order, physics and state), rated per DOF."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cb, _ = oracle_sample(a.order, n_sample=8, reps=1)
-    # each step = one oracle RHS on the bounded sample
-    from fr_inputs import periodic_box, fields
-    from oracle.system import FRSystem
-    m = periodic_box("hex", 8, 0.0, 2 * np.pi)
-    o = FRSystem(m, a.order, "ns", **PRM)
-    U = [fields.perturbed_taylor_green(o.solution_coords(0), M=0.1).transpose(1, 0, 2).copy()]
-    for _ in range(a.warmup):
-        o.rhs(U)
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        o.rhs(U)
-    dt = time.perf_counter() - t0
-    val = U[0].size * a.steps / dt / 1e9
+    n, avail = host_cores()
+    nproc = max(1, min(n, int(0.7 * avail / 0.3e9) if avail else n))
+    val, t_rhs, used = oracle_processes(8, a.order, nproc, a.warmup, a.steps)
+    dof8 = 8 ** 3 * (a.order + 1) ** 3 * 5
+    sample = (f"periodic 8^3 hexes, p={a.order}, NS, FP64 numpy oracle, {used} independent processes (one thread "
+              f"each), {a.steps} RHS each after {a.warmup} warm-up; {dof8} DOF per copy")
+    cfg = dict(workload_config(a, 1))
+    cfg["workload"] = (f"FP64 CPU oracle on a bounded sample of the benchmark workload ({sample}); the workload: "
+                       + cfg["workload"])
     line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=a.gpus, steps=a.steps,
-                warmup=a.warmup, ms_per_step=dt / a.steps * 1e3, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload_config(a, 1),
-                            reference="FP64 CPU oracle; each step is one oracle RHS on a bounded sample of the "
-                                      "workload (periodic 8^3 hexes, same order, physics and state), rated per DOF"),
-                cpu_baseline=dict(cb, value=val, sample="periodic 8^3 hexes, one oracle RHS per step, 1 thread"),
+                warmup=a.warmup, ms_per_step=t_rhs * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", config=cfg,
+                cpu_baseline=dict(value=val, unit=UNIT, cores=used, kind="oracle", sample=sample),
                 e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
     return 0
@@ -286,7 +352,7 @@ def main():
 
     cpu_baseline = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        cpu_baseline, _ = oracle_sample(a.order)         # before any CUDA call
+        cpu_baseline = oracle_baseline(a.order)          # spawned processes, before any CUDA call
 
     import torch
     from fr_inputs import periodic_box, fields
@@ -340,17 +406,17 @@ def main():
     stream = torch.cuda.current_stream()
     dt = 1e-4
 
+    # warm-up: the first call captures the RK4 step as a CUDA graph
     for _ in range(a.warmup):
         s.rk4([u], dt, 1, stream)
     torch.cuda.synchronize()
-    s.profile_enable(True)
-    s.profile_read()
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         uuid = None
+    # headline: the product's default path, one captured RK4 step replayed per step
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(uuid) as clk:
         barrier()
@@ -362,14 +428,25 @@ def main():
         torch.cuda.synchronize()
         barrier()
     ms = ev0.elapsed_time(ev1)
-    prof = s.profile_read()
-    s.profile_enable(False)
     stages = 4 * a.steps
     value, ms = replica_value(ms, dof * stages, world, dist, "cuda")
     assert s.sync_status() == fr.OK
+    # kernel-level pass: the same steps launched directly, each kernel between a
+    # pair of CUDA events on the launch stream (graph replay is off while timing)
+    s.profile_enable(True)
+    s.profile_read()
+    evp0, evp1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evp0.record(stream)
+    for _ in range(a.steps):
+        s.rk4([u], dt, 1, stream)
+    evp1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = evp0.elapsed_time(evp1)
+    prof = s.profile_read()
+    s.profile_enable(False)
     s.check_finite([u])
     finite_ok = s.sync_status() == fr.OK
-    launches = sum(v[0] for v in prof.values())
+    launches = sum(v[0] for v in prof.values())          # the same kernels the graph replays
 
     # roofline of the dominant kernel: the binding one of its HBM time and its
     # arithmetic time (tensor cores for the split-precision GEMMs, CUDA cores otherwise)
@@ -402,6 +479,8 @@ def main():
             r.update(bound="hbm", achieved=kb / avg / 1e9, peak=hbm_peak, unit="GB/s",
                      peak_source=f"{peak_src} hbm_gbs")
         r["frac"] = r["achieved"] / r["peak"]
+        r["timed"] = ("kernel-level pass of the same steps right after the headline (direct launches, CUDA "
+                      "events per kernel on the launch stream)")
         return r
 
     top = max(prof.items(), key=lambda kv: kv[1][1])
@@ -417,58 +496,98 @@ def main():
         b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz, tc_path)
         if b:
             d["GB_s"] = round(b / (d["ms"] / d["launches"] / 1e3) / 1e9, 1)
+            d["hbm_frac"] = round(d["GB_s"] / hbm_peak, 3)
         if f:
             d["TFLOP_s_algorithmic"] = round(f / (d["ms"] / d["launches"] / 1e3) / 1e12, 2)
         per_kernel[k] = d
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: every step copies the state
+    # in from pinned host memory, runs one RK4 step and copies it back (fr_rk4_host)
     e2e = None
     if not a.no_e2e:
         uh = u_init.cpu().pin_memory()
-        rh = torch.empty_like(uh).pin_memory()
-        s.rhs_host([uh], [rh], stream)
-        torch.cuda.synchronize()
+        s.rk4_host([uh], dt, 1, stream)                      # staging allocation and graph capture
+        ne = max(3, min(a.steps, 5))
         t0 = time.perf_counter()
-        ne = max(3, min(a.steps, 10))
         for _ in range(ne):
-            s.rhs_host([uh], [rh], stream)
+            s.rk4_host([uh], dt, 1, stream)
         te = (time.perf_counter() - t0) / ne
         nbytes = uh.numel() * uh.element_size()
-        e2e = dict(value=dof * world / te / 1e9, unit=UNIT, h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes,
-                   note="one RHS per call: H2D of U, RHS, D2H of R, host-synchronous")
-        del uh, rh
+        e2e = dict(value=dof * 4 * world / te / 1e9, unit=UNIT, h2d_bytes_per_step=nbytes,
+                   d2h_bytes_per_step=nbytes, ms_per_step=round(te * 1e3, 2),
+                   note="fr_rk4_host: per step H2D of U from pinned memory, one RK4 step (graph replay), D2H of "
+                        "U, host-synchronous; rated per RK stage like the headline")
+        del uh
 
-    # comparison legs on the same mesh and state: plain FP32 (CUDA-core operator
-    # products) and plain FP64, one RHS per step
-    def rhs_leg(prec, reps):
+    # reference result for the error statements below: the FP64 GPU RHS of the
+    # same (FP32-rounded) state; the FP64 path matches the oracle to 1e-13 of the
+    # terms' magnitude in the parity tests
+    r_main = torch.empty_like(u_init)
+    s.rhs([u_init], [r_main], stream)
+    s.close()
+    del u
+    torch.cuda.empty_cache()
+
+    def rel_l2_vs(r, ref):
+        x = r[:, :, :nelem].double()
+        num = ((x - ref) ** 2).sum(dim=(0, 2)).sqrt()
+        den = (ref ** 2).sum(dim=(0, 2)).sqrt()
+        return [float(v) for v in (num / den).cpu()]
+
+    # comparison legs on the same mesh and state, per RK stage like the headline
+    def rk_leg(prec, warm, reps, graphs=True):
         sl = fr.Solver(mesh, a.order, "ns", prec, device=local, **PRM, **REF)
+        sl.set_option("graphs", 1 if graphs else 0)
         dtp = torch.float64 if prec == "fp64" else torch.float32
         ul = u_init.to(dtp)
         rl = torch.empty_like(ul)
-        sl.rhs([ul], [rl], stream)
+        sl.rhs([ul], [rl], stream)                          # loads every kernel
+        if warm:
+            sl.rk4([ul], dt, warm, stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(reps):
-            sl.rhs([ul], [rl], stream)
+        sl.rk4([ul], dt, reps, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / reps
+        st_l = sl.sync_status()
         sl.close()
-        del ul, rl
-        torch.cuda.empty_cache()
+        del ul
         fl = operator_flops_per_rhs(nu, nf, V, D, nelem)
         pk, wf, pname = {"fp32": (fp32_peak, 1.0, "FP32 FMA (measured)"), "fp64": (fp64_peak, 1.0, "FP64 FMA (measured)"),
                          "bf16x3": (bf16_peak, 3.0, "BF16 tensor (measured cuBLAS)"),
                          "tf32x3": (bf16_peak * 1.1 / 2.25, 3.0, "TF32 tensor")}[prec]
-        whole = fl * wf / (t / 1e3) / 1e12
-        return dict(gdofs_per_rhs=dof / (t / 1e3) / 1e9, ms_per_rhs=t, precision=prec,
-                    operator_tflops_whole_rhs=round(whole, 2), alu_peak_tflops=round(pk, 2), alu_peak=pname,
-                    alu_frac_whole_rhs=round(whole / pk, 3),
-                    note="operator flops (x3 for split precision) over the whole RHS time, all kernels included")
+        whole = 4 * fl * wf / (t / 1e3) / 1e12
+        out = dict(gdofs_per_rk_stage=4 * dof / (t / 1e3) / 1e9, ms_per_rk4_step=t, precision=prec,
+                   graphs=graphs, operator_tflops_whole_step=round(whole, 2), alu_peak_tflops=round(pk, 2),
+                   alu_peak=pname, alu_frac_whole_step=round(whole / pk, 3),
+                   status="ok" if st_l == fr.OK else fr.STATUS_NAMES[st_l],
+                   note="operator flops (x3 for split precision) over the whole RK4 step time, all kernels included")
+        return out, rl
 
-    s.close()
-    del u
+    fp64, parity, r64 = None, None, None
+    if not a.no_fp64 and a.precision != "fp64":
+        # one RK4 step of the FP64 path takes seconds: direct launches, one step timed
+        fp64, r64 = rk_leg("fp64", 0, 1, graphs=False)
+        r64 = r64[:, :, :nelem].clone()
+        torch.cuda.empty_cache()
+        parity = dict(reference="FP64 GPU RHS of the same FP32-rounded state (full 96^3 box, every element)",
+                      variables=["rho", "rho u", "rho v", "rho w", "E"],
+                      rel_l2_per_var={a.precision: rel_l2_vs(r_main, r64)})
+    del r_main
+    fp32 = bf16 = None
+    if not a.no_fp32 and a.precision != "fp32":
+        fp32, r32 = rk_leg("fp32", 1, 2)
+        if parity is not None:
+            parity["rel_l2_per_var"]["fp32"] = rel_l2_vs(r32, r64)
+        del r32
+    if not a.no_bf16 and a.precision != "bf16x3":
+        bf16, rb = rk_leg("bf16x3", 1, 3)
+        if parity is not None:
+            parity["rel_l2_per_var"]["bf16x3"] = rel_l2_vs(rb, r64)
+        del rb
+    del r64
     torch.cuda.empty_cache()
     # mixed-mesh workload: 2D NS on the annulus (100k quads + 60k triangles, p = 4, Re 100, M 0.2)
     mixed = None
@@ -490,24 +609,14 @@ def main():
                 um.append(torch.from_numpy(sm.pack(b, Ub)).to(dtp).cuda())
                 mdof += Ub.size
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            if prec == "fp64":
-                rm = [torch.empty_like(x) for x in um]
-                sm.rhs(um, rm, stream)
-                e0.record(stream)
-                for _ in range(nrep):
-                    sm.rhs(um, rm, stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                mixed["fp64_gdofs_per_rhs"] = mdof * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
-            else:
-                # dt well inside the viscous limit of the wall ring (h ~ 0.006, p = 4, mu = 0.01)
-                sm.rk4(um, 2e-6, 3, stream)
-                e0.record(stream)
-                sm.rk4(um, 2e-6, nrep, stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                mixed[f"{prec}_gdofs_per_rk_stage"] = mdof * 4 * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
-                mixed["ms_per_rk4_step"] = e0.elapsed_time(e1) / nrep
+            # dt well inside the viscous limit of the wall ring (h ~ 0.006, p = 4, mu = 0.01)
+            sm.rk4(um, 2e-6, 1 if prec == "fp64" else 3, stream)
+            e0.record(stream)
+            sm.rk4(um, 2e-6, nrep, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mixed[f"{prec}_gdofs_per_rk_stage"] = mdof * 4 * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
+            mixed[f"{prec}_ms_per_rk4_step"] = e0.elapsed_time(e1) / nrep
             sm.check_finite(um)
             st_m = sm.sync_status()
             mixed[f"{prec}_status"] = "ok" if st_m == fr.OK else fr.STATUS_NAMES[st_m]
@@ -527,22 +636,12 @@ def main():
             ut = torch.from_numpy(st_.pack(0, Ut.transpose(1, 0, 2))).to(dtp).cuda()
             tdof = Ut.size
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            if prec == "fp64":
-                rt = [torch.empty_like(ut)]
-                st_.rhs([ut], rt, stream)
-                e0.record(stream)
-                for _ in range(nrep):
-                    st_.rhs([ut], rt, stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                tgv32["fp64_gdofs_per_rhs"] = tdof * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
-            else:
-                st_.rk4([ut], 2e-4, 3, stream)
-                e0.record(stream)
-                st_.rk4([ut], 2e-4, nrep, stream)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                tgv32[f"{prec}_gdofs_per_rk_stage"] = tdof * 4 * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
+            st_.rk4([ut], 2e-4, 1 if prec == "fp64" else 3, stream)
+            e0.record(stream)
+            st_.rk4([ut], 2e-4, nrep, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tgv32[f"{prec}_gdofs_per_rk_stage"] = tdof * 4 * nrep / (e0.elapsed_time(e1) / 1e3) / 1e9
             tgv32["dof"] = tdof
             st_.close()
             del ut, Ut
@@ -639,9 +738,6 @@ def main():
             sx.close()
             del ux, rx
             torch.cuda.empty_cache()
-    fp32 = rhs_leg("fp32", 3) if (not a.no_fp32 and a.precision != "fp32") else None
-    fp64 = rhs_leg("fp64", 2) if (not a.no_fp64 and a.precision != "fp64") else None
-    bf16 = rhs_leg("bf16x3", 3) if (not a.no_bf16 and a.precision != "bf16x3") else None
 
     if rank != 0:
         return 0
@@ -654,7 +750,8 @@ def main():
                     l2="inputs larger than L2 (state alone is %.1f GB)" % (u_init.numel() * u_init.element_size() / 1e9),
                     setup_s=round(t_setup, 1)),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
-        clocks=clk.summary(), per_kernel=per_kernel, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed, tgv32_p3=tgv32,
+        clocks=clk.summary(), per_kernel=per_kernel, kernel_pass_ms_per_step=ms_prof / a.steps,
+        parity=parity, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed, tgv32_p3=tgv32,
         adjoint_16cube_p4=adjoint, corrections_steppers_64cube=extra,
         alu_peaks=alu_peaks, finite=finite_ok,
     )

@@ -232,6 +232,26 @@ fr_status fr_dopri5(fr_ctx* ctx, void* const* u, double dt, int nsteps, double a
  */
 fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
 
+/*
+ * fr_rk_step -- the stepping call of the boundary under its generic name: the
+ * same classical RK4 steps (end of Sec. 2) as fr_rk4, with the same
+ * arguments, behaviour and errors.
+ */
+fr_status fr_rk_step(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
+
+/*
+ * fr_rk4_host -- as fr_rk4 (classical RK4, end of Sec. 2), but u holds HOST
+ * buffers (any host memory; pinned memory makes the copies asynchronous),
+ * one per block, laid out as the device state ([nupts][nvars][ld], double
+ * for FR_PREC_FP64 else float).  The library copies u to a device staging
+ * buffer it owns (allocated on the first host-buffer call, shared with
+ * fr_rhs_host), advances it nsteps steps as fr_rk4 does (the captured step is
+ * reused from call to call), copies it back into u and synchronises `stream`
+ * before returning.  Errors as fr_rk4, plus FR_ERR_CUDA / FR_ERR_OOM for the
+ * copies and the staging allocation.
+ */
+fr_status fr_rk4_host(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
+
 /* Context options (not in the paper): "graphs" (default 1) enables the RK4-step CUDA graph of
  * fr_rk4.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
@@ -400,7 +420,7 @@ fr_status fr_rhs_parts(fr_ctx* const* parts, int32_t nparts, void* const* const*
                        void* stream);
 
 /* ABI version (increments on any signature change); not in the paper. */
-int32_t fr_version(void);   /* 4 */
+int32_t fr_version(void);   /* 5 */
 
 #ifdef __cplusplus
 }

@@ -414,7 +414,7 @@ void ctx_set_error(fr_ctx* c, const char* msg) {
 // ====================================================================== ABI
 extern "C" {
 
-int32_t fr_version(void) { return 4; }
+int32_t fr_version(void) { return 5; }
 
 fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops) {
     if (!fp32_tflops || !fp64_tflops) return FR_ERR_ARG;
@@ -874,6 +874,43 @@ fr_status fr_rk4(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* strea
         e = fr::launch_rk4(ctx->dev, u, dt, nsteps, st);
     }
     if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+fr_status fr_rk_step(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream) {
+    return fr_rk4(ctx, u, dt, nsteps, stream);
+}
+
+fr_status fr_rk4_host(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if ((s = whole_mesh(ctx)) != FR_OK) return s;
+    if (!ptrs_ok(ctx, u) || nsteps < 0) return set_err(ctx, FR_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t rs = ctx->prm.precision == FR_PREC_FP64 ? sizeof(double) : sizeof(float);
+    std::vector<void*> dv(ctx->dev.blocks.size());
+    try {
+        for (size_t b = 0; b < ctx->dev.blocks.size(); ++b) {
+            fr::DevBlock& B = ctx->dev.blocks[b];
+            const size_t bytes = (size_t)B.nupts * B.nvars * B.ld * rs;
+            if (!B.stage) B.stage = dalloc(ctx, bytes);
+            dv[b] = B.stage;
+            CK(cudaMemcpyAsync(B.stage, u[b], bytes, cudaMemcpyHostToDevice, st));
+        }
+    } catch (const Fail& f) {
+        return set_err(ctx, f.st, f.msg);
+    }
+    // the staging pointers do not change between calls, so the captured RK4 step is reused
+    if ((s = fr_rk4(ctx, dv.data(), dt, nsteps, stream)) != FR_OK) return s;
+    try {
+        for (size_t b = 0; b < ctx->dev.blocks.size(); ++b) {
+            fr::DevBlock& B = ctx->dev.blocks[b];
+            CK(cudaMemcpyAsync(u[b], B.stage, (size_t)B.nupts * B.nvars * B.ld * rs, cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+    } catch (const Fail& f) {
+        return set_err(ctx, f.st, f.msg);
+    }
     return FR_OK;
 }
 

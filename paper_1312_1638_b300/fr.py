@@ -28,7 +28,8 @@ EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pai
            "fr_rhs_host", "fr_rk4", "fr_sum_weighted", "fr_sync_status", "fr_check_finite",
            "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read",
            "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint", "fr_set_option", "fr_fma_peak",
-           "fr_euler", "fr_dopri5", "fr_setup_part", "fr_part_slots", "fr_rhs_parts"]
+           "fr_euler", "fr_dopri5", "fr_setup_part", "fr_part_slots", "fr_rhs_parts", "fr_rk_step",
+           "fr_rk4_host"]
 
 
 class FRError(RuntimeError):
@@ -83,6 +84,8 @@ def load():
     lib.fr_rhs_host.argtypes = [vp, vpp, vpp, vp]
     lib.fr_rk4.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_rk4_noalloc.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
+    lib.fr_rk_step.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
+    lib.fr_rk4_host.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_adjoint_rhs.argtypes = [vp, vpp, vpp, vpp, vp]
     lib.fr_set_option.argtypes = [vp, C.c_char_p, C.c_int64]
     lib.fr_rk4_adjoint.argtypes = [vp, vpp, vpp, C.c_double, C.c_int, C.c_int, vp]
@@ -370,6 +373,14 @@ class Solver:
 
     def rk4(self, u, dt, nsteps, stream=None):
         self._check(self.lib.fr_rk4(self.ctx, _ptrs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+
+    def rk4_host(self, u, dt, nsteps, stream=None):
+        """nsteps RK4 steps on host buffers (numpy arrays or pinned torch CPU
+        tensors, layout of pack()); copies in and out inside the call."""
+        def hp(x):
+            return x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+        self._check(self.lib.fr_rk4_host(self.ctx, _ptrs([hp(x) for x in u]), C.c_double(dt), nsteps,
+                                         _stream_ptr(stream)))
 
     def euler(self, u, dt, nsteps, stream=None):
         """nsteps forward Euler steps in place."""

@@ -34,3 +34,31 @@ def rel_l2_per_var(x, ref):
     num = np.sqrt(((x - ref) ** 2).sum(axis=(0, 2)))
     den = np.sqrt((ref ** 2).sum(axis=(0, 2)))
     return float((num / np.maximum(den, 1e-300)).max())
+
+
+def kappa_per_var(S, R):
+    """Condition of each variable's RHS: ||S_v||_2 / ||R_v||_2 (arrays [npts, nvars, nelem])."""
+    num = np.sqrt((S ** 2).sum(axis=(0, 2)))
+    den = np.sqrt((R ** 2).sum(axis=(0, 2)))
+    return num / np.maximum(den, 1e-300)
+
+
+def rel_l2_vars(x, ref):
+    """||x_v - ref_v||_2 / ||ref_v||_2 for every variable v (arrays [npts, nvars, nelem])."""
+    num = np.sqrt(((x - ref) ** 2).sum(axis=(0, 2)))
+    den = np.sqrt((ref ** 2).sum(axis=(0, 2)))
+    return num / np.maximum(den, 1e-300)
+
+
+def record_parity(case, prec, **fields):
+    """Append one JSON line of measured errors to the file named by
+    FR_PARITY_LOG (nothing when it is unset)."""
+    import json
+    path = os.environ.get("FR_PARITY_LOG")
+    if not path:
+        return
+    rec = dict(case=case, precision=prec)
+    for k, v in fields.items():
+        rec[k] = [float(x) for x in v] if hasattr(v, "__len__") else float(v)
+    with open(path, "a") as fh:
+        fh.write(json.dumps(rec) + "\n")

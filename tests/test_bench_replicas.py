@@ -53,3 +53,12 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     a = types.SimpleNamespace(order=4, gpus=2, steps=1, warmup=1)
     assert bench.run_reference(a) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_processes_time_concurrent_copies():
+    """The CPU baseline's timing helper: independent spawned oracle processes
+    (one thread each) on a tiny sample, aggregated over the slowest one."""
+    val, t_rhs, used = bench.oracle_processes(2, 1, 2, 0, 1)
+    assert used == 2 and t_rhs > 0
+    dof = 2 ** 3 * 2 ** 3 * 5
+    assert val == pytest.approx(2 * dof / t_rhs / 1e9, rel=1e-9)

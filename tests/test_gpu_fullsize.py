@@ -25,7 +25,8 @@ import pytest
 
 from fr_inputs import periodic_box, fields
 from oracle.system import FRSystem
-from tests.libutil import ensure_built
+from tests.libutil import ensure_built, kappa_per_var, record_parity, rel_l2_vars
+from tests.test_gpu_parity import KAPPA_WELL, TOL_L2
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +75,12 @@ def test_full_size_tiled_periodic_box(prec, beta):
     ref, sc = R[:, :, small_of[pick]], S[:, :, small_of[pick]]
     err_c = float(np.max(np.abs(g - ref) / sc))
     assert err_c <= {"fp32": 2e-6, "tf32x3": 4e-6}[prec], err_c
+    # error per result over the compared elements, with each variable's conditioning
+    rel, kap = rel_l2_vars(g, ref), kappa_per_var(sc, ref)
+    record_parity(f"c5_hex96_p4_ns_tile6_beta{beta}", prec, rel_l2=rel, kappa=kap, componentwise=err_c,
+                  elements=len(pick))
+    ok = kap <= KAPPA_WELL
+    assert np.all(rel[ok] <= TOL_L2[prec]), (rel, kap)
     assert s.sync_status() == fr.OK
     # identical elements of the big box give bit-identical results
     a = r[:, :, 2 + 2 * n + 2 * n * n].cpu().numpy()

@@ -12,8 +12,8 @@ import pytest
 
 from fr_inputs import annulus_mixed, fields
 from oracle.system import FRSystem
-from tests.libutil import ensure_built
-from tests.test_gpu_parity import TOL_C
+from tests.libutil import ensure_built, kappa_per_var, record_parity, rel_l2_vars
+from tests.test_gpu_parity import KAPPA_WELL, TOL_C, TOL_L2
 
 pytestmark = pytest.mark.gpu
 
@@ -51,5 +51,10 @@ def test_full_size_mixed_annulus(case, prec):
         g = r[b][:, :, :U[b].shape[2]].double().cpu().numpy()
         err = float(np.max(np.abs(g - R[b]) / np.maximum(S[b], 1e-300)))
         assert err <= TOL_C[prec], (b, err)
+        rel, kap = rel_l2_vars(g, R[b]), kappa_per_var(S[b], R[b])
+        record_parity(f"c3_annulus_p4_ns_block{b}", prec, rel_l2=rel, kappa=kap, componentwise=err)
+        if prec != "fp64":
+            ok = kap <= KAPPA_WELL
+            assert np.all(rel[ok] <= TOL_L2[prec]), (b, rel, kap)
     assert s.sync_status() == fr.OK
     s.close()

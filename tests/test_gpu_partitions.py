@@ -1,13 +1,16 @@
 """Partitioned right-hand side (Sec. 3.6 int/mpi split) on one GPU: 2-4
 partitions exchanging flux-point values give the whole-mesh right-hand side
 bit for bit (every pair is evaluated with the same inputs in the same
-order of operations)."""
+order of operations), and match the FP64 oracle's whole-mesh right-hand side
+element by element within the componentwise bound of the parity tests."""
 
 import numpy as np
 import pytest
 
 from fr_inputs import periodic_box, annulus_mixed, fields
-from tests.libutil import ensure_built
+from oracle.system import FRSystem
+from tests.libutil import ensure_built, oracle_state
+from tests.test_gpu_parity import TOL_C, mean_ref
 from tests.test_part_host import _partition
 
 pytestmark = pytest.mark.gpu
@@ -82,3 +85,43 @@ def test_partitioned_rhs_is_bit_identical(torch, name, nparts, prec):
     with pytest.raises(fr.FRError) as e:                           # a partition alone has no whole RHS
         ps.ranks[0].rhs(up[0], rp[0])
     assert e.value.status == fr.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("name,nparts", [("hex_ns", 2), ("hex_ns", 4), ("quad_euler", 3), ("mixed_ns", 2),
+                                         ("mixed_ns", 3)])
+def test_partitioned_rhs_matches_oracle(torch, name, nparts, prec):
+    from paper_1312_1638_b300 import fr
+    m, p, system, prm, st = _case(name)
+    o = FRSystem(m, p, system, **prm)
+    U = oracle_state(o, st)
+    if prec != "fp64":
+        U = [u.astype(np.float32).astype(np.float64) for u in U]
+    R, S = o.rhs(U, scale=True)
+    part = _partition(m, nparts, seed=11 * nparts)
+    ps = fr.PartitionedSolver(m, part, nparts, p, system, prec, device=0, **prm, **mean_ref(U))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    up, rp = [], []
+    for k in range(nparts):
+        s = ps.ranks[k]
+        uk, rk = [], []
+        for b in range(len(m.blocks)):
+            loc = ps.local_elements(k, b)
+            x = torch.from_numpy(s.pack(b, U[b][:, :, loc])).to(dt).cuda()
+            uk.append(x)
+            rk.append(torch.full_like(x, float("nan")))
+        up.append(uk)
+        rp.append(rk)
+    ps.rhs(up, rp)
+    torch.cuda.synchronize()
+    for b in range(len(m.blocks)):
+        got = np.full_like(R[b], np.nan)
+        for k in range(nparts):
+            loc = ps.local_elements(k, b)
+            got[:, :, loc] = rp[k][b][:, :, :len(loc)].double().cpu().numpy()
+        assert np.isfinite(got).all()
+        err = float(np.max(np.abs(got - R[b]) / np.maximum(S[b], 1e-300)))
+        assert err <= TOL_C[prec], (b, err)
+    for s in ps.ranks:
+        assert s.sync_status() == fr.OK
+    ps.close()

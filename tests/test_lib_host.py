@@ -27,7 +27,7 @@ def test_library_exports_every_declared_symbol(fr):
     for n in names:
         assert hasattr(lib, n), n
     assert set(names) == set(fr.EXPORTS)
-    assert fr.load().fr_version() == 4
+    assert fr.load().fr_version() == 5
 
 
 CASES = [("quad", 3, 1, 0.1), ("quad", 3, 4, 0.1), ("hex", 2, 2, 0.1), ("hex", 2, 4, 0.0)]
