@@ -62,3 +62,26 @@ def record_parity(case, prec, **fields):
         rec[k] = [float(x) for x in v] if hasattr(v, "__len__") else float(v)
     with open(path, "a") as fh:
         fh.write(json.dumps(rec) + "\n")
+
+
+def m0_spread(osys, U, samples=2, ulps=8, seed=7):
+    """Per block, per variable: the largest change of the oracle's RHS when the
+    entries of every element type's interpolation operator M0 are perturbed by
+    up to `ulps` units in the last place (seeded samples).  FP64 results of two
+    exact-equivalent constructions of M0 differ at that level, and the RHS
+    amplifies it (Sec. 2 operators evaluated in FP64); computed from the
+    oracle alone."""
+    R0 = osys.rhs(U)
+    saved = [el.M0.copy() for el in osys.eles]
+    rng = np.random.default_rng(seed)
+    spread = [np.zeros(r.shape[1]) for r in R0]
+    try:
+        for _ in range(samples):
+            for el, M0 in zip(osys.eles, saved):
+                el.M0 = M0 * (1 + ulps * np.finfo(float).eps * rng.uniform(-1, 1, M0.shape))
+            for b, r in enumerate(osys.rhs(U)):
+                spread[b] = np.maximum(spread[b], np.abs(r - R0[b]).max(axis=(0, 2)))
+    finally:
+        for el, M0 in zip(osys.eles, saved):
+            el.M0 = M0
+    return spread

@@ -178,3 +178,34 @@ def test_ns_rk4_adjoint_against_fp64_finite_differences(torch):
     from tests.adjoint_fd_study import fd_check
     r = fd_check(4, 64, "fp32", system="ns")
     assert not r["bad"], r["bad"][:5]
+
+
+@pytest.mark.parametrize("system", ["euler", "ns"])
+def test_autograd_gradcheck_mixed_mesh_blocks(torch, system):
+    """FRStepBlocks on a two-block mesh (quadrilaterals with a curved wall ring
+    and triangles, wall and free-stream boundaries): torch's gradcheck of the
+    tuple of block states against central differences of fr_rk4."""
+    from fr_inputs import annulus_mixed
+    from paper_1312_1638_b300 import fr
+    from paper_1312_1638_b300.autograd import rk4
+    m = annulus_mixed(ntheta=6, nr_quad=1, nr_tri=1, r0=0.5, r1=2.0, jitter=0.05, seed=5)
+    prm = dict(gamma=1.4, bc_rho=1.0, bc_v=(0.5, 0.1, 0.0), bc_p=2.0, outflow_p=2.0, wall_cpTw=3.5)
+    if system == "ns":
+        prm.update(NS_PRM)
+    s = fr.Solver(m, 1, system, "fp64", device=0, **prm)
+    xs, lays = [], []
+    for b in range(s.nblocks):
+        X = s.solution_points(b)
+        U = fields.smooth_random(X, seed=3 + b, amp=0.05, vel0=(0.5, 0.1), p0=2.0).transpose(1, 0, 2)
+        xs.append(torch.from_numpy(U.copy()).cuda().requires_grad_(True))
+        lays.append(s.layout(b))
+
+    def f(*x):
+        u = []
+        for b, (xb, lay) in enumerate(zip(x, lays)):
+            ub = torch.zeros((lay["nupts"], lay["nvars"], lay["ld"]), dtype=torch.float64, device="cuda")
+            u.append(ub.index_copy(2, torch.arange(lay["nelem"], device="cuda"), xb))
+        out = rk4(s, u, 1e-3, 2, 1)
+        return tuple(o[:, :, :lay["nelem"]] for o, lay in zip(out, lays))
+    assert torch.autograd.gradcheck(f, tuple(xs), eps=1e-6, atol=1e-7, rtol=1e-6)
+    assert s.sync_status() == fr.OK
