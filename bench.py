@@ -250,12 +250,15 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline bookkeeping
-def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False):
+def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False, one_side=False):
     """Algorithmic (bytes, flops) of one launch of each kernel on the whole block.
 
     Bytes count every value the kernel must read or write once (state, metric
     terms, per-pair tables); flops count the dense operator products as the
-    paper defines them (App. A)."""
+    paper defines them (App. A).  one_side: LDG beta = +-1/2, where one side of
+    each pair has weight zero in the common solution and in the viscous common
+    flux, so that side's U^(f) (common solution) or Q^(f) (common flux) is not
+    read."""
     E = nelem
     if name == "disu_gemm":
         return (nu + nf) * V * s * E, 2.0 * nf * nu * V * E
@@ -277,9 +280,9 @@ def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False):
     if name == "tdisf":
         return (nu * V + 2 * D * nu * V + D * D * nu) * s * E, 0.0
     if name == "comm_sol":
-        return npairs * (4 * V * s + 8), 0.0
+        return npairs * ((3 if one_side else 4) * V * s + 8), 0.0
     if name == "comm_flux":
-        return npairs * ((4 * V + 2 * D * V + D + 2) * s + 8), 0.0
+        return npairs * ((4 * V + (1 if one_side else 2) * D * V + D + 2) * s + 8), 0.0
     if name == "rk_stage":
         return 17 * nu * V * s * E / 4, 0.0       # stages read/write 4, 5, 5, 3 values per entry
     return None, None
@@ -462,8 +465,10 @@ def main():
         "fp64": (fp64_peak, 1.0, "FP64", alu_src),
     }[a.precision]
 
+    one_side = PRM["ldg_beta"] in (0.5, -0.5)
+
     def roof_of(name, launches, tms):
-        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz, tc_path)
+        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz, tc_path, one_side)
         avg = tms / launches / 1e3
         t_hbm = kb / (hbm_peak * 1e9) if kb else 0.0
         t_alu = (kf * arith[1]) / (arith[0] * 1e12) if kf else 0.0
@@ -493,7 +498,7 @@ def main():
         if not v[0]:
             continue
         d = dict(launches=v[0], ms=round(v[1], 3), share=round(v[1] / max(total_ms, 1e-9), 4))
-        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz, tc_path)
+        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz, tc_path, one_side)
         if b:
             d["GB_s"] = round(b / (d["ms"] / d["launches"] / 1e3) / 1e9, 1)
             d["hbm_frac"] = round(d["GB_s"] / hbm_peak, 3)

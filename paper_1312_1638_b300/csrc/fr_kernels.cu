@@ -398,8 +398,10 @@ __global__ void tflux_kernel(int nupts, int64_t nelem, int64_t ld, const T* __re
 
 // ============================================================ interfaces (PI)
 // LDG common solution (Eq. commsoln, Sec. 4.3): each pair visited once,
-// the same value written to both sides.
-template <typename T, int D>
+// the same value written to both sides.  SIDE = 1 (beta = +1/2): C = u_R,
+// SIDE = 2 (beta = -1/2): C = u_L, so the side with weight zero is not read;
+// SIDE = 0: any beta.
+template <typename T, int D, int SIDE = 0>
 __global__ void comm_sol_kernel(int64_t npairs, const uint32_t* __restrict__ offL, const uint32_t* __restrict__ offR,
                                 const T* __restrict__ UfL, const T* __restrict__ UfR, int64_t ldL, int64_t ldR,
                                 T* __restrict__ CL, T* __restrict__ CR, T beta) {
@@ -410,11 +412,17 @@ __global__ void comm_sol_kernel(int64_t npairs, const uint32_t* __restrict__ off
     T wl = T(0.5) - beta, wr = T(0.5) + beta;
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-        T c = wl * UfL[oL + a * ldL] + wr * UfR[oR + a * ldR];
+        T c;
+        if constexpr (SIDE == 1) c = UfR[oR + a * ldR];
+        else if constexpr (SIDE == 2) c = UfL[oL + a * ldL];
+        else c = wl * UfL[oL + a * ldL] + wr * UfR[oR + a * ldR];
         CL[oL + a * ldL] = c;
         CR[oR + a * ldR] = c;
     }
 }
+
+// beta = +-1/2 makes one LDG weight zero (the alternating fluxes of Sec. 4.3)
+static inline int ldg_side(double beta) { return beta == 0.5 ? 1 : beta == -0.5 ? 2 : 0; }
 
 template <typename T, int D>
 __global__ void comm_sol_bc_kernel(int64_t nb, int bctype, const uint32_t* __restrict__ off, const T* __restrict__ Uf,
@@ -434,8 +442,10 @@ __global__ void comm_sol_bc_kernel(int64_t nb, int bctype, const uint32_t* __res
 
 // Common normal flux (Eq. commpflux): Rusanov (App. B) minus the LDG viscous
 // flux with a dissipative tau penalty (Sec. 4.3), scaled by J^(f) n^(f) and
-// written with opposite signs to both sides, in place over U^(f).
-template <typename T, int D, bool NS>
+// written with opposite signs to both sides, in place over U^(f).  SIDE = 1
+// (beta = +1/2) / 2 (beta = -1/2): the viscous flux of the side whose weight
+// is zero is neither read nor evaluated (SIDE = 0: any beta).
+template <typename T, int D, bool NS, int SIDE = 0>
 __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ offL, const uint32_t* __restrict__ offR,
                                  T* UfL, T* UfR, const T* __restrict__ QfL, const T* __restrict__ QfR,
                                  int64_t ldL, int64_t ldR, int64_t qsL, int64_t qsR, const T* __restrict__ nrm,
@@ -461,7 +471,9 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
         T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
         T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
         T fvn[NV];
-        {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) fvn[a] = T(0);
+        if constexpr (SIDE != 2) {
             T q[D][NV], fv[D][NV];
 #pragma unroll
             for (int j = 0; j < D; ++j)
@@ -476,7 +488,7 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
                 fvn[a] = wl * acc;
             }
         }
-        {
+        if constexpr (SIDE != 1) {
             T q[D][NV], fv[D][NV];
 #pragma unroll
             for (int j = 0; j < D; ++j)
@@ -506,7 +518,7 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
     }
 }
 
-template <typename T, int D, bool NS>
+template <typename T, int D, bool NS, int SIDE = 0>
 __global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __restrict__ off, T* Uf,
                                     const T* __restrict__ Qf, int64_t ld, int64_t qs, const T* __restrict__ nrm,
                                     const T* __restrict__ mag, DevParams P) {
@@ -534,8 +546,9 @@ __global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __re
                 qg[j][a] = grad_is_qL ? qL[j][a] : T(0);
             }
         T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
-        Gas<T, D>::vis_flux(uL, qL, rf, gm1, mu, kappa, fvL);
-        Gas<T, D>::vis_flux(gl, qg, rf, gm1, mu, kappa, fvR);
+        // a side with LDG weight zero (SIDE 1: the ghost, SIDE 2: the interior) is not evaluated
+        if constexpr (SIDE != 2) Gas<T, D>::vis_flux(uL, qL, rf, gm1, mu, kappa, fvL);
+        if constexpr (SIDE != 1) Gas<T, D>::vis_flux(gl, qg, rf, gm1, mu, kappa, fvR);
         T beta = T(P.beta), tau = T(P.tau), wl = T(0.5) + beta, wr = T(0.5) - beta;
         T du[NV], fvn[NV];
         Gas<T, D>::jump(uL, gl, rf, du);
@@ -543,7 +556,11 @@ __global__ void comm_flux_bc_kernel(int64_t nb, int bctype, const uint32_t* __re
         for (int a = 0; a < NV; ++a) {
             T fv = T(0);
 #pragma unroll
-            for (int i = 0; i < D; ++i) fv += n[i] * (wl * fvL[i][a] + wr * fvR[i][a]);
+            for (int i = 0; i < D; ++i) {
+                if constexpr (SIDE == 1) fv += n[i] * (wl * fvL[i][a]);
+                else if constexpr (SIDE == 2) fv += n[i] * (wr * fvR[i][a]);
+                else fv += n[i] * (wl * fvL[i][a] + wr * fvR[i][a]);
+            }
             fvn[a] = fv;
         }
         fvn[NV - 1] += rf.h * fvn[0];
@@ -693,6 +710,32 @@ __global__ void pack_kernel(int64_t n, int nvars, int ncomp, const uint32_t* __r
         for (int a = 0; a < nvars; ++a) buf[(int64_t)(j * nvars + a) * nslots + sl] = src[j * qs + o + a * ld];
 }
 
+template <typename T, int D>
+static void launch_comm_sol(int side, int64_t n, const uint32_t* oL, const uint32_t* oR, const T* UL, const T* UR,
+                            int64_t ldL, int64_t ldR, T* CL, T* CR, T beta, cudaStream_t st) {
+    if (side == 1)
+        comm_sol_kernel<T, D, 1><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, ldL, ldR, CL, CR, beta);
+    else if (side == 2)
+        comm_sol_kernel<T, D, 2><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, ldL, ldR, CL, CR, beta);
+    else
+        comm_sol_kernel<T, D, 0><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, ldL, ldR, CL, CR, beta);
+}
+
+template <typename T, int D>
+static void launch_comm_flux_ns(int side, int64_t n, const uint32_t* oL, const uint32_t* oR, T* UL, T* UR,
+                                const T* QL, const T* QR, int64_t ldL, int64_t ldR, int64_t qsL, int64_t qsR,
+                                const T* nrm, const T* mL, const T* mR, const DevParams& P, cudaStream_t st) {
+    if (side == 1)
+        comm_flux_kernel<T, D, true, 1><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
+                                                                          qsR, nrm, mL, mR, P);
+    else if (side == 2)
+        comm_flux_kernel<T, D, true, 2><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
+                                                                          qsR, nrm, mL, mR, P);
+    else
+        comm_flux_kernel<T, D, true, 0><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
+                                                                          qsR, nrm, mL, mR, P);
+}
+
 // RK stage to fuse into the divergence GEMM's epilogue (tensor-core paths):
 // the stage's k is not stored; see tc::RkFuse
 struct RkStage {
@@ -706,6 +749,7 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
                             const RkStage* rk = nullptr) {
     constexpr int NV = D + 2;
     const bool ns = c.system == 1;
+    const int side = ldg_side(c.prm.beta);
     Sub<T> sub{};
     sub.v[0] = T(c.prm.ref_rho);
     sub.v[NV - 1] = T(c.prm.ref_E);
@@ -732,8 +776,8 @@ phase_b1:
             DevBlock &L = c.blocks[g.bL], &R = c.blocks[g.bR];
             if (!g.n) continue;
             prof_begin(c, K_COMM_SOL, st);
-            comm_sol_kernel<T, D><<<lin_grid(g.n, 128), 128, 0, st>>>(
-                g.n, g.offL, g.offR, (const T*)L.Uf, (const T*)R.Uf, L.ld, R.ld, (T*)L.Qf, (T*)R.Qf, T(c.prm.beta));
+            launch_comm_sol<T, D>(side, g.n, g.offL, g.offR, (const T*)L.Uf, (const T*)R.Uf, L.ld, R.ld, (T*)L.Qf,
+                                  (T*)R.Qf, T(c.prm.beta), st);
             prof_end(c, st);
         }
         for (auto& g : c.bgroups) {
@@ -754,13 +798,11 @@ phase_b1:
             DevNeighbour& q = c.nbrs[g.nb];
             prof_begin(c, K_COMM_SOL, st);
             if (g.mine_L)
-                comm_sol_kernel<T, D><<<lin_grid(g.n, 128), 128, 0, st>>>(
-                    g.n, g.off, g.slot, (const T*)B.Uf, (const T*)q.recv_u, B.ld, q.nslots, (T*)B.Qf, (T*)q.recv_q,
-                    T(c.prm.beta));
+                launch_comm_sol<T, D>(side, g.n, g.off, g.slot, (const T*)B.Uf, (const T*)q.recv_u, B.ld, q.nslots,
+                                      (T*)B.Qf, (T*)q.recv_q, T(c.prm.beta), st);
             else
-                comm_sol_kernel<T, D><<<lin_grid(g.n, 128), 128, 0, st>>>(
-                    g.n, g.slot, g.off, (const T*)q.recv_u, (const T*)B.Uf, q.nslots, B.ld, (T*)q.recv_q, (T*)B.Qf,
-                    T(c.prm.beta));
+                launch_comm_sol<T, D>(side, g.n, g.slot, g.off, (const T*)q.recv_u, (const T*)B.Uf, q.nslots, B.ld,
+                                      (T*)q.recv_q, (T*)B.Qf, T(c.prm.beta), st);
             prof_end(c, st);
         }
         for (size_t b = 0; b < c.blocks.size(); ++b) {
@@ -822,9 +864,9 @@ phase_b1:
         int64_t qsL = (int64_t)L.nfpts * NV * L.ld, qsR = (int64_t)R.nfpts * NV * R.ld;
         prof_begin(c, K_COMM_FLUX, st);
         if (ns)
-            comm_flux_kernel<T, D, true><<<lin_grid(g.n, 128), 128, 0, st>>>(
-                g.n, g.offL, g.offR, (T*)L.Uf, (T*)R.Uf, (const T*)L.Qf, (const T*)R.Qf, L.ld, R.ld, qsL, qsR,
-                (const T*)g.nrm, (const T*)g.magL, (const T*)g.magR, c.prm);
+            launch_comm_flux_ns<T, D>(side, g.n, g.offL, g.offR, (T*)L.Uf, (T*)R.Uf, (const T*)L.Qf, (const T*)R.Qf,
+                                      L.ld, R.ld, qsL, qsR, (const T*)g.nrm, (const T*)g.magL, (const T*)g.magR,
+                                      c.prm, st);
         else
             comm_flux_kernel<T, D, false><<<lin_grid(g.n, 128), 128, 0, st>>>(
                 g.n, g.offL, g.offR, (T*)L.Uf, (T*)R.Uf, nullptr, nullptr, L.ld, R.ld, qsL, qsR,
@@ -836,9 +878,17 @@ phase_b1:
         DevBlock& B = c.blocks[g.b];
         int64_t qs = (int64_t)B.nfpts * NV * B.ld;
         prof_begin(c, K_COMM_FLUX_BC, st);
-        if (ns)
-            comm_flux_bc_kernel<T, D, true><<<lin_grid(g.n, 128), 128, 0, st>>>(
-                g.n, g.bctype, g.off, (T*)B.Uf, (const T*)B.Qf, B.ld, qs, (const T*)g.nrm, (const T*)g.mag, c.prm);
+        if (ns) {
+            if (side == 1)
+                comm_flux_bc_kernel<T, D, true, 1><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                    g.n, g.bctype, g.off, (T*)B.Uf, (const T*)B.Qf, B.ld, qs, (const T*)g.nrm, (const T*)g.mag, c.prm);
+            else if (side == 2)
+                comm_flux_bc_kernel<T, D, true, 2><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                    g.n, g.bctype, g.off, (T*)B.Uf, (const T*)B.Qf, B.ld, qs, (const T*)g.nrm, (const T*)g.mag, c.prm);
+            else
+                comm_flux_bc_kernel<T, D, true><<<lin_grid(g.n, 128), 128, 0, st>>>(
+                    g.n, g.bctype, g.off, (T*)B.Uf, (const T*)B.Qf, B.ld, qs, (const T*)g.nrm, (const T*)g.mag, c.prm);
+        }
         else
             comm_flux_bc_kernel<T, D, false><<<lin_grid(g.n, 128), 128, 0, st>>>(
                 g.n, g.bctype, g.off, (T*)B.Uf, nullptr, B.ld, qs, (const T*)g.nrm, (const T*)g.mag, c.prm);
@@ -862,9 +912,8 @@ phase_c2:
         const int64_t qsL = g.mine_L ? qsB : qsQ, qsR = g.mine_L ? qsQ : qsB;
         prof_begin(c, K_COMM_FLUX, st);
         if (ns)
-            comm_flux_kernel<T, D, true><<<lin_grid(g.n, 128), 128, 0, st>>>(
-                g.n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL, qsR, (const T*)g.nrm, (const T*)g.magL, (const T*)g.magR,
-                c.prm);
+            launch_comm_flux_ns<T, D>(side, g.n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL, qsR, (const T*)g.nrm,
+                                      (const T*)g.magL, (const T*)g.magR, c.prm, st);
         else
             comm_flux_kernel<T, D, false><<<lin_grid(g.n, 128), 128, 0, st>>>(
                 g.n, oL, oR, UL, UR, nullptr, nullptr, ldL, ldR, qsL, qsR, (const T*)g.nrm, (const T*)g.magL,

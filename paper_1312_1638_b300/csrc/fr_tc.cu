@@ -786,8 +786,10 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
         a.rk_tmp = rk->tmp;
         a.rk_nelem = rk->nelem;
     }
-    // the variables of one element range share the metric terms through L2
+    // the variables of one element range share the metric terms (adj(J), 1/J)
+    // through L2: their column tiles run on neighbouring CTAs at the same time
     a.vinter = (gx && gx->nvars > 1 && ld % (nt * BN) == 0 && N == (int64_t)gx->nvars * ld) ? gx->nvars : 0;
+    if (!gx && rcp && (epi == 1 || rk) && ld % (nt * BN) == 0 && N % ld == 0 && N / ld > 1) a.vinter = (int)(N / ld);
     CUtensorMap m1, m2;
     if (!make_map(&m1, B1, N, K1, kce, nt)) return cudaErrorInvalidValue;
     if (K2 > 0) {

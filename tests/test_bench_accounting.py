@@ -50,6 +50,10 @@ def test_interface_kernel_work_per_pair():
     assert bench.kernel_work("comm_sol", NU, NF, V, D, 0, 1, S)[0] == 4 * 5 * 4 + 8
     # + both sides' Q^(f), the normal (3) and J^(f) n^(f) of both sides
     assert bench.kernel_work("comm_flux", NU, NF, V, D, 0, 1, S)[0] == (4 * 5 + 2 * 3 * 5 + 3 + 2) * 4 + 8
+    # LDG beta = +-1/2: the zero-weight side's U^(f) (common solution) and Q^(f)
+    # (viscous common flux) are not read
+    assert bench.kernel_work("comm_sol", NU, NF, V, D, 0, 1, S, one_side=True)[0] == 3 * 5 * 4 + 8
+    assert bench.kernel_work("comm_flux", NU, NF, V, D, 0, 1, S, one_side=True)[0] == (4 * 5 + 3 * 5 + 3 + 2) * 4 + 8
 
 
 def test_dominant_kernel_bytes_at_full_size():
