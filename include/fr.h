@@ -252,6 +252,31 @@ fr_status fr_rk_step(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* s
  */
 fr_status fr_rk4_host(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* stream);
 
+/*
+ * Kernel-variant autotuning (not in the paper; the paper's Sec. 3.4 leaves
+ * the operator products to cuBLAS, which chooses its own kernels).  On the
+ * tensor-core paths every operator product (disu: M0 U; tgradu: the corrected
+ * gradient with its transform; gradfpts: M0 Q; tdivf: the corrected
+ * divergence, with the RK stage on the RK4 path) can run as one of several
+ * kernel variants, which differ in how many 128-column subtiles a work item
+ * holds (nt) and how many warps convert the state operand (cw) or drain the
+ * accumulators (eg).  fr_autotune times every variant that fits each product
+ * of each block: 1 + reps RK4 steps of size 0 on a private copy of u (device
+ * memory allocated and freed by the call; u is not modified), kernels timed
+ * by CUDA events, and keeps the fastest in the context.  It synchronises
+ * `stream`.  On the FP64 / FP32 paths it does nothing.
+ * fr_get_tuning writes the context's choices as text,
+ * "b0:disu=1.8.3,tgradu=1.4.4,gradfpts=1.8.3,tdivf=2.8.2;b1:..." (nt.cw.eg,
+ * or "default" for the built-in rule), NUL-terminated into buf (FR_ERR_ARG if
+ * size is too small); fr_set_tuning applies such text (any subset of blocks
+ * and products; FR_ERR_ARG, with nothing applied, for a malformed entry or a
+ * variant that does not fit the product).  Changing the choices drops the
+ * captured RK4 step.
+ */
+fr_status fr_autotune(fr_ctx* ctx, void* const* u, int reps, void* stream);
+fr_status fr_get_tuning(const fr_ctx* ctx, char* buf, int64_t size);
+fr_status fr_set_tuning(fr_ctx* ctx, const char* text);
+
 /* Context options (not in the paper): "graphs" (default 1) enables the RK4-step CUDA graph of
  * fr_rk4.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
@@ -420,7 +445,7 @@ fr_status fr_rhs_parts(fr_ctx* const* parts, int32_t nparts, void* const* const*
                        void* stream);
 
 /* ABI version (increments on any signature change); not in the paper. */
-int32_t fr_version(void);   /* 5 */
+int32_t fr_version(void);   /* 6 */
 
 #ifdef __cplusplus
 }

@@ -414,7 +414,7 @@ void ctx_set_error(fr_ctx* c, const char* msg) {
 // ====================================================================== ABI
 extern "C" {
 
-int32_t fr_version(void) { return 5; }
+int32_t fr_version(void) { return 6; }
 
 fr_status fr_fma_peak(int cuda_device, double* fp32_tflops, double* fp64_tflops) {
     if (!fp32_tflops || !fp64_tflops) return FR_ERR_ARG;
@@ -911,6 +911,165 @@ fr_status fr_rk4_host(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* 
     } catch (const Fail& f) {
         return set_err(ctx, f.st, f.msg);
     }
+    return FR_OK;
+}
+
+static const char* const kTuneNames[fr::TUNE_N] = {"disu", "tgradu", "gradfpts", "tdivf"};
+
+static void drop_graph(fr_ctx* ctx) {
+    if (ctx->rk_exec) {                        // a captured RK4 step holds the old kernel choices
+        cudaGraphExecDestroy(ctx->rk_exec);
+        ctx->rk_exec = nullptr;
+    }
+}
+
+fr_status fr_autotune(fr_ctx* ctx, void* const* u, int reps, void* stream) {
+    fr_status s = check_dev(ctx);
+    if (s != FR_OK) return s;
+    if ((s = whole_mesh(ctx)) != FR_OK) return s;
+    if (!ptrs_ok(ctx, u) || reps < 1) return set_err(ctx, FR_ERR_ARG, "bad argument");
+    fr::DevCtx& D = ctx->dev;
+    if (D.precision < 2) return FR_OK;                       // CUDA-core paths: nothing to choose
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t rs = sizeof(float);
+    std::vector<void*> tmp(D.blocks.size(), nullptr);
+    const bool prof = D.prof;
+    cudaError_t e = cudaSuccess;
+    try {
+        for (size_t b = 0; b < D.blocks.size(); ++b) {
+            fr::DevBlock& B = D.blocks[b];
+            const size_t bytes = (size_t)B.nupts * B.nvars * B.ld * rs;
+            if (!B.rk_acc) B.rk_acc = dalloc(ctx, bytes);
+            if (!B.rk_tmp) B.rk_tmp = dalloc(ctx, bytes);
+            CK(cudaMalloc(&tmp[b], bytes));
+            CK(cudaMemcpyAsync(tmp[b], u[b], bytes, cudaMemcpyDeviceToDevice, st));
+        }
+        {
+            int64_t l0[fr::K_NKERNELS];
+            double t0[fr::K_NKERNELS];
+            CK(fr::prof_drain(D, l0, t0));             // records of earlier calls are not this tuning's
+        }
+        D.prof = true;
+        // one product and one block at a time: every candidate runs 1 + reps RK4
+        // steps of size 0 on the copy (the state does not change), timed per kernel
+        // by the profiler; the other blocks' choices stay fixed, so the difference
+        // between candidates is this block's
+        const int kid[fr::TUNE_N] = {fr::K_DISU, fr::K_TGRADU, fr::K_GRADFPTS, fr::K_TDIVF};
+        for (int slot = 0; slot < fr::TUNE_N; ++slot)
+            for (size_t b = 0; b < D.blocks.size(); ++b) {
+                fr::DevBlock& B = D.blocks[b];
+                int cand[8];
+                const int nc = fr::tune_candidates(D, B, slot, cand);
+                if (nc < 2) continue;
+                double best_t = 1e300;
+                int best = B.tune[slot];
+                for (int i = 0; i < nc; ++i) {
+                    B.tune[slot] = cand[i];
+                    CK(fr::launch_rk4(D, tmp.data(), 0.0, 1, st));
+                    int64_t l[fr::K_NKERNELS];
+                    double t[fr::K_NKERNELS];
+                    CK(fr::prof_drain(D, l, t));
+                    CK(fr::launch_rk4(D, tmp.data(), 0.0, reps, st));
+                    CK(fr::prof_drain(D, l, t));
+                    if (t[kid[slot]] < best_t) {
+                        best_t = t[kid[slot]];
+                        best = cand[i];
+                    }
+                }
+                B.tune[slot] = best;
+            }
+    } catch (const Fail& f) {
+        D.prof = prof;
+        for (void* p : tmp)
+            if (p) cudaFree(p);
+        drop_graph(ctx);
+        return set_err(ctx, f.st, f.msg);
+    }
+    D.prof = prof;
+    e = cudaStreamSynchronize(st);
+    for (void* p : tmp) cudaFree(p);
+    drop_graph(ctx);
+    if (e != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    return FR_OK;
+}
+
+fr_status fr_get_tuning(const fr_ctx* ctx, char* buf, int64_t size) {
+    if (!ctx || !buf || size < 1) return FR_ERR_ARG;
+    std::string out;
+    for (size_t b = 0; b < ctx->dev.blocks.size(); ++b) {
+        const fr::DevBlock& B = ctx->dev.blocks[b];
+        if (b) out += ";";
+        out += "b" + std::to_string(b) + ":";
+        for (int slot = 0; slot < fr::TUNE_N; ++slot) {
+            if (slot) out += ",";
+            out += kTuneNames[slot];
+            out += "=";
+            if (B.tune[slot] < 0) {
+                out += "default";
+            } else {
+                const fr::tc::Variant V = fr::tc::variant_of(slot == fr::TUNE_TGRADU ? ctx->ndims : 0, B.tune[slot]);
+                out += std::to_string(V.nt) + "." + std::to_string(V.cw) + "." + std::to_string(V.eg);
+            }
+        }
+    }
+    if ((int64_t)out.size() + 1 > size) return FR_ERR_ARG;
+    std::memcpy(buf, out.c_str(), out.size() + 1);
+    return FR_OK;
+}
+
+fr_status fr_set_tuning(fr_ctx* ctx, const char* text) {
+    if (!ctx || !text) return FR_ERR_ARG;
+    if (ctx->dev.device < 0) return set_err(ctx, FR_ERR_UNSUPPORTED, "host-only context has no device state");
+    // parse fully before applying anything
+    std::vector<std::array<int, fr::TUNE_N>> want(ctx->dev.blocks.size());
+    for (size_t b = 0; b < want.size(); ++b) want[b] = {ctx->dev.blocks[b].tune[0], ctx->dev.blocks[b].tune[1],
+                                                        ctx->dev.blocks[b].tune[2], ctx->dev.blocks[b].tune[3]};
+    std::string t(text);
+    size_t pos = 0;
+    while (pos < t.size()) {
+        size_t end = t.find(';', pos);
+        if (end == std::string::npos) end = t.size();
+        const std::string part = t.substr(pos, end - pos);
+        pos = end + 1;
+        if (part.empty()) continue;
+        const size_t colon = part.find(':');
+        if (part[0] != 'b' || colon == std::string::npos) return set_err(ctx, FR_ERR_ARG, "tuning: expected b<k>:...");
+        const int b = std::atoi(part.substr(1, colon - 1).c_str());
+        if (b < 0 || b >= (int)want.size()) return set_err(ctx, FR_ERR_ARG, "tuning: block index out of range");
+        size_t q = colon + 1;
+        while (q < part.size()) {
+            size_t e2 = part.find(',', q);
+            if (e2 == std::string::npos) e2 = part.size();
+            const std::string kv = part.substr(q, e2 - q);
+            q = e2 + 1;
+            const size_t eq = kv.find('=');
+            if (eq == std::string::npos) return set_err(ctx, FR_ERR_ARG, "tuning: expected name=value");
+            int slot = -1;
+            for (int k = 0; k < fr::TUNE_N; ++k)
+                if (kv.substr(0, eq) == kTuneNames[k]) slot = k;
+            if (slot < 0) return set_err(ctx, FR_ERR_ARG, "tuning: unknown product " + kv.substr(0, eq));
+            const std::string val = kv.substr(eq + 1);
+            if (val == "default") {
+                want[b][slot] = -1;
+                continue;
+            }
+            int nt = 0, cw = 0, eg = 0;
+            if (std::sscanf(val.c_str(), "%d.%d.%d", &nt, &cw, &eg) != 3)
+                return set_err(ctx, FR_ERR_ARG, "tuning: expected nt.cw.eg, got " + val);
+            int cand[8];
+            const int nc = fr::tune_candidates(ctx->dev, ctx->dev.blocks[b], slot, cand);
+            int found = -1;
+            for (int i = 0; i < nc; ++i) {
+                const fr::tc::Variant V = fr::tc::variant_of(slot == fr::TUNE_TGRADU ? ctx->ndims : 0, cand[i]);
+                if (V.nt == nt && V.cw == cw && V.eg == eg) found = cand[i];
+            }
+            if (found < 0) return set_err(ctx, FR_ERR_ARG, "tuning: variant " + val + " does not fit " + kTuneNames[slot]);
+            want[b][slot] = found;
+        }
+    }
+    for (size_t b = 0; b < want.size(); ++b)
+        for (int k = 0; k < fr::TUNE_N; ++k) ctx->dev.blocks[b].tune[k] = want[b][k];
+    drop_graph(ctx);
     return FR_OK;
 }
 

@@ -52,7 +52,12 @@ struct DevBlock {
     void* rk_tmp = nullptr;
     void* dp_k = nullptr;          // DOPRI5: 7 slope arrays, one state size apart
     void* dp_y = nullptr;          // DOPRI5: stage input / new solution
+    // tensor-core kernel variant of each operator product (TUNE_*; -1: the default rule)
+    int tune[4] = {-1, -1, -1, -1};
 };
+
+// operator products whose kernel variant can be chosen (DevBlock::tune)
+enum TuneSlot { TUNE_DISU = 0, TUNE_TGRADU, TUNE_GRADFPTS, TUNE_TDIVF, TUNE_N };
 
 struct DevPairGroup {          // interior pairs between block bL and block bR
     int bL = 0, bR = 0;
@@ -151,6 +156,10 @@ cudaError_t launch_rk4_adjoint(DevCtx& c, void* const* u0, void* const* lam, dou
                                const std::vector<std::vector<void*>>& tmp, cudaStream_t st);
 // classical RK4, nsteps steps of dt, in place on u
 cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st);
+// whether block b's divergence product carries the RK stage (tensor-core paths)
+bool tdivf_fused(const DevCtx& c, const DevBlock& B);
+// candidate kernel variants of operator product `slot` of block B (at most 8), count returned
+int tune_candidates(const DevCtx& c, const DevBlock& B, int slot, int* out);
 // RHS phases of a partitioned context (all of them for an ordinary one):
 // A = disu + pack U^(f); B1 = common solution, interior and boundary pairs;
 // B2 = common solution at partition pairs, gradients, pack Q^(f);

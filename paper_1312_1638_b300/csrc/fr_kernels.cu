@@ -123,7 +123,7 @@ static void gemm(int M, int K, int K1, const void* A, const void* B1, const void
 template <typename T>
 static cudaError_t op_gemm(DevCtx& c, const void* opA, const void* tcA, int M, int K, int K1, const void* B1,
                     const void* B2, int64_t N, void* C, int epi, const void* rcp, int64_t ld, cudaStream_t st,
-                    int ks0, int ks1, Sub<T> sub) {
+                    int ks0, int ks1, Sub<T> sub, int variant = -1) {
     if (c.precision >= 2) {
         tc::SubRef sr;
         for (int a = 0; a < 5; ++a) sr.v[a] = (float)sub.v[a];
@@ -131,7 +131,7 @@ static cudaError_t op_gemm(DevCtx& c, const void* opA, const void* tcA, int M, i
         const int subseg = ks1 > ks0 ? (ks0 == 0 ? 1 : 2) : 0;
         return tc::gemm(c.precision == 3 ? 0 : 1, M, K1, K - K1, tcA, (const float*)B1, (const float*)B2, N,
                         (float*)C, epi, (const float*)rcp, ld, subseg, sr, c.flags, st, nullptr, nullptr,
-                        c.tc_wait_limit);
+                        c.tc_wait_limit, variant);
     }
     gemm<T>(M, K, K1, opA, B1, B2, N, C, epi, rcp, ld, st, ks0, ks1, sub);
     return cudaGetLastError();
@@ -759,7 +759,7 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
         DevBlock& B = c.blocks[b];
         prof_begin(c, K_DISU, st);
         FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0, nullptr,
-                   B.ld, st, 0, B.nupts, sub));
+                   B.ld, st, 0, B.nupts, sub, B.tune[TUNE_DISU]));
         prof_end(c, st);
     }
     // partition pairs: my side of U^(f) into the exchange buffers
@@ -817,7 +817,7 @@ phase_b1:
                 const tc::GradXform gx{(const float*)B.smat, D, B.nupts, NV};
                 FR_TRY(tc::gemm(c.precision == 3 ? 0 : 1, D * B.nupts, B.nfpts, B.nupts, B.tcQ, (const float*)B.Qf,
                                 (const float*)u[b], N, (float*)B.Q, 0, (const float*)B.rcpdjac, B.ld, 2, sr, c.flags,
-                                st, &gx, nullptr, c.tc_wait_limit));
+                                st, &gx, nullptr, c.tc_wait_limit, B.tune[TUNE_TGRADU]));
                 prof_end(c, st);
             } else {
                 FR_TRY(op_gemm<T>(c, B.opQ, B.tcQ, D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.Qf, u[b], N, B.Q, 0,
@@ -832,7 +832,8 @@ phase_b1:
             for (int i = 0; i < D; ++i) {
                 prof_begin(c, K_GRADFPTS, st);
                 FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, (const T*)B.Q + (int64_t)i * B.nupts * N,
-                           nullptr, N, (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st, 0, 0, Sub<T>{}));
+                           nullptr, N, (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st, 0, 0, Sub<T>{},
+                           B.tune[TUNE_GRADFPTS]));
                 prof_end(c, st);
             }
         }
@@ -929,10 +930,10 @@ phase_c2:
                                (float*)B.rk_tmp, B.nelem};
             FR_TRY(tc::gemm(c.precision == 3 ? 0 : 1, B.nupts, B.nfpts, D * B.nupts, B.tcR, (const float*)B.Uf,
                             (const float*)B.Q, (int64_t)NV * B.ld, nullptr, 1, (const float*)B.rcpdjac, B.ld, 0,
-                            tc::SubRef{}, c.flags, st, nullptr, &f, c.tc_wait_limit));
+                            tc::SubRef{}, c.flags, st, nullptr, &f, c.tc_wait_limit, B.tune[TUNE_TDIVF]));
         } else {
             FR_TRY(op_gemm<T>(c, B.opR, B.tcR, B.nupts, B.nfpts + D * B.nupts, B.nfpts, B.Uf, B.Q, (int64_t)NV * B.ld,
-                              r[b], 1, B.rcpdjac, B.ld, st, 0, 0, Sub<T>{}));
+                              r[b], 1, B.rcpdjac, B.ld, st, 0, 0, Sub<T>{}, B.tune[TUNE_TDIVF]));
         }
         prof_end(c, st);
     }
@@ -977,7 +978,7 @@ static cudaError_t rk4_impl(DevCtx& c, void* const* u, double dt, int nsteps, cu
     std::vector<void*> tmp(c.blocks.size());
     for (size_t b = 0; b < c.blocks.size(); ++b) tmp[b] = c.blocks[b].rk_tmp;
     bool fuse = c.precision >= 2;
-    for (auto& B : c.blocks) fuse = fuse && tc::rk_fusable(B.nupts);
+    for (auto& B : c.blocks) fuse = fuse && tdivf_fused(c, B);
     for (int step = 0; step < nsteps; ++step) {
         const double a_acc[4] = {dt / 6, dt / 3, dt / 3, dt / 6};
         const double a_tmp[3] = {dt / 2, dt / 2, dt};
@@ -1004,6 +1005,33 @@ static cudaError_t rk4_impl(DevCtx& c, void* const* u, double dt, int nsteps, cu
         }
     }
     return cudaGetLastError();
+}
+
+bool tdivf_fused(const DevCtx& c, const DevBlock& B) {
+    if (c.precision < 2 || !tc::rk_fusable(B.nupts)) return false;
+    // the RK stage lives in the two-subtile epilogue
+    return B.tune[TUNE_TDIVF] < 0 || tc::variant_of(0, B.tune[TUNE_TDIVF]).nt == 2;
+}
+
+int tune_candidates(const DevCtx& c, const DevBlock& B, int slot, int* out) {
+    if (c.precision < 2) return 0;
+    const int D = c.ndims;
+    int M = 0, gd = 0;
+    switch (slot) {
+        case TUNE_DISU: case TUNE_GRADFPTS: M = B.nfpts; break;
+        case TUNE_TGRADU: M = D * B.nupts; gd = D; if (c.system != 1) return 0; break;
+        default: M = B.nupts; break;
+    }
+    if (slot == TUNE_GRADFPTS && c.system != 1) return 0;
+    int all[8];
+    const int n = tc::variants(gd, tc::padded_rows(M, gd ? gd : 1), all);
+    int k = 0;
+    for (int i = 0; i < n; ++i) {
+        // keep the RK stage fused where the default fuses it
+        if (slot == TUNE_TDIVF && tc::rk_fusable(B.nupts) && tc::variant_of(0, all[i]).nt != 2) continue;
+        out[k++] = all[i];
+    }
+    return k;
 }
 
 cudaError_t launch_rk4(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {

@@ -101,16 +101,11 @@ __host__ __device__ inline RowBlocks row_blocks(int M, int group) {
 // 128-column subtiles per work item: two when the row block is at most 128
 // rows, so that both accumulators still fit twice in tensor memory
 __host__ __device__ constexpr int subtiles_for(int nrp) { return nrp <= 128 ? 2 : 1; }
-// epilogue warp groups (4 warps each, one per TMEM lane quadrant)
-// (the gradient transform epilogue, gd > 0, holds more registers per thread)
-constexpr int GX_EG = 4;                       // epilogue warp groups with the gradient transform
-__host__ __device__ constexpr int epi_groups(int nt, int gd) { return gd ? GX_EG : nt == 2 ? 2 : 3; }
-// converter warps (sets of 4, one warp per scheduler each): two sets split
-// each chunk's conversion, except beside the register-hungry gradient epilogue
-__host__ __device__ constexpr int conv_warps(int gd) { return gd ? 4 : 8; }
-__host__ __device__ constexpr int nthreads_for(int nt, int gd) {
-    return 64 + 32 * conv_warps(gd) + 128 * epi_groups(nt, gd);
-}
+// Threads of a kernel variant: producer and MMA warps, cw converter warps
+// (sets of 4, one warp per scheduler each; the sets split each chunk's
+// conversion) and eg epilogue warp groups (4 warps each, one per TMEM lane
+// quadrant).
+__host__ __device__ constexpr int nthreads_for(int cw, int eg) { return 64 + 32 * cw + 128 * eg; }
 
 struct Layout {
     int nrp;                      // rows per block (MMA N)
@@ -297,11 +292,9 @@ __device__ __forceinline__ float sub_of(const TcArgs& a, int64_t v) {
     return v == 0 ? a.sub0 : v == 1 ? a.sub1 : v == 2 ? a.sub2 : v == 3 ? a.sub3 : a.sub4;
 }
 
-template <int KIND, int NT, int GD>
-__global__ void __launch_bounds__(nthreads_for(NT, GD), 1)
+template <int KIND, int NT, int GD, int CONVW, int EG>
+__global__ void __launch_bounds__(nthreads_for(CONVW, EG), 1)
 tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2) {
-    constexpr int EG = epi_groups(NT, GD);
-    constexpr int CONVW = conv_warps(GD);
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[MAX_NST], bar_conv[MAX_NST], bar_empty[MAX_NST];
     __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
@@ -681,19 +674,62 @@ static bool make_map(CUtensorMap* m, const float* base, int64_t N, int rows, int
 static int g_nsm = 0;
 static bool g_attr[2] = {false, false};
 
+// Kernel variants (subtiles, converter warps, epilogue groups), by epilogue
+// class: the plain / -1/J / RK-stage epilogue (gd = 0) and the gradient
+// transform (gd = 2, 3).  Entry 0 of each list is the default rule's choice
+// for one subtile, entry 1 for two subtiles.
+constexpr int NV0 = 6, NVG = 5;
+static const Variant kVar0[NV0] = {{1, 8, 3}, {2, 8, 2}, {1, 8, 2}, {1, 12, 2}, {2, 4, 3}, {1, 4, 3}};
+static const Variant kVarG[NVG] = {{1, 4, 4}, {2, 4, 4}, {1, 8, 3}, {1, 8, 4}, {2, 8, 3}};
+
+template <int KIND, int GD>
+static const void* variant_fn(int v) {
+    if constexpr (GD == 0) {
+        switch (v) {
+            case 0: return (const void*)tc_gemm_kernel<KIND, 1, 0, 8, 3>;
+            case 1: return (const void*)tc_gemm_kernel<KIND, 2, 0, 8, 2>;
+            case 2: return (const void*)tc_gemm_kernel<KIND, 1, 0, 8, 2>;
+            case 3: return (const void*)tc_gemm_kernel<KIND, 1, 0, 12, 2>;
+            case 4: return (const void*)tc_gemm_kernel<KIND, 2, 0, 4, 3>;
+            case 5: return (const void*)tc_gemm_kernel<KIND, 1, 0, 4, 3>;
+        }
+    } else {
+        switch (v) {
+            case 0: return (const void*)tc_gemm_kernel<KIND, 1, GD, 4, 4>;
+            case 1: return (const void*)tc_gemm_kernel<KIND, 2, GD, 4, 4>;
+            case 2: return (const void*)tc_gemm_kernel<KIND, 1, GD, 8, 3>;
+            case 3: return (const void*)tc_gemm_kernel<KIND, 1, GD, 8, 4>;
+            case 4: return (const void*)tc_gemm_kernel<KIND, 2, GD, 8, 3>;
+        }
+    }
+    return nullptr;
+}
+
 template <int KIND>
 static cudaError_t set_smem() {
-    const void* fns[6] = {(const void*)tc_gemm_kernel<KIND, 1, 0>, (const void*)tc_gemm_kernel<KIND, 2, 0>,
-                          (const void*)tc_gemm_kernel<KIND, 1, 2>, (const void*)tc_gemm_kernel<KIND, 2, 2>,
-                          (const void*)tc_gemm_kernel<KIND, 1, 3>, (const void*)tc_gemm_kernel<KIND, 2, 3>};
-    for (const void* f : fns) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
-        if (e != cudaSuccess) return e;
-    }
+    for (int gd : {0, 2, 3})
+        for (int v = 0; v < (gd ? NVG : NV0); ++v) {
+            const void* f = gd == 0 ? variant_fn<KIND, 0>(v) : gd == 2 ? variant_fn<KIND, 2>(v) : variant_fn<KIND, 3>(v);
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
+            if (e != cudaSuccess) return e;
+        }
     return cudaSuccess;
 }
 
 bool rk_fusable(int M) { return subtiles_for(row_blocks(M, 1).nrp) == 2; }
+
+int variants(int gd, int nrp, int* out) {
+    const Variant* tab = gd ? kVarG : kVar0;
+    const int n = gd ? NVG : NV0;
+    int k = 0;
+    for (int v = 0; v < n; ++v)
+        if (tab[v].nt == 1 || nrp <= 128) out[k++] = v;
+    return k;
+}
+
+Variant variant_of(int gd, int v) { return (gd ? kVarG : kVar0)[v]; }
+
+int padded_rows(int M, int group) { return row_blocks(M, group).nrp; }
 
 cudaError_t prepare() {
     int dev = 0;
@@ -707,31 +743,27 @@ cudaError_t prepare() {
 }
 
 template <int KIND>
-static cudaError_t launch(const TcArgs& a, int nt, const CUtensorMap& m1, const CUtensorMap& m2, int nsm,
+static cudaError_t launch(const TcArgs& a, int v, const CUtensorMap& m1, const CUtensorMap& m2, int nsm,
                           cudaStream_t st) {
-    const Layout L = make_layout(KIND, a.nrp, nt);
+    const int gd = a.epi == 2 ? a.gD : 0;
+    const Variant V = variant_of(gd, v);
+    const Layout L = make_layout(KIND, a.nrp, V.nt);
     if (!g_attr[KIND]) {
         cudaError_t e = set_smem<KIND>();
         if (e != cudaSuccess) return e;
         g_attr[KIND] = true;
     }
     const int grid = std::min(a.nwork, nsm);
-    const int gd = a.epi == 2 ? a.gD : 0;
-    if (nt == 2) {
-        if (gd == 3) tc_gemm_kernel<KIND, 2, 3><<<grid, nthreads_for(2, 3), L.smem, st>>>(a, m1, m2);
-        else if (gd == 2) tc_gemm_kernel<KIND, 2, 2><<<grid, nthreads_for(2, 2), L.smem, st>>>(a, m1, m2);
-        else tc_gemm_kernel<KIND, 2, 0><<<grid, nthreads_for(2, 0), L.smem, st>>>(a, m1, m2);
-    } else {
-        if (gd == 3) tc_gemm_kernel<KIND, 1, 3><<<grid, nthreads_for(1, 3), L.smem, st>>>(a, m1, m2);
-        else if (gd == 2) tc_gemm_kernel<KIND, 1, 2><<<grid, nthreads_for(1, 2), L.smem, st>>>(a, m1, m2);
-        else tc_gemm_kernel<KIND, 1, 0><<<grid, nthreads_for(1, 0), L.smem, st>>>(a, m1, m2);
-    }
-    return cudaGetLastError();
+    const int nth = nthreads_for(V.cw, V.eg);
+    const void* f = gd == 0 ? variant_fn<KIND, 0>(v) : gd == 2 ? variant_fn<KIND, 2>(v) : variant_fn<KIND, 3>(v);
+    if (!f) return cudaErrorInvalidValue;
+    void* args[3] = {(void*)&a, (void*)&m1, (void*)&m2};
+    return cudaLaunchKernel(f, dim3(grid), dim3(nth), args, (size_t)L.smem, st);
 }
 
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
-                 cudaStream_t st, const GradXform* gx, const RkFuse* rk, long long wait_limit) {
+                 cudaStream_t st, const GradXform* gx, const RkFuse* rk, long long wait_limit, int variant) {
     if (!g_nsm) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
@@ -741,7 +773,12 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
     if (gx && (gx->ndims < 2 || gx->ndims > 3 || M != gx->ndims * gx->nupts || !gx->smat || !rcp))
         return cudaErrorInvalidValue;
     const RowBlocks B = row_blocks(M, gx ? gx->ndims : 1);
-    const int nt = subtiles_for(B.nrp);
+    const int gdv = gx ? gx->ndims : 0;
+    if (variant < 0) variant = subtiles_for(B.nrp) == 2 ? 1 : 0;      // the default rule
+    if (variant >= (gdv ? NVG : NV0)) return cudaErrorInvalidValue;
+    const Variant V = variant_of(gdv, variant);
+    if (V.nt == 2 && B.nrp > 128) return cudaErrorInvalidValue;       // two accumulators per buffer must fit
+    const int nt = V.nt;
     TcArgs a;
     a.M = M;
     a.nrb = B.nrb;
@@ -797,7 +834,7 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
     } else {
         m2 = m1;
     }
-    return kind == 0 ? launch<0>(a, nt, m1, m2, g_nsm, st) : launch<1>(a, nt, m1, m2, g_nsm, st);
+    return kind == 0 ? launch<0>(a, variant, m1, m2, g_nsm, st) : launch<1>(a, variant, m1, m2, g_nsm, st);
 }
 
 }  // namespace tc

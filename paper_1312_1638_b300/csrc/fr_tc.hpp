@@ -58,11 +58,26 @@ struct RkFuse {
 };
 
 // wait_limit: SM clock cycles after which a bounded wait gives up and sets
-// flags[1] (0: about two seconds)
+// flags[1] (0: about two seconds).  variant: index of the kernel variant
+// (see variants(); -1: the default rule), cudaErrorInvalidValue if it does
+// not fit the operator.
 cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
                  float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
                  cudaStream_t st, const GradXform* gx = nullptr, const RkFuse* rk = nullptr,
-                 long long wait_limit = 0);
+                 long long wait_limit = 0, int variant = -1);
+
+// A kernel variant: 128-column subtiles per work item (1 or 2), converter
+// warps and epilogue warp groups.
+struct Variant {
+    int nt, cw, eg;
+};
+// Variants that fit an operator of nrp padded rows per row block, for the
+// plain / -1/J / RK-stage epilogue (gd = 0) or the gradient transform of gd
+// dimensions: their indices into out[] (at most 8); returns the count.
+int variants(int gd, int nrp, int* out);
+Variant variant_of(int gd, int v);
+// padded rows per row block of an M-row operator (group g: whole points of g rows)
+int padded_rows(int M, int group);
 
 // whether an M-row operator runs with two 128-column subtiles, the kernels
 // that carry the fused RK stage epilogue (M <= 128)

@@ -15,6 +15,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(_HERE, "libfr.so")
+# kernel-variant choices measured on B300 by fr_autotune, keyed by Solver.tuning_key()
+TUNING_CACHE = os.path.join(_HERE, "tuning_b300.json")
 
 OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_OOM = range(8)
 EULER, NAVIER_STOKES = 0, 1
@@ -29,7 +31,7 @@ EXPORTS = ["fr_setup", "fr_layout", "fr_solution_points", "fr_operator", "fr_pai
            "fr_last_error", "fr_destroy", "fr_version", "fr_profile_enable", "fr_profile_read",
            "fr_rk4_noalloc", "fr_adjoint_rhs", "fr_rk4_adjoint", "fr_set_option", "fr_fma_peak",
            "fr_euler", "fr_dopri5", "fr_setup_part", "fr_part_slots", "fr_rhs_parts", "fr_rk_step",
-           "fr_rk4_host"]
+           "fr_rk4_host", "fr_autotune", "fr_get_tuning", "fr_set_tuning"]
 
 
 class FRError(RuntimeError):
@@ -85,6 +87,9 @@ def load():
     lib.fr_rk4.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_rk4_noalloc.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_rk_step.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
+    lib.fr_autotune.argtypes = [vp, vpp, C.c_int, vp]
+    lib.fr_get_tuning.argtypes = [vp, C.c_char_p, C.c_int64]
+    lib.fr_set_tuning.argtypes = [vp, C.c_char_p]
     lib.fr_rk4_host.argtypes = [vp, vpp, C.c_double, C.c_int, vp]
     lib.fr_adjoint_rhs.argtypes = [vp, vpp, vpp, vpp, vp]
     lib.fr_set_option.argtypes = [vp, C.c_char_p, C.c_int64]
@@ -430,6 +435,51 @@ class Solver:
 
     def check_finite(self, u, stream=None):
         self._check(self.lib.fr_check_finite(self.ctx, _ptrs(u), _stream_ptr(stream)))
+
+    def autotune(self, u, reps=2, stream=None):
+        """Time every tensor-core kernel variant of each operator product on a
+        copy of u and keep the fastest (fr_autotune); returns tuning()."""
+        self._check(self.lib.fr_autotune(self.ctx, _ptrs(u), int(reps), _stream_ptr(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        """The context's kernel-variant choices as text (fr_get_tuning)."""
+        buf = C.create_string_buffer(4096)
+        self._check(self.lib.fr_get_tuning(self.ctx, buf, len(buf)))
+        return buf.value.decode()
+
+    def set_tuning(self, text):
+        self._check(self.lib.fr_set_tuning(self.ctx, text.encode()))
+
+    def tuning_key(self):
+        """Key of a tuning cache entry: element types, order, system, precision."""
+        ets = "+".join(b.etype for b in self.mesh.blocks)
+        prec = {FP64: "fp64", FP32: "fp32", BF16X3: "bf16x3", TF32X3: "tf32x3"}[self.precision]
+        sysn = "ns" if self.system == NAVIER_STOKES else "euler"
+        return f"{ets}/p{self.params.order}/{sysn}/{prec}"
+
+    def apply_tuning(self, u=None, cache=None, reps=2, stream=None):
+        """Apply the cached choices for tuning_key() from the JSON file `cache`
+        (default: the library's committed B300 table); without an entry, and
+        given a state u, autotune and add the result to the file.  Returns
+        (source, text) with source "cache", "autotuned" or "default"."""
+        import json
+        path = cache or TUNING_CACHE
+        table = {}
+        if os.path.exists(path):
+            with open(path) as fh:
+                table = json.load(fh)
+        key = self.tuning_key()
+        if key in table:
+            self.set_tuning(table[key])
+            return "cache", self.tuning()
+        if u is None:
+            return "default", self.tuning()
+        text = self.autotune(u, reps, stream)
+        table[key] = text
+        with open(path, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+        return "autotuned", text
 
     def set_option(self, name, value):
         self._check(self.lib.fr_set_option(self.ctx, name.encode(), int(value)))

@@ -27,7 +27,7 @@ def test_library_exports_every_declared_symbol(fr):
     for n in names:
         assert hasattr(lib, n), n
     assert set(names) == set(fr.EXPORTS)
-    assert fr.load().fr_version() == 5
+    assert fr.load().fr_version() == 6
 
 
 CASES = [("quad", 3, 1, 0.1), ("quad", 3, 4, 0.1), ("hex", 2, 2, 0.1), ("hex", 2, 4, 0.0)]
@@ -196,3 +196,15 @@ def test_device_calls_on_a_host_only_context_are_refused(fr):
     assert s.lib.fr_adjoint_rhs(s.ctx, None, None, None, None) in (fr.ERR_ARG, fr.ERR_UNSUPPORTED)
     assert s.lib.fr_rk4(s.ctx, None, 1e-3, 1, None) in (fr.ERR_ARG, fr.ERR_UNSUPPORTED)
     assert s.lib.fr_sync_status(s.ctx) == fr.ERR_UNSUPPORTED
+
+
+def test_tuning_calls_on_host_only_contexts(fr):
+    """fr_get_tuning reports no blocks on a host-only context, fr_set_tuning
+    refuses (it chooses device kernels)."""
+    m = periodic_box("hex", 2, 0.0, 1.0)
+    s = fr.Solver(m, 2, "ns", "tf32x3", device=-1)
+    assert s.tuning() == ""
+    with pytest.raises(fr.FRError) as e:
+        s.set_tuning("b0:disu=1.8.3")
+    assert e.value.status == fr.ERR_UNSUPPORTED
+    assert "tf32x3" in s.tuning_key() and s.tuning_key().startswith("hex/p2/ns")
