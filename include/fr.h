@@ -278,7 +278,12 @@ fr_status fr_get_tuning(const fr_ctx* ctx, char* buf, int64_t size);
 fr_status fr_set_tuning(fr_ctx* ctx, const char* text);
 
 /* Context options (not in the paper): "graphs" (default 1) enables the RK4-step CUDA graph of
- * fr_rk4.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
+ * fr_rk4.  "group_blocks" (default 1): on the tensor-core paths each operator
+ * product of a mesh with 2 to 4 element blocks (a mixed mesh) runs as one
+ * persistent launch over the work items of every block, and the D
+ * interpolations of the gradient (Eq. gradufpts) run as one launch; 0 gives
+ * every block its own launches.  Changing it drops the captured RK4 step;
+ * results are the same bits either way.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
  * operator GEMMs gives up: the kernel then drains its own copies and MMAs,
  * returns, and fr_sync_status reports FR_ERR_TIMEOUT; the context stays

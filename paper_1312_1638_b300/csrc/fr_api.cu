@@ -955,16 +955,34 @@ fr_status fr_autotune(fr_ctx* ctx, void* const* u, int reps, void* stream) {
         // by the profiler; the other blocks' choices stay fixed, so the difference
         // between candidates is this block's
         const int kid[fr::TUNE_N] = {fr::K_DISU, fr::K_TGRADU, fr::K_GRADFPTS, fr::K_TDIVF};
+        // a grouped context launches each product once for all blocks: its blocks
+        // share one choice, among the variants that fit every block
+        const bool grouped = D.group_blocks && D.blocks.size() > 1 && (int)D.blocks.size() <= fr::tc::group_max();
         for (int slot = 0; slot < fr::TUNE_N; ++slot)
-            for (size_t b = 0; b < D.blocks.size(); ++b) {
+            for (size_t b = 0; b < (grouped ? 1 : D.blocks.size()); ++b) {
                 fr::DevBlock& B = D.blocks[b];
                 int cand[8];
-                const int nc = fr::tune_candidates(D, B, slot, cand);
+                int nc = fr::tune_candidates(D, B, slot, cand);
+                if (grouped) {
+                    int k = 0;
+                    for (int i = 0; i < nc; ++i) {
+                        bool fits = true;
+                        for (auto& B2 : D.blocks) {
+                            int c2[8];
+                            const int n2 = fr::tune_candidates(D, B2, slot, c2);
+                            fits = fits && std::find(c2, c2 + n2, cand[i]) != c2 + n2;
+                        }
+                        if (fits) cand[k++] = cand[i];
+                    }
+                    nc = k;
+                }
                 if (nc < 2) continue;
                 double best_t = 1e300;
                 int best = B.tune[slot];
                 for (int i = 0; i < nc; ++i) {
                     B.tune[slot] = cand[i];
+                    if (grouped)
+                        for (auto& B2 : D.blocks) B2.tune[slot] = cand[i];
                     CK(fr::launch_rk4(D, tmp.data(), 0.0, 1, st));
                     int64_t l[fr::K_NKERNELS];
                     double t[fr::K_NKERNELS];
@@ -977,6 +995,8 @@ fr_status fr_autotune(fr_ctx* ctx, void* const* u, int reps, void* stream) {
                     }
                 }
                 B.tune[slot] = best;
+                if (grouped)
+                    for (auto& B2 : D.blocks) B2.tune[slot] = best;
             }
     } catch (const Fail& f) {
         D.prof = prof;
@@ -1077,6 +1097,11 @@ fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value) {
     if (!ctx || !name) return FR_ERR_ARG;
     if (std::string(name) == "graphs") {
         ctx->use_graphs = value != 0;
+        return FR_OK;
+    }
+    if (std::string(name) == "group_blocks") {
+        ctx->dev.group_blocks = value != 0;
+        drop_graph(ctx);
         return FR_OK;
     }
     if (std::string(name) == "tc_wait_limit") {

@@ -130,6 +130,7 @@ struct DevCtx {
     std::vector<DevMpiGroup> mgroups;
     int* flags = nullptr;          // [0] non-finite seen, [1] timeout
     long long tc_wait_limit = 0;   // tensor-core GEMM wait limit in SM cycles (0: about two seconds)
+    bool group_blocks = true;      // tensor-core products of all element blocks in one launch per stage
     double* partial = nullptr;     // reduction scratch
     int64_t npartial = 0;
 };

@@ -744,6 +744,31 @@ struct RkStage {
     void* const* u;           // the step's state (per block)
 };
 
+// Tensor-core products of every block in one launch (the blocks' problems
+// form one work list), when the context groups them.
+static bool grouped(const DevCtx& c) {
+    return c.group_blocks && c.precision >= 2 && c.blocks.size() > 1 && (int)c.blocks.size() <= tc::group_max();
+}
+
+// the kernel variant of a grouped launch: block 0's choice (the tuner keeps
+// the blocks' choices equal in grouped contexts); -1 when it does not fit
+static int group_variant(const DevCtx& c, int slot) {
+    const int v = c.blocks[0].tune[slot];
+    if (v < 0) return -1;
+    for (const DevBlock& B : c.blocks) {
+        int cand[8];
+        const int n = tune_candidates(c, B, slot, cand);
+        if (std::find(cand, cand + n, v) == cand + n) return -1;
+    }
+    return v;
+}
+
+static cudaError_t run_group(DevCtx& c, int epi, const std::vector<tc::GemmProblem>& P, tc::SubRef sr, int slot,
+                             cudaStream_t st) {
+    return tc::gemm_group(c.precision == 3 ? 0 : 1, epi, P.data(), (int)P.size(), sr, c.flags, st, c.tc_wait_limit,
+                          group_variant(c, slot));
+}
+
 template <typename T, int D>
 static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStream_t st, int phases = PH_ALL,
                             const RkStage* rk = nullptr) {
@@ -753,14 +778,28 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
     Sub<T> sub{};
     sub.v[0] = T(c.prm.ref_rho);
     sub.v[NV - 1] = T(c.prm.ref_E);
+    tc::SubRef sr;
+    for (int a = 0; a < 5; ++a) sr.v[a] = (float)sub.v[a];
     if (!(phases & PH_A)) goto phase_b1;
     // 1. U'^(f) = M0 (U - u_ref)  (K1, disu)
-    for (size_t b = 0; b < c.blocks.size(); ++b) {
-        DevBlock& B = c.blocks[b];
+    if (grouped(c)) {
+        std::vector<tc::GemmProblem> P;
+        for (size_t b = 0; b < c.blocks.size(); ++b) {
+            DevBlock& B = c.blocks[b];
+            P.push_back({B.nfpts, B.nupts, 0, B.tcM0, (const float*)u[b], nullptr, (int64_t)NV * B.ld, (float*)B.Uf,
+                         nullptr, B.ld, 1, nullptr, nullptr});
+        }
         prof_begin(c, K_DISU, st);
-        FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0, nullptr,
-                   B.ld, st, 0, B.nupts, sub, B.tune[TUNE_DISU]));
+        FR_TRY(run_group(c, 0, P, sr, TUNE_DISU, st));
         prof_end(c, st);
+    } else {
+        for (size_t b = 0; b < c.blocks.size(); ++b) {
+            DevBlock& B = c.blocks[b];
+            prof_begin(c, K_DISU, st);
+            FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0,
+                              nullptr, B.ld, st, 0, B.nupts, sub, B.tune[TUNE_DISU]));
+            prof_end(c, st);
+        }
     }
     // partition pairs: my side of U^(f) into the exchange buffers
     for (auto& g : c.mgroups) {
@@ -805,21 +844,61 @@ phase_b1:
                                       (T*)q.recv_q, (T*)B.Qf, T(c.prm.beta), st);
             prof_end(c, st);
         }
-        for (size_t b = 0; b < c.blocks.size(); ++b) {
-            DevBlock& B = c.blocks[b];
-            int64_t N = (int64_t)NV * B.ld;
-            // 3. Q~ = M6 C + (M4 - M6 M0) U  (tgradu, eq. tquptsm)
-            // 4. Q = J^{-T} Q~ (gradcoru; in the tensor-core GEMM's epilogue)
-            prof_begin(c, K_TGRADU, st);
-            if (c.precision >= 2) {
-                tc::SubRef sr;
-                for (int a = 0; a < 5; ++a) sr.v[a] = (float)sub.v[a];
-                const tc::GradXform gx{(const float*)B.smat, D, B.nupts, NV};
-                FR_TRY(tc::gemm(c.precision == 3 ? 0 : 1, D * B.nupts, B.nfpts, B.nupts, B.tcQ, (const float*)B.Qf,
-                                (const float*)u[b], N, (float*)B.Q, 0, (const float*)B.rcpdjac, B.ld, 2, sr, c.flags,
-                                st, &gx, nullptr, c.tc_wait_limit, B.tune[TUNE_TGRADU]));
+        // 3. Q~ = M6 C + (M4 - M6 M0) U  (tgradu, eq. tquptsm)
+        // 4. Q = J^{-T} Q~ (gradcoru; in the tensor-core GEMM's epilogue)
+        // 5. Q^(f) = M5 Q (block diagonal: M0 per component)
+        if (c.precision >= 2) {
+            std::vector<tc::GradXform> gx(c.blocks.size());
+            std::vector<tc::GemmProblem> PQ, PF;
+            for (size_t b = 0; b < c.blocks.size(); ++b) {
+                DevBlock& B = c.blocks[b];
+                const int64_t N = (int64_t)NV * B.ld;
+                gx[b] = tc::GradXform{(const float*)B.smat, D, B.nupts, NV};
+                PQ.push_back({D * B.nupts, B.nfpts, B.nupts, B.tcQ, (const float*)B.Qf, (const float*)u[b], N,
+                              (float*)B.Q, (const float*)B.rcpdjac, B.ld, 2, &gx[b], nullptr});
+                for (int i = 0; i < D; ++i)
+                    PF.push_back({B.nfpts, B.nupts, 0, B.tcM0, (const float*)B.Q + (int64_t)i * B.nupts * N, nullptr,
+                                  N, (float*)B.Qf + (int64_t)i * B.nfpts * N, nullptr, B.ld, 0, nullptr, nullptr});
+            }
+            if (grouped(c)) {
+                prof_begin(c, K_TGRADU, st);
+                FR_TRY(run_group(c, 0, PQ, sr, TUNE_TGRADU, st));
                 prof_end(c, st);
             } else {
+                for (size_t b = 0; b < c.blocks.size(); ++b) {
+                    prof_begin(c, K_TGRADU, st);
+                    FR_TRY(tc::gemm_group(c.precision == 3 ? 0 : 1, 0, &PQ[b], 1, sr, c.flags, st, c.tc_wait_limit,
+                                          c.blocks[b].tune[TUNE_TGRADU]));
+                    prof_end(c, st);
+                }
+            }
+            // the D interpolations of the gradient (and of every block, when grouped)
+            // in as few launches as the group size allows
+            const int gmax = tc::group_max();
+            if (grouped(c) || c.blocks.size() == 1) {
+                for (size_t i0 = 0; i0 < PF.size(); i0 += gmax) {
+                    const std::vector<tc::GemmProblem> part(PF.begin() + i0,
+                                                            PF.begin() + std::min(PF.size(), i0 + (size_t)gmax));
+                    prof_begin(c, K_GRADFPTS, st);
+                    FR_TRY(c.blocks.size() == 1
+                               ? tc::gemm_group(c.precision == 3 ? 0 : 1, 0, part.data(), (int)part.size(), sr,
+                                                c.flags, st, c.tc_wait_limit, c.blocks[0].tune[TUNE_GRADFPTS])
+                               : run_group(c, 0, part, sr, TUNE_GRADFPTS, st));
+                    prof_end(c, st);
+                }
+            } else {
+                for (size_t b = 0; b < c.blocks.size(); ++b) {
+                    prof_begin(c, K_GRADFPTS, st);
+                    FR_TRY(tc::gemm_group(c.precision == 3 ? 0 : 1, 0, &PF[b * D], D, sr, c.flags, st,
+                                          c.tc_wait_limit, c.blocks[b].tune[TUNE_GRADFPTS]));
+                    prof_end(c, st);
+                }
+            }
+        } else {
+            for (size_t b = 0; b < c.blocks.size(); ++b) {
+                DevBlock& B = c.blocks[b];
+                int64_t N = (int64_t)NV * B.ld;
+                prof_begin(c, K_TGRADU, st);
                 FR_TRY(op_gemm<T>(c, B.opQ, B.tcQ, D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.Qf, u[b], N, B.Q, 0,
                                   nullptr, B.ld, st, B.nfpts, B.nfpts + B.nupts, sub));
                 prof_end(c, st);
@@ -827,14 +906,13 @@ phase_b1:
                 grad_transform_kernel<T, D><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
                     B.nupts, B.nelem, B.ld, (const T*)B.smat, (const T*)B.rcpdjac, (T*)B.Q);
                 prof_end(c, st);
-            }
-            // 5. Q^(f) = M5 Q (block diagonal: M0 per component)
-            for (int i = 0; i < D; ++i) {
-                prof_begin(c, K_GRADFPTS, st);
-                FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, (const T*)B.Q + (int64_t)i * B.nupts * N,
-                           nullptr, N, (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st, 0, 0, Sub<T>{},
-                           B.tune[TUNE_GRADFPTS]));
-                prof_end(c, st);
+                for (int i = 0; i < D; ++i) {
+                    prof_begin(c, K_GRADFPTS, st);
+                    FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts,
+                                      (const T*)B.Q + (int64_t)i * B.nupts * N, nullptr, N,
+                                      (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st, 0, 0, Sub<T>{}));
+                    prof_end(c, st);
+                }
             }
         }
         // partition pairs: my side of Q^(f) into the exchange buffers
@@ -922,6 +1000,22 @@ phase_c2:
         prof_end(c, st);
     }
     // 8. R = -J^{-1} [M3 D~ + (M1 - M3 M2) F~]  (tdivtpcorf + negdivconf)
+    if (grouped(c)) {
+        std::vector<tc::RkFuse> f(c.blocks.size());
+        std::vector<tc::GemmProblem> P;
+        for (size_t b = 0; b < c.blocks.size(); ++b) {
+            DevBlock& B = c.blocks[b];
+            if (rk) f[b] = tc::RkFuse{rk->mode, (float)rk->a, (float)rk->b, (float*)rk->u[b], (float*)B.rk_acc,
+                                      (float*)B.rk_tmp, B.nelem};
+            P.push_back({B.nupts, B.nfpts, D * B.nupts, B.tcR, (const float*)B.Uf, (const float*)B.Q,
+                         (int64_t)NV * B.ld, rk ? nullptr : (float*)r[b], (const float*)B.rcpdjac, B.ld, 0, nullptr,
+                         rk ? &f[b] : nullptr});
+        }
+        prof_begin(c, K_TDIVF, st);
+        FR_TRY(run_group(c, 1, P, tc::SubRef{}, TUNE_TDIVF, st));
+        prof_end(c, st);
+        return cudaGetLastError();
+    }
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
         prof_begin(c, K_TDIVF, st);

@@ -236,6 +236,26 @@ __device__ __forceinline__ int col_tile(const TcArgs& a, int tl) {
     return (tl % a.vinter) * per + tl / a.vinter;
 }
 
+// One launch serves a group of problems (the same operator product of every
+// element block of a mixed mesh): their work items form one list, problem
+// after problem.  Shared-memory stages and tensor-memory buffers are laid out
+// for the group's largest operator block (nrp); each work item's MMA width,
+// operator copy and epilogue follow its own problem.
+constexpr int MAXG = 4;
+struct TcGroup {
+    CUtensorMap m[2 * MAXG];      // state tensor maps (segments 1 and 2) of every problem
+    TcArgs p[MAXG];
+    int ng;
+    int wstart[MAXG + 1];         // first work item of each problem; wstart[ng] = all work items
+    int nrp;                      // largest padded rows per block of the group
+};
+
+__device__ __forceinline__ int group_of(const TcGroup& G, int w) {
+    int g = 0;
+    while (g + 1 < G.ng && w >= G.wstart[g + 1]) ++g;
+    return g;
+}
+
 // Epilogue of the gradient transform: 4-point units of one row block,
 // q_i = acc(s, i) from tensor memory, Q_j(s) = rcp(s) sum_i adj_ij(s) q_i
 // (Q = J^-T Q~, with adj = J J^-1 and rcp = 1/J stored per point).
@@ -294,15 +314,17 @@ __device__ __forceinline__ float sub_of(const TcArgs& a, int64_t v) {
 
 template <int KIND, int NT, int GD, int CONVW, int EG>
 __global__ void __launch_bounds__(nthreads_for(CONVW, EG), 1)
-tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2) {
+tc_gemm_kernel(const __grid_constant__ TcGroup G) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[MAX_NST], bar_conv[MAX_NST], bar_empty[MAX_NST];
     __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
     __shared__ uint32_t tmem_holder;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nch = a.nch1 + a.nch2;
-    const Layout L = make_layout(KIND, a.nrp, NT);
+    const int nwork = G.wstart[G.ng];
+    int* const flags = G.p[0].flags;
+    const long long limit = G.p[0].limit;
+    const Layout L = make_layout(KIND, G.nrp, NT);
     constexpr int ESZ = KIND == 0 ? 4 : 2;
     constexpr int KCE = ROWB / ESZ;
 
@@ -334,27 +356,31 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
         // ---------------------------------------------------------- producer
         if (lane == 0) {
             int it = 0;
-            for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x) {
-                const int tl = w / a.nrb, rb = w - tl * a.nrb;
+            for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+                const int g = group_of(G, w);
+                const TcArgs& a = G.p[g];
+                const int lw = w - G.wstart[g], nch = a.nch1 + a.nch2;
+                const int tl = lw / a.nrb, rb = lw - tl * a.nrb;
                 const int col0 = col_tile(a, tl) * NT * BN;
-                const uint8_t* ablk = a.Apack + (size_t)rb * nch * L.a_bytes;
+                const int ab = 2 * a.nrp * ROWB;                     // this problem's operator chunk
+                const uint8_t* ablk = a.Apack + (size_t)rb * nch * ab;
                 for (int c = 0; c < nch; ++c, ++it) {
                     const int s = it % L.nst, k = it / L.nst;
-                    if (k > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (k - 1) & 1, a.limit)) { ok = false; break; }
+                    if (k > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (k - 1) & 1, limit)) { ok = false; break; }
                     uint8_t* st = smem + s * L.stage;
                     const uint32_t fb = smem_u32(&bar_full[s]);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                                 "r"((uint32_t)(L.a_bytes + L.stg_bytes))
+                                 "r"((uint32_t)(ab + L.stg_bytes))
                                  : "memory");
-                    const uint8_t* src = ablk + (size_t)c * L.a_bytes;
+                    const uint8_t* src = ablk + (size_t)c * ab;
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                             smem_u32(st)),
-                        "l"(src), "r"((uint32_t)L.a_bytes), "r"(fb)
+                        "l"(src), "r"((uint32_t)ab), "r"(fb)
                         : "memory");
                     const bool seg1 = c < a.nch1;
                     const int row0 = (seg1 ? c : c - a.nch1) * KCE;
-                    const CUtensorMap* tm = seg1 ? &tm1 : &tm2;
+                    const CUtensorMap* tm = &G.m[2 * g + (seg1 ? 0 : 1)];
                     asm volatile(
                         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
                         "{%2, %3}], [%4];" ::"r"(smem_u32(st + L.off_stg)),
@@ -366,24 +392,26 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
             // last chunk armed on every stage before the CTA may exit
             for (int i = it > L.nst ? it - L.nst : 0; i < it; ++i)
                 if (!mbar_wait(smem_u32(&bar_full[i % L.nst]), (i / L.nst) & 1, DRAIN_LIMIT)) ok = false;
-            if (!ok) atomicOr(&a.flags[1], 1);
+            if (!ok) atomicOr(&flags[1], 1);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t id = instr_desc<KIND>(L.nrp);
             int it = 0, wc = 0;
-            for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x, ++wc) {
+            for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++wc) {
+                const TcArgs& a = G.p[group_of(G, w)];
+                const int nch = a.nch1 + a.nch2;
+                const uint32_t id = instr_desc<KIND>(a.nrp);
                 const int b = wc % L.tbuf;
-                if (!mbar_wait(smem_u32(&bar_tempty[b]), ((wc / L.tbuf) & 1) ^ 1, a.limit)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&bar_tempty[b]), ((wc / L.tbuf) & 1) ^ 1, limit)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t dbase = tmem + (uint32_t)(b * NT * L.nrp);
                 for (int c = 0; c < nch; ++c, ++it) {
                     const int s = it % L.nst, k = it / L.nst;
-                    if (!mbar_wait(smem_u32(&bar_conv[s]), k & 1, a.limit)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&bar_conv[s]), k & 1, limit)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t st = smem_u32(smem + s * L.stage);
-                    const uint32_t o_hi = st, o_lo = st + L.opart;            // operator parts (MMA B)
+                    const uint32_t o_hi = st, o_lo = st + (uint32_t)(a.nrp * ROWB);   // operator parts (MMA B)
 #pragma unroll
                     for (int t = 0; t < NT; ++t) {
                         const uint32_t s_hi = st + L.off_bhi + t * SPART, s_lo = st + L.off_blo + t * SPART;
@@ -413,7 +441,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                              smem_u32(&bar_drain))
                          : "memory");
             if (!mbar_wait(smem_u32(&bar_drain), 0, DRAIN_LIMIT)) ok = false;
-            if (!ok) atomicOr(&a.flags[1], 1);
+            if (!ok) atomicOr(&flags[1], 1);
         }
     } else if (warp < 2 + CONVW) {
         // ---------------------------------------------------------- converters
@@ -422,8 +450,11 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
         const int cset = (tid - 64) >> 7;
         constexpr int ncols = NT * BN;
         int it = 0;
-        for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x) {
-            const int tile = col_tile(a, w / a.nrb);
+        for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+            const int g = group_of(G, w);
+            const TcArgs& a = G.p[g];
+            const int nch = a.nch1 + a.nch2;
+            const int tile = col_tile(a, (w - G.wstart[g]) / a.nrb);
             float subv[NT];
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
@@ -432,7 +463,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
             }
             for (int c = 0; c < nch; ++c, ++it) {
                 const int s = it % L.nst, k = it / L.nst;
-                if (!mbar_wait(smem_u32(&bar_full[s]), k & 1, a.limit)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&bar_full[s]), k & 1, limit)) { ok = false; break; }
                 uint8_t* st = smem + s * L.stage;
                 const float* stg = (const float*)(st + L.off_stg);
                 const bool seg1 = c < a.nch1;
@@ -479,21 +510,24 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
                 mbar_arrive(smem_u32(&bar_conv[s]));
             }
         }
-        if (!ok && tid == 64) atomicOr(&a.flags[1], 1);
+        if (!ok && tid == 64) atomicOr(&flags[1], 1);
     } else {
         // ---------------------------------------------------------- epilogue
         const int q = warp & 3;                        // TMEM lane quadrant of this warp
         const int grp = (warp - 2 - CONVW) >> 2;       // 16-row groups grp, grp + EG, ...
         int wc = 0;
-        for (int w = blockIdx.x; w < a.nwork && ok; w += gridDim.x, ++wc) {
-            const int tl = w / a.nrb, rb = w - tl * a.nrb;
+        for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++wc) {
+            const int g = group_of(G, w);
+            const TcArgs& a = G.p[g];
+            const int lw = w - G.wstart[g];
+            const int tl = lw / a.nrb, rb = lw - tl * a.nrb;
             const int tile = col_tile(a, tl);
             const int rbase = rb * a.rr;                          // first operator row of the block
             const int mr = min(a.rr, a.M - rbase);                // real rows in the block
             const int b = wc % L.tbuf;
             // the give-up decision is taken by the whole warp: the tensor-memory loads
             // below are .sync.aligned and must be executed by all 32 lanes or none
-            const bool got = mbar_wait(smem_u32(&bar_tfull[b]), (wc / L.tbuf) & 1, a.limit);
+            const bool got = mbar_wait(smem_u32(&bar_tfull[b]), (wc / L.tbuf) & 1, limit);
             if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
@@ -575,7 +609,7 @@ tc_gemm_kernel(const TcArgs a, const __grid_constant__ CUtensorMap tm1, const __
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(smem_u32(&bar_tempty[b]));
         }
-        if (!ok && tid == 64 + 32 * CONVW) atomicOr(&a.flags[1], 1);
+        if (!ok && tid == 64 + 32 * CONVW) atomicOr(&flags[1], 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -743,56 +777,45 @@ cudaError_t prepare() {
 }
 
 template <int KIND>
-static cudaError_t launch(const TcArgs& a, int v, const CUtensorMap& m1, const CUtensorMap& m2, int nsm,
-                          cudaStream_t st) {
-    const int gd = a.epi == 2 ? a.gD : 0;
+static cudaError_t launch(const TcGroup& G, int v, int gd, int nsm, cudaStream_t st) {
     const Variant V = variant_of(gd, v);
-    const Layout L = make_layout(KIND, a.nrp, V.nt);
+    const Layout L = make_layout(KIND, G.nrp, V.nt);
     if (!g_attr[KIND]) {
         cudaError_t e = set_smem<KIND>();
         if (e != cudaSuccess) return e;
         g_attr[KIND] = true;
     }
-    const int grid = std::min(a.nwork, nsm);
+    const int grid = std::min(G.wstart[G.ng], nsm);
     const int nth = nthreads_for(V.cw, V.eg);
     const void* f = gd == 0 ? variant_fn<KIND, 0>(v) : gd == 2 ? variant_fn<KIND, 2>(v) : variant_fn<KIND, 3>(v);
     if (!f) return cudaErrorInvalidValue;
-    void* args[3] = {(void*)&a, (void*)&m1, (void*)&m2};
+    void* args[1] = {(void*)&G};
     return cudaLaunchKernel(f, dim3(grid), dim3(nth), args, (size_t)L.smem, st);
 }
 
-cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
-                 float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
-                 cudaStream_t st, const GradXform* gx, const RkFuse* rk, long long wait_limit, int variant) {
-    if (!g_nsm) {
-        cudaError_t e = prepare();
-        if (e != cudaSuccess) return e;
-    }
-    if (N % BN != 0 || M <= 0) return cudaErrorInvalidValue;
+// The arguments and tensor maps of one problem of a launch with nt subtiles.
+static cudaError_t build_problem(int kind, int epi, const GemmProblem& q, int nt, SubRef sub, int* flags,
+                                 long long wait_limit, TcArgs& a, CUtensorMap& m1, CUtensorMap& m2) {
     const int esz = kind == 0 ? 4 : 2, kce = ROWB / esz;
-    if (gx && (gx->ndims < 2 || gx->ndims > 3 || M != gx->ndims * gx->nupts || !gx->smat || !rcp))
+    const GradXform* gx = q.gx;
+    const RkFuse* rk = q.rk;
+    if (q.N % BN != 0 || q.M <= 0) return cudaErrorInvalidValue;
+    if (gx && (gx->ndims < 2 || gx->ndims > 3 || q.M != gx->ndims * gx->nupts || !gx->smat || !q.rcp))
         return cudaErrorInvalidValue;
-    const RowBlocks B = row_blocks(M, gx ? gx->ndims : 1);
-    const int gdv = gx ? gx->ndims : 0;
-    if (variant < 0) variant = subtiles_for(B.nrp) == 2 ? 1 : 0;      // the default rule
-    if (variant >= (gdv ? NVG : NV0)) return cudaErrorInvalidValue;
-    const Variant V = variant_of(gdv, variant);
-    if (V.nt == 2 && B.nrp > 128) return cudaErrorInvalidValue;       // two accumulators per buffer must fit
-    const int nt = V.nt;
-    TcArgs a;
-    a.M = M;
+    const RowBlocks B = row_blocks(q.M, gx ? gx->ndims : 1);
+    a.M = q.M;
     a.nrb = B.nrb;
     a.rr = B.rr;
     a.nrp = B.nrp;
-    a.nch1 = (K1 + kce - 1) / kce;
-    a.nch2 = K2 > 0 ? (K2 + kce - 1) / kce : 0;
-    a.subseg = subseg;
-    a.Apack = (const uint8_t*)Apack;
-    a.N = N;
-    a.ld = ld;
-    a.C = C;
+    a.nch1 = (q.K1 + kce - 1) / kce;
+    a.nch2 = q.K2 > 0 ? (q.K2 + kce - 1) / kce : 0;
+    a.subseg = q.subseg;
+    a.Apack = (const uint8_t*)q.Apack;
+    a.N = q.N;
+    a.ld = q.ld;
+    a.C = q.C;
     a.epi = epi;
-    a.rcp = rcp;
+    a.rcp = q.rcp;
     a.sub0 = sub.v[0];
     a.sub1 = sub.v[1];
     a.sub2 = sub.v[2];
@@ -800,7 +823,7 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
     a.sub4 = sub.v[4];
     a.flags = flags;
     a.limit = wait_limit > 0 ? wait_limit : 4000000000LL;   // SM clock cycles per wait (default ~2 s)
-    a.ntiles = (int)((N + nt * BN - 1) / (nt * BN));
+    a.ntiles = (int)((q.N + nt * BN - 1) / (nt * BN));
     a.nwork = a.ntiles * a.nrb;
     a.smat = gx ? gx->smat : nullptr;
     a.gD = gx ? gx->ndims : 0;
@@ -812,7 +835,7 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
     a.rk_nelem = 0;
     if (rk) {
         if (nt != 2) return cudaErrorInvalidValue;          // fused only into the two-subtile kernels
-        if (gx || !rcp || rk->mode < 0 || rk->mode > 2 || !rk->u || !rk->acc || (rk->mode < 2 && !rk->tmp))
+        if (gx || !q.rcp || rk->mode < 0 || rk->mode > 2 || !rk->u || !rk->acc || (rk->mode < 2 && !rk->tmp))
             return cudaErrorInvalidValue;
         a.epi = 3;
         a.rk_mode = rk->mode;
@@ -825,17 +848,59 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
     }
     // the variables of one element range share the metric terms (adj(J), 1/J)
     // through L2: their column tiles run on neighbouring CTAs at the same time
+    const int64_t ld = q.ld, N = q.N;
     a.vinter = (gx && gx->nvars > 1 && ld % (nt * BN) == 0 && N == (int64_t)gx->nvars * ld) ? gx->nvars : 0;
-    if (!gx && rcp && (epi == 1 || rk) && ld % (nt * BN) == 0 && N % ld == 0 && N / ld > 1) a.vinter = (int)(N / ld);
-    CUtensorMap m1, m2;
-    if (!make_map(&m1, B1, N, K1, kce, nt)) return cudaErrorInvalidValue;
-    if (K2 > 0) {
-        if (!make_map(&m2, B2, N, K2, kce, nt)) return cudaErrorInvalidValue;
+    if (!gx && q.rcp && (epi == 1 || rk) && ld % (nt * BN) == 0 && N % ld == 0 && N / ld > 1) a.vinter = (int)(N / ld);
+    if (!make_map(&m1, q.B1, N, q.K1, kce, nt)) return cudaErrorInvalidValue;
+    if (q.K2 > 0) {
+        if (!make_map(&m2, q.B2, N, q.K2, kce, nt)) return cudaErrorInvalidValue;
     } else {
         m2 = m1;
     }
-    return kind == 0 ? launch<0>(a, variant, m1, m2, g_nsm, st) : launch<1>(a, variant, m1, m2, g_nsm, st);
+    return cudaSuccess;
 }
+
+cudaError_t gemm_group(int kind, int epi, const GemmProblem* probs, int n, SubRef sub, int* flags, cudaStream_t st,
+                       long long wait_limit, int variant) {
+    if (!g_nsm) {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+    }
+    if (n < 1 || n > MAXG) return cudaErrorInvalidValue;
+    // one epilogue class for the whole group
+    const int gd = probs[0].gx ? probs[0].gx->ndims : 0;
+    int nrp = 0;
+    for (int i = 0; i < n; ++i) {
+        if ((probs[i].gx ? probs[i].gx->ndims : 0) != gd || (probs[i].rk != nullptr) != (probs[0].rk != nullptr))
+            return cudaErrorInvalidValue;
+        nrp = std::max(nrp, row_blocks(probs[i].M, gd ? gd : 1).nrp);
+    }
+    if (variant < 0) variant = subtiles_for(nrp) == 2 ? 1 : 0;          // the default rule
+    if (variant >= (gd ? NVG : NV0)) return cudaErrorInvalidValue;
+    const Variant V = variant_of(gd, variant);
+    if (V.nt == 2 && nrp > 128) return cudaErrorInvalidValue;          // two accumulators per buffer must fit
+    TcGroup G;
+    std::memset(&G, 0, sizeof(G));
+    G.ng = n;
+    G.nrp = nrp;
+    G.wstart[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = build_problem(kind, epi, probs[i], V.nt, sub, flags, wait_limit, G.p[i], G.m[2 * i],
+                                      G.m[2 * i + 1]);
+        if (e != cudaSuccess) return e;
+        G.wstart[i + 1] = G.wstart[i] + G.p[i].nwork;
+    }
+    return kind == 0 ? launch<0>(G, variant, gd, g_nsm, st) : launch<1>(G, variant, gd, g_nsm, st);
+}
+
+cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float* B1, const float* B2, int64_t N,
+                 float* C, int epi, const float* rcp, int64_t ld, int subseg, SubRef sub, int* flags,
+                 cudaStream_t st, const GradXform* gx, const RkFuse* rk, long long wait_limit, int variant) {
+    const GemmProblem q{M, K1, K2, Apack, B1, B2, N, C, rcp, ld, subseg, gx, rk};
+    return gemm_group(kind, epi, &q, 1, sub, flags, st, wait_limit, variant);
+}
+
+int group_max() { return MAXG; }
 
 }  // namespace tc
 }  // namespace fr

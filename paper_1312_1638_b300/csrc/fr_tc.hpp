@@ -66,6 +66,27 @@ cudaError_t gemm(int kind, int M, int K1, int K2, const void* Apack, const float
                  cudaStream_t st, const GradXform* gx = nullptr, const RkFuse* rk = nullptr,
                  long long wait_limit = 0, int variant = -1);
 
+// One problem of a grouped launch: C[M x N] = A [B1; B2] with the arguments
+// of gemm() (epi and the variant are the group's).
+struct GemmProblem {
+    int M, K1, K2;
+    const void* Apack;
+    const float *B1, *B2;
+    int64_t N;
+    float* C;
+    const float* rcp;
+    int64_t ld;
+    int subseg;
+    const GradXform* gx;
+    const RkFuse* rk;
+};
+// The same operator product of up to group_max() element blocks in one
+// persistent launch (one work list; all with or all without gx, all with or
+// all without rk, gx of one dimension).  The variant must fit every problem.
+cudaError_t gemm_group(int kind, int epi, const GemmProblem* probs, int n, SubRef sub, int* flags, cudaStream_t st,
+                       long long wait_limit = 0, int variant = -1);
+int group_max();
+
 // A kernel variant: 128-column subtiles per work item (1 or 2), converter
 // warps and epilogue warp groups.
 struct Variant {

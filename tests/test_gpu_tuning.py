@@ -125,3 +125,37 @@ def test_tuned_rk4_equals_default_rk4(torch):
     torch.cuda.synchronize()
     assert torch.equal(a[0], b[0])
     assert s.sync_status() == fr.OK and t.sync_status() == fr.OK
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_grouped_launches_match_per_block_launches(torch, prec):
+    """On a mixed mesh (quadrilaterals and triangles) each tensor-core product
+    runs as one launch over both blocks' work items: the same bits as one
+    launch per block, for the right-hand side and for graph-replayed RK4, with
+    one launch per product and stage (the two gradient interpolations of both
+    blocks included) instead of one per block."""
+    from paper_1312_1638_b300 import fr
+    m, s = _solver(fr, "mixed", prec)
+    _, t = _solver(fr, "mixed", prec)
+    t.set_option("group_blocks", 0)
+    u = _state(torch, s, m)
+    s.profile_enable(True)
+    t.profile_enable(True)
+    a, b = _rhs(torch, s, u), _rhs(torch, t, u)
+    ps, pt = s.profile_read(), t.profile_read()
+    for k in ("disu_gemm", "tgradu_gemm", "gradfpts_gemm", "tdivf_gemm"):
+        assert ps[k][0] == 1, (k, ps[k])
+        assert pt[k][0] == 2, (k, pt[k])                  # per block (the gradient's 2 directions in one)
+    for x, y, blk in zip(a, b, m.blocks):
+        ne = blk.nodes.shape[0]
+        assert torch.equal(x[:, :, :ne], y[:, :, :ne])
+    s.profile_enable(False)
+    t.profile_enable(False)
+    ua, ub = [x.clone() for x in u], [x.clone() for x in u]
+    s.rk4(ua, 1e-6, 3)
+    t.rk4(ub, 1e-6, 3)
+    torch.cuda.synchronize()
+    for x, y, blk in zip(ua, ub, m.blocks):
+        ne = blk.nodes.shape[0]
+        assert torch.equal(x[:, :, :ne], y[:, :, :ne])
+    assert s.sync_status() == fr.OK and t.sync_status() == fr.OK
