@@ -261,9 +261,11 @@ fr_status fr_rk4_host(fr_ctx* ctx, void* const* u, double dt, int nsteps, void* 
  * kernel variants, which differ in how many 128-column subtiles a work item
  * holds (nt) and how many warps convert the state operand (cw) or drain the
  * accumulators (eg).  fr_autotune times every variant that fits each product
- * of each block: 1 + reps RK4 steps of size 0 on a private copy of u (device
- * memory allocated and freed by the call; u is not modified), kernels timed
- * by CUDA events, and keeps the fastest in the context.  It synchronises
+ * of each block (of all blocks together when they run as one launch, see the
+ * option "group_blocks"): 1 + reps RK4 steps of size 0 on a private copy of u
+ * (device memory allocated and freed by the call; u is not modified), in two
+ * passes over the variants, kernels timed by CUDA events, and keeps the
+ * fastest in the context.  It synchronises
  * `stream`.  On the FP64 / FP32 paths it does nothing.
  * fr_get_tuning writes the context's choices as text,
  * "b0:disu=1.8.3,tgradu=1.4.4,gradfpts=1.8.3,tdivf=2.8.2;b1:..." (nt.cw.eg,
@@ -280,9 +282,9 @@ fr_status fr_set_tuning(fr_ctx* ctx, const char* text);
 /* Context options (not in the paper): "graphs" (default 1) enables the RK4-step CUDA graph of
  * fr_rk4.  "group_blocks" (default 1): on the tensor-core paths each operator
  * product of a mesh with 2 to 4 element blocks (a mixed mesh) runs as one
- * persistent launch over the work items of every block, and the D
- * interpolations of the gradient (Eq. gradufpts) run as one launch; 0 gives
- * every block its own launches.  Changing it drops the captured RK4 step;
+ * persistent launch over the work items of every block (the D
+ * interpolations of the gradient, Eq. gradufpts, of every block included);
+ * 0 gives every block its own launches.  Changing it drops the captured RK4 step;
  * results are the same bits either way.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
  * operator GEMMs gives up: the kernel then drains its own copies and MMAs,

@@ -312,7 +312,9 @@ __device__ __forceinline__ float sub_of(const TcArgs& a, int64_t v) {
     return v == 0 ? a.sub0 : v == 1 ? a.sub1 : v == 2 ? a.sub2 : v == 3 ? a.sub3 : a.sub4;
 }
 
-template <int KIND, int NT, int GD, int CONVW, int EG>
+// MULTI: the launch serves several problems (found per work item); a
+// single-problem launch reads its arguments at fixed parameter offsets
+template <int KIND, int NT, int GD, int CONVW, int EG, bool MULTI>
 __global__ void __launch_bounds__(nthreads_for(CONVW, EG), 1)
 tc_gemm_kernel(const __grid_constant__ TcGroup G) {
     extern __shared__ uint8_t smem_raw[];
@@ -357,7 +359,7 @@ tc_gemm_kernel(const __grid_constant__ TcGroup G) {
         if (lane == 0) {
             int it = 0;
             for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-                const int g = group_of(G, w);
+                const int g = (MULTI ? group_of(G, w) : 0);
                 const TcArgs& a = G.p[g];
                 const int lw = w - G.wstart[g], nch = a.nch1 + a.nch2;
                 const int tl = lw / a.nrb, rb = lw - tl * a.nrb;
@@ -399,7 +401,7 @@ tc_gemm_kernel(const __grid_constant__ TcGroup G) {
         if (lane == 0) {
             int it = 0, wc = 0;
             for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++wc) {
-                const TcArgs& a = G.p[group_of(G, w)];
+                const TcArgs& a = G.p[(MULTI ? group_of(G, w) : 0)];
                 const int nch = a.nch1 + a.nch2;
                 const uint32_t id = instr_desc<KIND>(a.nrp);
                 const int b = wc % L.tbuf;
@@ -451,7 +453,7 @@ tc_gemm_kernel(const __grid_constant__ TcGroup G) {
         constexpr int ncols = NT * BN;
         int it = 0;
         for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-            const int g = group_of(G, w);
+            const int g = (MULTI ? group_of(G, w) : 0);
             const TcArgs& a = G.p[g];
             const int nch = a.nch1 + a.nch2;
             const int tile = col_tile(a, (w - G.wstart[g]) / a.nrb);
@@ -517,7 +519,7 @@ tc_gemm_kernel(const __grid_constant__ TcGroup G) {
         const int grp = (warp - 2 - CONVW) >> 2;       // 16-row groups grp, grp + EG, ...
         int wc = 0;
         for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++wc) {
-            const int g = group_of(G, w);
+            const int g = (MULTI ? group_of(G, w) : 0);
             const TcArgs& a = G.p[g];
             const int lw = w - G.wstart[g];
             const int tl = lw / a.nrb, rb = lw - tl * a.nrb;
@@ -565,28 +567,32 @@ tc_gemm_kernel(const __grid_constant__ TcGroup G) {
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if constexpr (NT == 2) {
                       if (col_ok && a.epi == 3) {
-                        // fused RK stage: k never goes to memory.  All 16 rows of u / acc
-                        // are loaded before the first store (the stores may alias them
-                        // as far as the compiler knows).
-                        float uu[16], aa[16];
+                        // fused RK stage: k never goes to memory.  Rows go in two halves
+                        // of 8 (fewer live registers); the 8 rows of u / acc of a half are
+                        // loaded before its first store (the stores may alias them as far
+                        // as the compiler knows).
                         const int64_t i0 = i_col + (int64_t)r0 * a.N;
                         const bool need_u = a.rk_mode != 2, need_acc = a.rk_mode != 0;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const bool in = r0 + j < mr;
-                            uu[j] = (in && need_u) ? __ldg(a.rk_u + i0 + (int64_t)j * a.N) : 0.f;
-                            aa[j] = (in && need_acc) ? a.rk_acc[i0 + (int64_t)j * a.N] : 0.f;
-                        }
+                        for (int h = 0; h < 16; h += 8) {
+                            float uu[8], aa[8];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (r0 + j < mr) {
-                                const float k = -__uint_as_float(r[j]) * rc[j];
-                                const int64_t i = i0 + (int64_t)j * a.N;
-                                if (a.rk_mode == 2) {
-                                    a.rk_u[i] = aa[j] + a.rk_a * k;
-                                } else {
-                                    a.rk_acc[i] = (a.rk_mode == 0 ? uu[j] : aa[j]) + a.rk_a * k;
-                                    a.rk_tmp[i] = uu[j] + a.rk_b * k;
+                            for (int j = 0; j < 8; ++j) {
+                                const bool in = r0 + h + j < mr;
+                                uu[j] = (in && need_u) ? __ldg(a.rk_u + i0 + (int64_t)(h + j) * a.N) : 0.f;
+                                aa[j] = (in && need_acc) ? a.rk_acc[i0 + (int64_t)(h + j) * a.N] : 0.f;
+                            }
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                if (r0 + h + j < mr) {
+                                    const float k = -__uint_as_float(r[h + j]) * rc[h + j];
+                                    const int64_t i = i0 + (int64_t)(h + j) * a.N;
+                                    if (a.rk_mode == 2) {
+                                        a.rk_u[i] = aa[j] + a.rk_a * k;
+                                    } else {
+                                        a.rk_acc[i] = (a.rk_mode == 0 ? uu[j] : aa[j]) + a.rk_a * k;
+                                        a.rk_tmp[i] = uu[j] + a.rk_b * k;
+                                    }
                                 }
                             }
                         }
@@ -716,37 +722,44 @@ constexpr int NV0 = 6, NVG = 5;
 static const Variant kVar0[NV0] = {{1, 8, 3}, {2, 8, 2}, {1, 8, 2}, {1, 12, 2}, {2, 4, 3}, {1, 4, 3}};
 static const Variant kVarG[NVG] = {{1, 4, 4}, {2, 4, 4}, {1, 8, 3}, {1, 8, 4}, {2, 8, 3}};
 
-template <int KIND, int GD>
-static const void* variant_fn(int v) {
+template <int KIND, int GD, bool M>
+static const void* variant_fn_m(int v) {
     if constexpr (GD == 0) {
         switch (v) {
-            case 0: return (const void*)tc_gemm_kernel<KIND, 1, 0, 8, 3>;
-            case 1: return (const void*)tc_gemm_kernel<KIND, 2, 0, 8, 2>;
-            case 2: return (const void*)tc_gemm_kernel<KIND, 1, 0, 8, 2>;
-            case 3: return (const void*)tc_gemm_kernel<KIND, 1, 0, 12, 2>;
-            case 4: return (const void*)tc_gemm_kernel<KIND, 2, 0, 4, 3>;
-            case 5: return (const void*)tc_gemm_kernel<KIND, 1, 0, 4, 3>;
+            case 0: return (const void*)tc_gemm_kernel<KIND, 1, 0, 8, 3, M>;
+            case 1: return (const void*)tc_gemm_kernel<KIND, 2, 0, 8, 2, M>;
+            case 2: return (const void*)tc_gemm_kernel<KIND, 1, 0, 8, 2, M>;
+            case 3: return (const void*)tc_gemm_kernel<KIND, 1, 0, 12, 2, M>;
+            case 4: return (const void*)tc_gemm_kernel<KIND, 2, 0, 4, 3, M>;
+            case 5: return (const void*)tc_gemm_kernel<KIND, 1, 0, 4, 3, M>;
         }
     } else {
         switch (v) {
-            case 0: return (const void*)tc_gemm_kernel<KIND, 1, GD, 4, 4>;
-            case 1: return (const void*)tc_gemm_kernel<KIND, 2, GD, 4, 4>;
-            case 2: return (const void*)tc_gemm_kernel<KIND, 1, GD, 8, 3>;
-            case 3: return (const void*)tc_gemm_kernel<KIND, 1, GD, 8, 4>;
-            case 4: return (const void*)tc_gemm_kernel<KIND, 2, GD, 8, 3>;
+            case 0: return (const void*)tc_gemm_kernel<KIND, 1, GD, 4, 4, M>;
+            case 1: return (const void*)tc_gemm_kernel<KIND, 2, GD, 4, 4, M>;
+            case 2: return (const void*)tc_gemm_kernel<KIND, 1, GD, 8, 3, M>;
+            case 3: return (const void*)tc_gemm_kernel<KIND, 1, GD, 8, 4, M>;
+            case 4: return (const void*)tc_gemm_kernel<KIND, 2, GD, 8, 3, M>;
         }
     }
     return nullptr;
 }
 
+template <int KIND, int GD>
+static const void* variant_fn(int v, bool multi) {
+    return multi ? variant_fn_m<KIND, GD, true>(v) : variant_fn_m<KIND, GD, false>(v);
+}
+
 template <int KIND>
 static cudaError_t set_smem() {
-    for (int gd : {0, 2, 3})
-        for (int v = 0; v < (gd ? NVG : NV0); ++v) {
-            const void* f = gd == 0 ? variant_fn<KIND, 0>(v) : gd == 2 ? variant_fn<KIND, 2>(v) : variant_fn<KIND, 3>(v);
-            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
-            if (e != cudaSuccess) return e;
-        }
+    for (int multi = 0; multi < 2; ++multi)
+        for (int gd : {0, 2, 3})
+            for (int v = 0; v < (gd ? NVG : NV0); ++v) {
+                const void* f = gd == 0 ? variant_fn<KIND, 0>(v, multi) : gd == 2 ? variant_fn<KIND, 2>(v, multi)
+                                                                                  : variant_fn<KIND, 3>(v, multi);
+                cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 
@@ -787,7 +800,9 @@ static cudaError_t launch(const TcGroup& G, int v, int gd, int nsm, cudaStream_t
     }
     const int grid = std::min(G.wstart[G.ng], nsm);
     const int nth = nthreads_for(V.cw, V.eg);
-    const void* f = gd == 0 ? variant_fn<KIND, 0>(v) : gd == 2 ? variant_fn<KIND, 2>(v) : variant_fn<KIND, 3>(v);
+    const bool multi = G.ng > 1;
+    const void* f = gd == 0 ? variant_fn<KIND, 0>(v, multi) : gd == 2 ? variant_fn<KIND, 2>(v, multi)
+                                                                    : variant_fn<KIND, 3>(v, multi);
     if (!f) return cudaErrorInvalidValue;
     void* args[1] = {(void*)&G};
     return cudaLaunchKernel(f, dim3(grid), dim3(nth), args, (size_t)L.smem, st);
