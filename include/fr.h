@@ -285,7 +285,15 @@ fr_status fr_set_tuning(fr_ctx* ctx, const char* text);
  * persistent launch over the work items of every block (the D
  * interpolations of the gradient, Eq. gradufpts, of every block included);
  * 0 gives every block its own launches.  Changing it drops the captured RK4 step;
- * results are the same bits either way.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
+ * results are the same bits either way.  "structured_interp" (default 1):
+ * where every row of an element type's
+ * interpolation operator M0 (App. A) has at most 8 nonzeros (quadrilaterals
+ * and hexahedra: the p+1 solution points on the line through a face point;
+ * entries below 1e-15 of their row's largest are dropped), the products with
+ * M0 (U^(f) and the gradient at flux points) run as a structured kernel with
+ * FP32 / FP64 multiply-adds of those entries, in every precision (they need
+ * no split: FP32 multiply-adds are as accurate as the split products); 0
+ * uses the dense operator products.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
  * operator GEMMs gives up: the kernel then drains its own copies and MMAs,
  * returns, and fr_sync_status reports FR_ERR_TIMEOUT; the context stays

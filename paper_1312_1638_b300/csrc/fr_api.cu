@@ -1,6 +1,7 @@
 // C ABI of the FR library: context set-up (host work + device upload) and the
 // stream-ordered entry points declared in include/fr.h.
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <cstdio>
 #include <cstring>
@@ -171,6 +172,35 @@ void upload_device(fr_ctx* c) {
             CK(cudaMemset(B.Qf, 0, (size_t)d * nf * V * ld * rs));
         }
         B.opM0 = upload_real(c, el.M0, fp64);
+        {
+            // structured form of M0: the nonzeros of every row, if no row has more
+            // than 8 (entries below 1e-15 of their row's largest are rounding of a
+            // vanishing Lagrange factor and are dropped)
+            std::vector<std::vector<std::pair<int, double>>> rows((size_t)nf);
+            int nnz = 0;
+            for (int64_t r = 0; r < nf; ++r) {
+                double mx = 0;
+                for (int64_t k = 0; k < nu; ++k) mx = std::max(mx, std::fabs(el.M0[(size_t)r * nu + k]));
+                for (int64_t k = 0; k < nu; ++k) {
+                    const double v = el.M0[(size_t)r * nu + k];
+                    if (std::fabs(v) > 1e-15 * mx) rows[r].push_back({(int)k, v});
+                }
+                nnz = std::max(nnz, (int)rows[r].size());
+            }
+            if (nnz > 0 && nnz <= 8 && fr::interp_prepare((int)nu, (int)nf, nnz, fp64) == cudaSuccess) {
+                std::vector<int> idx((size_t)nf * nnz, 0);
+                std::vector<double> val((size_t)nf * nnz, 0.0);
+                for (int64_t r = 0; r < nf; ++r)
+                    for (size_t j = 0; j < rows[r].size(); ++j) {
+                        idx[(size_t)r * nnz + j] = rows[r][j].first;
+                        val[(size_t)r * nnz + j] = rows[r][j].second;
+                    }
+                B.sp_nnz = nnz;
+                B.sp_idx = (int*)upload(c, idx);
+                B.sp_val = upload_real(c, val, fp64);
+            }
+            (void)cudaGetLastError();
+        }
         B.opQ = upload_real(c, hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu), fp64);
         B.opR = upload_real(c, hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu), fp64);
         {
@@ -961,6 +991,13 @@ fr_status fr_autotune(fr_ctx* ctx, void* const* u, int reps, void* stream) {
         for (int slot = 0; slot < fr::TUNE_N; ++slot)
             for (size_t b = 0; b < (grouped ? 1 : D.blocks.size()); ++b) {
                 fr::DevBlock& B = D.blocks[b];
+                if ((slot == fr::TUNE_DISU || slot == fr::TUNE_GRADFPTS) && D.structured_interp) {
+                    // products on the structured kernel have no variants to time
+                    bool dense = B.sp_nnz <= 0;
+                    if (grouped)
+                        for (const auto& B2 : D.blocks) dense = dense || B2.sp_nnz <= 0;
+                    if (!dense) continue;
+                }
                 int cand[8];
                 int nc = fr::tune_candidates(D, B, slot, cand);
                 if (grouped) {
@@ -1104,6 +1141,11 @@ fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value) {
     if (!ctx || !name) return FR_ERR_ARG;
     if (std::string(name) == "graphs") {
         ctx->use_graphs = value != 0;
+        return FR_OK;
+    }
+    if (std::string(name) == "structured_interp") {
+        ctx->dev.structured_interp = value != 0;
+        drop_graph(ctx);
         return FR_OK;
     }
     if (std::string(name) == "group_blocks") {

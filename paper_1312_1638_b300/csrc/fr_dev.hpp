@@ -54,6 +54,11 @@ struct DevBlock {
     void* dp_y = nullptr;          // DOPRI5: stage input / new solution
     // tensor-core kernel variant of each operator product (TUNE_*; -1: the default rule)
     int tune[4] = {-1, -1, -1, -1};
+    // M0 in structured form (every row with at most sp_nnz <= 8 nonzeros; 0: dense):
+    // column indices [nfpts][sp_nnz] and values (T) of each row, zero-padded
+    int sp_nnz = 0;
+    int* sp_idx = nullptr;
+    void* sp_val = nullptr;
 };
 
 // operator products whose kernel variant can be chosen (DevBlock::tune)
@@ -131,6 +136,7 @@ struct DevCtx {
     int* flags = nullptr;          // [0] non-finite seen, [1] timeout
     long long tc_wait_limit = 0;   // tensor-core GEMM wait limit in SM cycles (0: about two seconds)
     bool group_blocks = true;      // tensor-core products of all element blocks in one launch per stage
+    bool structured_interp = true; // M0 products through the structured kernel where M0 allows
     double* partial = nullptr;     // reduction scratch
     int64_t npartial = 0;
 };
@@ -176,6 +182,9 @@ cudaError_t launch_sum_weighted(DevCtx& c, void* const* u, double* host_out, cud
 cudaError_t launch_check_finite(DevCtx& c, void* const* u, cudaStream_t st);
 // FP32 and FP64 FMA throughput of the current device (TFLOP/s), synchronous
 cudaError_t measure_fma(double* fp32_tflops, double* fp64_tflops);
+// raise the structured interpolation kernel's shared-memory limit for an
+// element type (nupts solution, nfpts flux points, nnz nonzeros per row)
+cudaError_t interp_prepare(int nupts, int nfpts, int nnz, bool fp64);
 // look up the allocation-free RK4's fixed device array on `device` (current),
 // reserving it there; failures are left for fr_rk4_noalloc to report
 void noalloc_prepare(int device);

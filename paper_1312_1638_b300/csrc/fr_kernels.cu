@@ -101,10 +101,134 @@ gemm_kernel(int M, int K, int K1, const T* __restrict__ A, const T* __restrict__
     }
 }
 
+// FP32 operator product on the CUDA cores.  256 threads: 16 column groups
+// (8 columns each, as two float4 64 columns apart, so that a warp's shared
+// reads are conflict-free) x 16 row groups (RM rows each): a 16 RM x 128
+// tile.  K runs in chunks of 16, double-buffered: the next chunk's operator
+// and state values are loaded into registers while the current chunk is
+// multiplied out of shared memory.  The operator tile is stored transposed
+// ([k][row]: the row-group reads are broadcasts), the state tile as is.
+template <int RM>
+__global__ void __launch_bounds__(256, 2)
+gemm_f32_kernel(int M, int K, int K1, const float* __restrict__ A, const float* __restrict__ B1,
+                const float* __restrict__ B2, int64_t N, float* __restrict__ C, int epi,
+                const float* __restrict__ rcp, int64_t ld, int ks0, int ks1, Sub<float> sub) {
+    constexpr int MB = 16 * RM, TN = 128, KC = 16;
+    constexpr int AE = (MB * KC + 255) / 256;            // operator values per thread and chunk
+    __shared__ __align__(16) float As[2][KC][MB];
+    __shared__ __align__(16) float Bs[2][KC][TN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t col0 = (int64_t)blockIdx.x * TN;
+    // this thread's share of a state chunk: rows kb, kb + 8 at columns 4 cb .. 4 cb + 3
+    const int cb = tid & 31, kb = tid >> 5;
+    const int64_t gcol = col0 + 4 * cb;
+    const bool colok = gcol < N;                          // N and col0 are multiples of 4
+    const float subv = colok ? sub.v[gcol / ld] : 0.f;
+    for (int m0 = 0; m0 < M; m0 += MB) {
+        float acc[RM][8];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        float ar[AE];
+        float4 br[2];
+        auto load = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < AE; ++q) {
+                const int e = tid + 256 * q, r = e % MB, kk = e / MB;
+                const int gr = m0 + r, gk = k0 + kk;
+                ar[q] = (e < MB * KC && gr < M && gk < K) ? __ldg(A + (int64_t)gr * K + gk) : 0.f;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gk = k0 + kb + 8 * h;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (colok && gk < K) {
+                    const float* src = gk < K1 ? B1 + (int64_t)gk * N : B2 + (int64_t)(gk - K1) * N;
+                    v = __ldg((const float4*)(src + gcol));
+                    if (gk >= ks0 && gk < ks1) { v.x -= subv; v.y -= subv; v.z -= subv; v.w -= subv; }
+                }
+                br[h] = v;
+            }
+        };
+        auto store = [&](int buf) {
+#pragma unroll
+            for (int q = 0; q < AE; ++q) {
+                const int e = tid + 256 * q;
+                if (e < MB * KC) As[buf][e / MB][e % MB] = ar[q];
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) *(float4*)&Bs[buf][kb + 8 * h][4 * cb] = br[h];
+        };
+        load(0);
+        store(0);
+        __syncthreads();
+        int buf = 0;
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            const bool more = k0 + KC < K;
+            if (more) load(k0 + KC);
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                float a[RM];
+#pragma unroll
+                for (int i = 0; i < RM; ++i) a[i] = As[buf][kk][ty * RM + i];
+                const float4 b0 = *(const float4*)&Bs[buf][kk][4 * tx];
+                const float4 b1 = *(const float4*)&Bs[buf][kk][64 + 4 * tx];
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < RM; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+            if (more) store(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+#pragma unroll
+        for (int i = 0; i < RM; ++i) {
+            const int row = m0 + ty * RM + i;
+            if (row >= M) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t col = col0 + 64 * h + 4 * tx;
+                if (col >= N) continue;
+                float4 v = make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+                if (epi == 1) {
+                    const float4 r = __ldg((const float4*)(rcp + (int64_t)row * ld + (col % ld)));
+                    v.x = -v.x * r.x; v.y = -v.y * r.y; v.z = -v.z * r.z; v.w = -v.w * r.w;
+                }
+                *(float4*)(C + (int64_t)row * N + col) = v;
+            }
+        }
+    }
+}
+
+// row-tile height for an M-row operator: the fewest padded rows, ties to the taller tile
+static int f32_rows_per_group(int M) {
+    int best = 8, waste = 1 << 30;
+    for (int rm : {8, 4, 2, 1}) {
+        const int mb = 16 * rm, w = (M + mb - 1) / mb * mb - M;
+        if (w < waste) { waste = w; best = rm; }
+    }
+    return best;
+}
+
 template <typename T>
 static void gemm(int M, int K, int K1, const void* A, const void* B1, const void* B2, int64_t N,
                  void* C, int epi, const void* rcp, int64_t ld, cudaStream_t st, int ks0 = 0, int ks1 = 0,
                  Sub<T> sub = Sub<T>{}) {
+    if constexpr (sizeof(T) == 4) {
+        dim3 grid((unsigned)((N + 127) / 128));
+        const float *a = (const float*)A, *b1 = (const float*)B1, *b2 = (const float*)B2, *rc = (const float*)rcp;
+        float* c = (float*)C;
+        switch (f32_rows_per_group(M)) {
+            case 1: gemm_f32_kernel<1><<<grid, 256, 0, st>>>(M, K, K1, a, b1, b2, N, c, epi, rc, ld, ks0, ks1, sub); break;
+            case 2: gemm_f32_kernel<2><<<grid, 256, 0, st>>>(M, K, K1, a, b1, b2, N, c, epi, rc, ld, ks0, ks1, sub); break;
+            case 4: gemm_f32_kernel<4><<<grid, 256, 0, st>>>(M, K, K1, a, b1, b2, N, c, epi, rc, ld, ks0, ks1, sub); break;
+            default: gemm_f32_kernel<8><<<grid, 256, 0, st>>>(M, K, K1, a, b1, b2, N, c, epi, rc, ld, ks0, ks1, sub);
+        }
+        return;
+    }
     constexpr int TN = GemmCfg<T>::TN;
     dim3 grid((unsigned)((N + TN - 1) / TN));
     if (M <= 16)
@@ -116,6 +240,128 @@ static void gemm(int M, int K, int K1, const void* A, const void* B1, const void
     else
         gemm_kernel<T, 8><<<grid, 256, 0, st>>>(M, K, K1, (const T*)A, (const T*)B1, (const T*)B2, N, (T*)C, epi,
                                                 (const T*)rcp, ld, ks0, ks1, sub);
+}
+
+// ============================================================ structured interpolation
+// C[r][c] = sum_k val[r][k] (B[idx[r][k]][c] - sub(c)) for an operator whose
+// rows have at most SP_NNZ nonzeros.  On quadrilaterals and hexahedra with
+// tensor Gauss-Legendre solution points the interpolation to a face point
+// (M0, App. A) only involves the p+1 solution points on the line through it
+// (the other Lagrange factors vanish at the nodes), so the product needs
+// (p+1) of the N^(u) multiply-adds per entry and is bound by HBM alone.
+// A CTA of 256 threads owns TN = 32 x (16 bytes) columns: it stages all K
+// rows of them in shared memory with 16-byte asynchronous copies (every
+// thread has about K/8 copies in flight, so HBM sees tens of KB per CTA at
+// once), subtracts the reference state there, and then warp w forms output
+// rows w, w + 8, ..., each lane a 16-byte vector of columns (one table entry,
+// read as a broadcast, serves that vector's multiply-adds; the stores are
+// whole 512-byte rows).  The sums run over a row's nonzeros in increasing k,
+// the order of the dense product, which adds the remaining zeros exactly.
+constexpr int SP_NNZ = 8;
+constexpr int SP_THREADS = 256;
+template <typename T> struct SpCfg;
+template <> struct SpCfg<float> { static constexpr int VW = 4; using V = float4; };
+template <> struct SpCfg<double> { static constexpr int VW = 2; using V = double2; };
+template <typename T> struct SpEnt {
+    T v;
+    int k;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void sp_fma(T a, const typename SpCfg<T>::V& x, T* acc);
+template <>
+__device__ __forceinline__ void sp_fma<float>(float a, const float4& x, float* acc) {
+    acc[0] = fmaf(a, x.x, acc[0]); acc[1] = fmaf(a, x.y, acc[1]);
+    acc[2] = fmaf(a, x.z, acc[2]); acc[3] = fmaf(a, x.w, acc[3]);
+}
+template <>
+__device__ __forceinline__ void sp_fma<double>(double a, const double2& x, double* acc) {
+    acc[0] = fma(a, x.x, acc[0]); acc[1] = fma(a, x.y, acc[1]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SP_THREADS)
+interp_sparse_kernel(int M, int K, int nnz, const int* __restrict__ idx, const T* __restrict__ val,
+                     const T* __restrict__ B, int64_t N, T* __restrict__ C, int64_t ld, Sub<T> sub, int dosub) {
+    using Cfg = SpCfg<T>;
+    using V = typename Cfg::V;
+    constexpr int VW = Cfg::VW, TN = 32 * VW, NW = SP_THREADS / 32;
+    extern __shared__ __align__(16) unsigned char sp_smem[];
+    T* tile = (T*)sp_smem;                                        // [K][TN]
+    SpEnt<T>* ent = (SpEnt<T>*)(tile + (size_t)K * TN);          // [M][nnz]
+    const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+    const int64_t col0 = (int64_t)blockIdx.x * TN;
+    for (int e = tid; e < K * 32; e += SP_THREADS) {
+        const int k = e / 32, q = e % 32;
+        cp_async16(tile + (size_t)k * TN + q * VW, B + (int64_t)k * N + col0 + q * VW);
+    }
+    for (int e = tid; e < M * nnz; e += SP_THREADS) ent[e] = SpEnt<T>{val[e], idx[e]};
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (dosub) {
+        // each thread on the vectors it copied; a 16-byte vector lies in one
+        // variable's columns (ld is a multiple of 128)
+        for (int e = tid; e < K * 32; e += SP_THREADS) {
+            const int k = e / 32, q = e % 32;
+            const T sv = sub.v[(col0 + q * VW) / ld];
+            T* t = tile + (size_t)k * TN + q * VW;
+#pragma unroll
+            for (int j = 0; j < VW; ++j) t[j] -= sv;
+        }
+    }
+    __syncthreads();
+    for (int r = w; r < M; r += NW) {
+        T acc[VW];
+#pragma unroll
+        for (int j = 0; j < VW; ++j) acc[j] = T(0);
+        const SpEnt<T>* er = ent + (size_t)r * nnz;
+        for (int j = 0; j < nnz; ++j) {
+            const SpEnt<T> en = er[j];
+            sp_fma<T>(en.v, *(const V*)(tile + (size_t)en.k * TN + lane * VW), acc);
+        }
+        V out;
+        if constexpr (VW == 4) out = V{acc[0], acc[1], acc[2], acc[3]};
+        else out = V{acc[0], acc[1]};
+        *(V*)(C + (int64_t)r * N + col0 + lane * VW) = out;
+    }
+}
+
+template <typename T>
+static size_t interp_smem(int M, int K, int nnz) {
+    return (size_t)K * 32 * SpCfg<T>::VW * sizeof(T) + (size_t)M * nnz * sizeof(SpEnt<T>);
+}
+
+// C = M0 B through the structured kernel (B.sp_nnz > 0).  N is a multiple of
+// the tile (the layout pads ld to 128 columns) and B, C start on 16 bytes;
+// anything else is rejected.
+template <typename T>
+static cudaError_t interp_sparse(const DevBlock& Bk, const void* B, int64_t N, void* C, Sub<T> sub, int dosub,
+                                 cudaStream_t st) {
+    constexpr int TN = 32 * SpCfg<T>::VW;
+    if (N % TN != 0 || Bk.ld % 128 != 0 || ((uintptr_t)B | (uintptr_t)C) % 16 != 0) return cudaErrorInvalidValue;
+    const size_t sm = interp_smem<T>(Bk.nfpts, Bk.nupts, Bk.sp_nnz);
+    interp_sparse_kernel<T><<<(unsigned)(N / TN), SP_THREADS, sm, st>>>(
+        Bk.nfpts, Bk.nupts, Bk.sp_nnz, Bk.sp_idx, (const T*)Bk.sp_val, (const T*)B, N, (T*)C, Bk.ld, sub, dosub);
+    return cudaGetLastError();
+}
+
+cudaError_t interp_prepare(int nupts, int nfpts, int nnz, bool fp64) {
+    // shared memory above the default 48 KB for the staged state tile.  The
+    // limit is a property of the kernel, shared by every block and context:
+    // it is raised to the largest a CTA may hold (never lowered to one
+    // block's need, which would fail a larger block's launch); a launch's
+    // occupancy follows the shared memory it asks for, not this limit.
+    constexpr int kMax = 227 * 1024;
+    const size_t sm = fp64 ? interp_smem<double>(nfpts, nupts, nnz) : interp_smem<float>(nfpts, nupts, nnz);
+    if (sm > (size_t)kMax) return cudaErrorInvalidValue;
+    return fp64 ? cudaFuncSetAttribute((const void*)interp_sparse_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMax)
+                : cudaFuncSetAttribute((const void*)interp_sparse_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
 }
 
 // Operator product dispatch: CUDA-core GEMM for FP64 / FP32, tensor-core
@@ -744,6 +990,15 @@ struct RkStage {
     void* const* u;           // the step's state (per block)
 };
 
+// blocks whose M0 products take the dense operator GEMM (no structured form,
+// or the structured kernel switched off)
+static int dense_blocks(const DevCtx& c) {
+    int n = 0;
+    for (const DevBlock& B : c.blocks)
+        if (!(c.structured_interp && B.sp_nnz > 0)) ++n;
+    return n;
+}
+
 // Tensor-core products of every block in one launch (the blocks' problems
 // form one work list), when the context groups them.
 static bool grouped(const DevCtx& c) {
@@ -781,11 +1036,19 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
     tc::SubRef sr;
     for (int a = 0; a < 5; ++a) sr.v[a] = (float)sub.v[a];
     if (!(phases & PH_A)) goto phase_b1;
-    // 1. U'^(f) = M0 (U - u_ref)  (K1, disu)
-    if (grouped(c)) {
+    // 1. U'^(f) = M0 (U - u_ref)  (K1, disu); blocks whose M0 is structured
+    // (tensor elements) take the structured kernel, the others the operator GEMM
+    if (grouped(c) && dense_blocks(c) > 1) {
+        // structured blocks on their own kernel, the dense ones in one launch
         std::vector<tc::GemmProblem> P;
         for (size_t b = 0; b < c.blocks.size(); ++b) {
             DevBlock& B = c.blocks[b];
+            if (c.structured_interp && B.sp_nnz > 0) {
+                prof_begin(c, K_DISU, st);
+                FR_TRY(interp_sparse<T>(B, u[b], (int64_t)NV * B.ld, B.Uf, sub, 1, st));
+                prof_end(c, st);
+                continue;
+            }
             P.push_back({B.nfpts, B.nupts, 0, B.tcM0, (const float*)u[b], nullptr, (int64_t)NV * B.ld, (float*)B.Uf,
                          nullptr, B.ld, 1, nullptr, nullptr});
         }
@@ -796,8 +1059,11 @@ static cudaError_t rhs_impl(DevCtx& c, void* const* u, void* const* r, cudaStrea
         for (size_t b = 0; b < c.blocks.size(); ++b) {
             DevBlock& B = c.blocks[b];
             prof_begin(c, K_DISU, st);
-            FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, u[b], nullptr, (int64_t)NV * B.ld, B.Uf, 0,
-                              nullptr, B.ld, st, 0, B.nupts, sub, B.tune[TUNE_DISU]));
+            if (c.structured_interp && B.sp_nnz > 0)
+                FR_TRY(interp_sparse<T>(B, u[b], (int64_t)NV * B.ld, B.Uf, sub, 1, st));
+            else
+                FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts, u[b], nullptr, (int64_t)NV * B.ld,
+                                  B.Uf, 0, nullptr, B.ld, st, 0, B.nupts, sub, B.tune[TUNE_DISU]));
             prof_end(c, st);
         }
     }
@@ -872,15 +1138,31 @@ phase_b1:
                     prof_end(c, st);
                 }
             }
-            // the D interpolations of the gradient: grouped with every block's in as
-            // few launches as the group size allows; otherwise one launch each (a
-            // single block's directions merged into one launch measured no faster
-            // at 96^3: 3.91 ms against 3 x 1.27 ms)
-            if (grouped(c)) {
+            // the D interpolations of the gradient: the structured kernel where M0
+            // is structured; grouped with every block's in as few launches as the
+            // group size allows; otherwise one launch each (a single block's
+            // directions merged into one launch measured no faster at 96^3: 3.91 ms
+            // against 3 x 1.27 ms)
+            if (grouped(c) && dense_blocks(c) > 1) {
+                std::vector<tc::GemmProblem> PD;
+                for (size_t b = 0; b < c.blocks.size(); ++b) {
+                    DevBlock& B = c.blocks[b];
+                    const int64_t N = (int64_t)NV * B.ld;
+                    for (int i = 0; i < D; ++i) {
+                        if (c.structured_interp && B.sp_nnz > 0) {
+                            prof_begin(c, K_GRADFPTS, st);
+                            FR_TRY(interp_sparse<T>(B, (const T*)B.Q + (int64_t)i * B.nupts * N, N,
+                                                    (T*)B.Qf + (int64_t)i * B.nfpts * N, Sub<T>{}, 0, st));
+                            prof_end(c, st);
+                        } else {
+                            PD.push_back(PF[b * D + i]);
+                        }
+                    }
+                }
                 const int gmax = tc::group_max();
-                for (size_t i0 = 0; i0 < PF.size(); i0 += gmax) {
-                    const std::vector<tc::GemmProblem> part(PF.begin() + i0,
-                                                            PF.begin() + std::min(PF.size(), i0 + (size_t)gmax));
+                for (size_t i0 = 0; i0 < PD.size(); i0 += gmax) {
+                    const std::vector<tc::GemmProblem> part(PD.begin() + i0,
+                                                            PD.begin() + std::min(PD.size(), i0 + (size_t)gmax));
                     prof_begin(c, K_GRADFPTS, st);
                     FR_TRY(run_group(c, 0, part, sr, TUNE_GRADFPTS, st));
                     prof_end(c, st);
@@ -888,9 +1170,15 @@ phase_b1:
             } else {
                 for (size_t b = 0; b < c.blocks.size(); ++b)
                     for (int i = 0; i < D; ++i) {
+                        DevBlock& B = c.blocks[b];
+                        const int64_t N = (int64_t)NV * B.ld;
                         prof_begin(c, K_GRADFPTS, st);
-                        FR_TRY(tc::gemm_group(c.precision == 3 ? 0 : 1, 0, &PF[b * D + i], 1, sr, c.flags, st,
-                                              c.tc_wait_limit, c.blocks[b].tune[TUNE_GRADFPTS]));
+                        if (c.structured_interp && B.sp_nnz > 0)
+                            FR_TRY(interp_sparse<T>(B, (const T*)B.Q + (int64_t)i * B.nupts * N, N,
+                                                    (T*)B.Qf + (int64_t)i * B.nfpts * N, Sub<T>{}, 0, st));
+                        else
+                            FR_TRY(tc::gemm_group(c.precision == 3 ? 0 : 1, 0, &PF[b * D + i], 1, sr, c.flags, st,
+                                                  c.tc_wait_limit, c.blocks[b].tune[TUNE_GRADFPTS]));
                         prof_end(c, st);
                     }
             }
@@ -908,9 +1196,13 @@ phase_b1:
                 prof_end(c, st);
                 for (int i = 0; i < D; ++i) {
                     prof_begin(c, K_GRADFPTS, st);
-                    FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts,
-                                      (const T*)B.Q + (int64_t)i * B.nupts * N, nullptr, N,
-                                      (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st, 0, 0, Sub<T>{}));
+                    if (c.structured_interp && B.sp_nnz > 0)
+                        FR_TRY(interp_sparse<T>(B, (const T*)B.Q + (int64_t)i * B.nupts * N, N,
+                                                (T*)B.Qf + (int64_t)i * B.nfpts * N, Sub<T>{}, 0, st));
+                    else
+                        FR_TRY(op_gemm<T>(c, B.opM0, B.tcM0, B.nfpts, B.nupts, B.nupts,
+                                          (const T*)B.Q + (int64_t)i * B.nupts * N, nullptr, N,
+                                          (T*)B.Qf + (int64_t)i * B.nfpts * N, 0, nullptr, B.ld, st, 0, 0, Sub<T>{}));
                     prof_end(c, st);
                 }
             }

@@ -194,7 +194,8 @@ class PartitionedSolver:
     def rhs(self, u, r, stream=None):
         """u[p][b], r[p][b]: device state / result of rank p, block b."""
         ctxs = (C.c_void_p * self.nparts)(*[s.ctx for s in self.ranks])
-        ua, ra = [_ptrs(x) for x in u], [_ptrs(x) for x in r]       # kept alive for the call
+        ua = [s._bufs(x) for s, x in zip(self.ranks, u)]             # kept alive for the call
+        ra = [s._bufs(x) for s, x in zip(self.ranks, r)]
         U = (C.POINTER(C.c_void_p) * self.nparts)(*[C.cast(a, C.POINTER(C.c_void_p)) for a in ua])
         R = (C.POINTER(C.c_void_p) * self.nparts)(*[C.cast(a, C.POINTER(C.c_void_p)) for a in ra])
         self._keep = (ua, ra, U, R)
@@ -366,36 +367,72 @@ class Solver:
         out[:, :, :L["nelem"]] = u_np
         return out
 
+    def _bufs(self, seq, host=False):
+        """Pointer array of one state-shaped buffer per element block, each
+        checked against the block's layout before any launch: shape [nupts,
+        nvars, ld], the context's dtype, C-contiguous, on the context's GPU
+        (host=True: in host memory, numpy or torch CPU).  The C ABI takes
+        plain pointers and cannot see a wrong size or dtype, which would make
+        its kernels read or write past the buffer; integers are taken as raw
+        addresses, unchecked."""
+        if len(seq) != self.nblocks:
+            raise ValueError(f"{len(seq)} buffers for {self.nblocks} element blocks")
+        if not hasattr(self, "_shapes"):
+            self._shapes = [(L["nupts"], L["nvars"], L["ld"]) for L in (self.layout(b) for b in range(self.nblocks))]
+        ptrs = []
+        for b, t in enumerate(seq):
+            if isinstance(t, int):
+                ptrs.append(t)
+                continue
+            if isinstance(t, np.ndarray):
+                shape, dt, contig, where = t.shape, str(t.dtype), t.flags.c_contiguous, "host"
+                ptr = t.ctypes.data
+            else:
+                shape, dt, contig = tuple(t.shape), str(t.dtype).replace("torch.", ""), t.is_contiguous()
+                where = "host" if t.device.type == "cpu" else (
+                    "gpu" if t.device.type == "cuda" and t.device.index == self.device else str(t.device))
+                ptr = t.data_ptr()
+            want = "host" if host else "gpu"
+            if tuple(shape) != self._shapes[b] or dt != self.dtype_name or not contig or where != want:
+                raise ValueError(f"block {b}: buffer {tuple(shape)} {dt} {'contiguous' if contig else 'strided'} "
+                                 f"on {where}; the context wants {self._shapes[b]} {self.dtype_name} contiguous "
+                                 f"on {'the host' if host else f'cuda:{self.device}'}")
+            ptrs.append(ptr)
+        return _ptrs(ptrs)
+
     def rhs(self, u, r, stream=None):
-        self._check(self.lib.fr_rhs(self.ctx, _ptrs(u), _ptrs(r), _stream_ptr(stream)))
+        self._check(self.lib.fr_rhs(self.ctx, self._bufs(u), self._bufs(r), _stream_ptr(stream)))
 
     def rhs_host(self, u, r, stream=None):
         """u, r: lists of C-contiguous host arrays (numpy or pinned torch CPU tensors)."""
-        def hp(x):
-            return x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
-        self._check(self.lib.fr_rhs_host(self.ctx, _ptrs([hp(x) for x in u]), _ptrs([hp(x) for x in r]),
-                                         _stream_ptr(stream)))
+        self._check(self.lib.fr_rhs_host(self.ctx, self._bufs(u, True), self._bufs(r, True), _stream_ptr(stream)))
 
     def rk4(self, u, dt, nsteps, stream=None):
-        self._check(self.lib.fr_rk4(self.ctx, _ptrs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+        self._check(self.lib.fr_rk4(self.ctx, self._bufs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+
+    def rk4_noalloc(self, u, dt, nsteps, stream=None):
+        """fr_rk4_noalloc: nsteps RK4 steps in place without device allocations."""
+        self._check(self.lib.fr_rk4_noalloc(self.ctx, self._bufs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+
+    def rk_step(self, u, dt, nsteps, stream=None):
+        """fr_rk_step: nsteps steps of the context's Butcher-table RK scheme in place."""
+        self._check(self.lib.fr_rk_step(self.ctx, self._bufs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
 
     def rk4_host(self, u, dt, nsteps, stream=None):
         """nsteps RK4 steps on host buffers (numpy arrays or pinned torch CPU
         tensors, layout of pack()); copies in and out inside the call."""
-        def hp(x):
-            return x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
-        self._check(self.lib.fr_rk4_host(self.ctx, _ptrs([hp(x) for x in u]), C.c_double(dt), nsteps,
+        self._check(self.lib.fr_rk4_host(self.ctx, self._bufs(u, True), C.c_double(dt), nsteps,
                                          _stream_ptr(stream)))
 
     def euler(self, u, dt, nsteps, stream=None):
         """nsteps forward Euler steps in place."""
-        self._check(self.lib.fr_euler(self.ctx, _ptrs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
+        self._check(self.lib.fr_euler(self.ctx, self._bufs(u), C.c_double(dt), nsteps, _stream_ptr(stream)))
 
     def dopri5(self, u, dt, nsteps, atol=1e-6, rtol=1e-6, error=False, stream=None):
         """nsteps fixed DOPRI5 steps in place; with error=True returns the
         scaled RMS norm of the last step's embedded error estimate (synchronises)."""
         e = C.c_double(0.0)
-        self._check(self.lib.fr_dopri5(self.ctx, _ptrs(u), C.c_double(dt), nsteps, C.c_double(atol),
+        self._check(self.lib.fr_dopri5(self.ctx, self._bufs(u), C.c_double(dt), nsteps, C.c_double(atol),
                                        C.c_double(rtol), C.byref(e) if error else None, _stream_ptr(stream)))
         return e.value if error else None
 
@@ -420,26 +457,26 @@ class Solver:
 
     def adjoint_rhs(self, u, lam, out, stream=None):
         """out = (dR/du)^T lam (Euler or Navier-Stokes; whole-mesh contexts)."""
-        self._check(self.lib.fr_adjoint_rhs(self.ctx, _ptrs(u), _ptrs(lam), _ptrs(out), _stream_ptr(stream)))
+        self._check(self.lib.fr_adjoint_rhs(self.ctx, self._bufs(u), self._bufs(lam), self._bufs(out), _stream_ptr(stream)))
 
     def rk4_adjoint(self, u0, lam, dt, nsteps, every=10, stream=None):
         """lam: dK/du_N on entry, dK/du0 on return (Euler or Navier-Stokes)."""
-        self._check(self.lib.fr_rk4_adjoint(self.ctx, _ptrs(u0), _ptrs(lam), C.c_double(dt), nsteps, every,
+        self._check(self.lib.fr_rk4_adjoint(self.ctx, self._bufs(u0), self._bufs(lam), C.c_double(dt), nsteps, every,
                                             _stream_ptr(stream)))
 
     def sum_weighted(self, u, stream=None):
         out = np.zeros(self.nvars)
-        self._check(self.lib.fr_sum_weighted(self.ctx, _ptrs(u), out.ctypes.data_as(C.POINTER(C.c_double)),
+        self._check(self.lib.fr_sum_weighted(self.ctx, self._bufs(u), out.ctypes.data_as(C.POINTER(C.c_double)),
                                              _stream_ptr(stream)))
         return out
 
     def check_finite(self, u, stream=None):
-        self._check(self.lib.fr_check_finite(self.ctx, _ptrs(u), _stream_ptr(stream)))
+        self._check(self.lib.fr_check_finite(self.ctx, self._bufs(u), _stream_ptr(stream)))
 
     def autotune(self, u, reps=2, stream=None):
         """Time every tensor-core kernel variant of each operator product on a
         copy of u and keep the fastest (fr_autotune); returns tuning()."""
-        self._check(self.lib.fr_autotune(self.ctx, _ptrs(u), int(reps), _stream_ptr(stream)))
+        self._check(self.lib.fr_autotune(self.ctx, self._bufs(u), int(reps), _stream_ptr(stream)))
         return self.tuning()
 
     def tuning(self):

@@ -127,23 +127,27 @@ def test_tuned_rk4_equals_default_rk4(torch):
     assert s.sync_status() == fr.OK and t.sync_status() == fr.OK
 
 
+@pytest.mark.parametrize("structured", [0, 1])
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
-def test_grouped_launches_match_per_block_launches(torch, prec):
+def test_grouped_launches_match_per_block_launches(torch, prec, structured):
     """On a mixed mesh (quadrilaterals and triangles) each tensor-core product
     runs as one launch over both blocks' work items: the same bits as one
     launch per block, for the right-hand side and for graph-replayed RK4, with
-    one launch per product and stage (the two gradient interpolations of both
-    blocks included) instead of one per block."""
+    one launch per product and stage (the gradient interpolations of both
+    blocks included) instead of one per block.  With the structured
+    interpolation on, the quadrilaterals' M0 products take it in both."""
     from paper_1312_1638_b300 import fr
     m, s = _solver(fr, "mixed", prec)
     _, t = _solver(fr, "mixed", prec)
     t.set_option("group_blocks", 0)
+    for x in (s, t):
+        x.set_option("structured_interp", structured)
     u = _state(torch, s, m)
     s.profile_enable(True)
     t.profile_enable(True)
     a, b = _rhs(torch, s, u), _rhs(torch, t, u)
     ps, pt = s.profile_read(), t.profile_read()
-    for k in ("disu_gemm", "tgradu_gemm", "gradfpts_gemm", "tdivf_gemm"):
+    for k in ("tgradu_gemm", "tdivf_gemm") + (() if structured else ("disu_gemm", "gradfpts_gemm")):
         assert ps[k][0] == 1, (k, ps[k])
         assert pt[k][0] == (4 if k == "gradfpts_gemm" else 2), (k, pt[k])    # per block (and direction)
     for x, y, blk in zip(a, b, m.blocks):
@@ -159,3 +163,59 @@ def test_grouped_launches_match_per_block_launches(torch, prec):
         ne = blk.nodes.shape[0]
         assert torch.equal(x[:, :, :ne], y[:, :, :ne])
     assert s.sync_status() == fr.OK and t.sync_status() == fr.OK
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("etype,n,p", [("quad", 12, 3), ("hex", 4, 4), ("hex", 3, 2)])
+def test_structured_interpolation_matches_the_dense_product(torch, etype, n, p, prec):
+    """On tensor elements M0 has p+1 nonzeros per row; the structured kernel
+    keeps those (entries below 1e-15 of their row's largest, the rounding of
+    a vanishing Lagrange factor, are dropped) and adds them in the order the
+    dense CUDA-core product does.  Both right-hand sides meet the precision's
+    parity bound against the oracle (|R_gpu - R| <= tol S), and they differ
+    from each other by a small fraction of it."""
+    from oracle.system import FRSystem
+    from paper_1312_1638_b300 import fr
+    m = periodic_box(etype, n, 0.0, 2 * np.pi, jitter=0.1, seed=4)
+    s = fr.Solver(m, p, "ns", prec, device=0, **PRM)
+    t = fr.Solver(m, p, "ns", prec, device=0, **PRM)
+    t.set_option("structured_interp", 0)
+    U = fields.smooth_random(s.solution_points(0), seed=3, amp=0.1, vel0=(0.3, 0.1, 0.0)[:m.ndims],
+                             p0=1.0 / (1.4 * 0.09)).transpose(1, 0, 2).copy()
+    if prec == "fp32":
+        U = U.astype(np.float32).astype(np.float64)
+    prm = {k: v for k, v in PRM.items() if not k.startswith("ref_")}
+    R, S = FRSystem(m, p, "ns", **prm).rhs([U], scale=True)
+    u = [torch.from_numpy(s.pack(0, U)).cuda()]
+    a, b = _rhs(torch, s, u), _rhs(torch, t, u)
+    ne = m.blocks[0].nodes.shape[0]
+    ga, gb = (x[0].cpu().numpy()[:, :, :ne].astype(np.float64) for x in (a, b))
+    tol = {"fp64": 1e-13, "fp32": 2e-6}[prec]
+    ea, eb, ed = (np.max(np.abs(x) / S[0]) for x in (ga - R[0], gb - R[0], ga - gb))
+    print(f"structured {etype} p{p} {prec}: {ea:.2e} dense {eb:.2e} difference {ed:.2e} (bound {tol:.0e})")
+    assert ea <= tol and eb <= tol
+    assert ed <= tol / 4
+    assert s.sync_status() == fr.OK
+
+
+def test_structured_kernel_limits_do_not_shrink_between_contexts(torch):
+    """The structured kernel's shared-memory limit belongs to the kernel, not
+    to a context or block: a context with a large tile (hexahedra, p = 4,
+    FP64) still runs after contexts with smaller ones are set up, as does a
+    mesh whose two structured blocks need different tiles (quadrilaterals and
+    triangles at p = 1), through an RK4 graph."""
+    from paper_1312_1638_b300 import fr
+    from fr_inputs.meshes import channel_mixed
+    m = periodic_box("hex", 3, 0.0, 2 * np.pi, jitter=0.1, seed=4)
+    big = fr.Solver(m, 4, "ns", "fp64", device=0, **PRM)
+    u = _state(torch, big, m)
+    before = _rhs(torch, big, u)
+    mc = channel_mixed(4, 4, jitter=0.1, seed=1)
+    small = fr.Solver(mc, 1, "ns", "fp64", device=0, **PRM)
+    uc = _state(torch, small, mc)
+    small.rk4(uc, 1e-5, 2)
+    torch.cuda.synchronize()
+    assert small.sync_status() == fr.OK
+    after = _rhs(torch, big, u)
+    assert torch.equal(before[0], after[0])
+    assert big.sync_status() == fr.OK
