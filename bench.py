@@ -338,6 +338,15 @@ def replica_value(ms_local, units_per_rank, world, dist=None, device="cpu"):
     return units_per_rank * world / (ms / 1e3) / 1e9, ms
 
 
+def structured_nonzeros(nu, nf, D, order):
+    """Nonzeros per output column of the products that run on structured
+    kernels on a hexahedral (tensor) mesh: M0 (p+1 per flux-point row, for U^(f)
+    and the gradient at flux points) and the corrected gradient [M6 | M4 - M6 M0]
+    (p+1 solution points and 2 flux points per row, D nu rows)."""
+    p1 = order + 1
+    return {"disu_gemm": nf * p1, "gradfpts_gemm": nf * p1, "tgradu_gemm": D * nu * (p1 + 2)}
+
+
 def operator_flops_per_rhs(nu, nf, V, D, nelem):
     """Dense operator flops of one NS right-hand side (App. A)."""
     f = 0.0
@@ -470,15 +479,31 @@ def main():
     }[a.precision]
 
     one_side = PRM["ldg_beta"] in (0.5, -0.5)
+    # products that run on a structured kernel on this workload (hexahedra): the
+    # nonzeros they multiply per column (M0 rows: p+1; corrected-gradient rows:
+    # p+1 solution points and 2 flux points), as FP32 (FP64) multiply-adds on
+    # the CUDA cores whatever the precision
+    structured = structured_nonzeros(nu, nf, D, a.order)
 
     def roof_of(name, launches, tms):
-        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz, tc_path, one_side)
+        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz, tc_path or name in structured, one_side)
         avg = tms / launches / 1e3
         t_hbm = kb / (hbm_peak * 1e9) if kb else 0.0
         t_alu = (kf * arith[1]) / (arith[0] * 1e12) if kf else 0.0
         r = dict(kernel=name, avg_launch_ms=tms / launches, algorithmic_bytes_per_launch=kb,
                  algorithmic_flops_per_launch=kf, hbm_frac=(kb / avg / 1e9) / hbm_peak if kb else None)
-        if t_alu > t_hbm:
+        if name in structured:
+            kx = 2.0 * structured[name] * V * nelem
+            pk = fp64_peak if a.precision == "fp64" else fp32_peak
+            t_alu = kx / (pk * 1e12)
+            r["executed_flops_per_launch"] = kx
+            r["structured"] = "CUDA-core multiply-adds of the operator's nonzeros (structured kernel)"
+            if t_alu > t_hbm:
+                r.update(bound="alu", achieved=kx / avg / 1e12, peak=pk, unit="TFLOP/s", peak_source=alu_src)
+            else:
+                r.update(bound="hbm", achieved=kb / avg / 1e9, peak=hbm_peak, unit="GB/s",
+                         peak_source=f"{peak_src} hbm_gbs")
+        elif t_alu > t_hbm:
             bound = "tensor" if a.precision in ("tf32x3", "bf16x3") else "alu"
             r.update(bound=bound, achieved=kf * arith[1] / avg / 1e12, peak=arith[0], unit="TFLOP/s",
                      peak_source=arith[3], work_factor=arith[1],
@@ -502,7 +527,7 @@ def main():
         if not v[0]:
             continue
         d = dict(launches=v[0], ms=round(v[1], 3), share=round(v[1] / max(total_ms, 1e-9), 4))
-        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz, tc_path, one_side)
+        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz, tc_path or k in structured, one_side)
         if b:
             d["GB_s"] = round(b / (d["ms"] / d["launches"] / 1e3) / 1e9, 1)
             d["hbm_frac"] = round(d["GB_s"] / hbm_peak, 3)

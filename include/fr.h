@@ -293,7 +293,19 @@ fr_status fr_set_tuning(fr_ctx* ctx, const char* text);
  * M0 (U^(f) and the gradient at flux points) run as a structured kernel with
  * FP32 / FP64 multiply-adds of those entries, in every precision (they need
  * no split: FP32 multiply-adds are as accurate as the split products); 0
- * uses the dense operator products.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
+ * uses the dense operator products.  "structured_grad" (default 1, Navier-Stokes):
+ * where every row of the corrected-gradient operator [M6 | M4 - M6 M0]
+ * (Eq. tquptsm) has at most 8 nonzeros (quadrilaterals and hexahedra: the
+ * p+1 solution points on a line and the two flux points ending it), the
+ * gradient Q = J^-T Q~ (Eq. gradufpts) runs as one structured kernel with
+ * FP32 / FP64 multiply-adds of those entries and the transform in the same
+ * pass, in every precision; 0 uses the dense operator product (tensor cores
+ * on the split-precision paths).  "structured_div" (default 1): the same for
+ * the divergence operator [M3 | M1 - M3 M2] (Eq. tdivflux; at most 24
+ * nonzeros per row: per direction the p+1 flux values on the line through
+ * the point and the two common fluxes ending it), -1/J (Eq. negdivconf) and, inside
+ * fr_rk4, the RK4 stage combination applied in the same pass.  Changing
+ * either drops the captured RK4 step.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
  * operator GEMMs gives up: the kernel then drains its own copies and MMAs,
  * returns, and fr_sync_status reports FR_ERR_TIMEOUT; the context stays

@@ -98,6 +98,20 @@ void* upload_real(fr_ctx* c, const std::vector<double>& h, bool fp64) {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// the rows' nonzeros (column, value) as [rows][nnz] packed entries in the
+// compute type, each row zero-padded with (value 0, column 0)
+template <typename T>
+static void* upload_pairs_t(fr_ctx* c, const std::vector<std::vector<std::pair<int, double>>>& rows, int nnz) {
+    std::vector<fr::SpPair<T>> e(rows.size() * (size_t)nnz, fr::SpPair<T>{T(0), 0});
+    for (size_t r = 0; r < rows.size(); ++r)
+        for (size_t j = 0; j < rows[r].size(); ++j) e[r * nnz + j] = fr::SpPair<T>{(T)rows[r][j].second, rows[r][j].first};
+    return upload(c, e);
+}
+
+void* upload_pairs(fr_ctx* c, const std::vector<std::vector<std::pair<int, double>>>& rows, int nnz, bool fp64) {
+    return fp64 ? upload_pairs_t<double>(c, rows, nnz) : upload_pairs_t<float>(c, rows, nnz);
+}
+
 fr_status set_err(fr_ctx* c, fr_status st, const std::string& m) {
     if (c) c->err = m;
     else g_setup_err = m;
@@ -138,6 +152,126 @@ void fill_metrics(fr_ctx* c, const fr::HostBlock& hb, fr::DevBlock& B, int d) {
     B.smat = upload(c, smat);
     B.rcpdjac = upload(c, rcp);
     B.wdet = (double*)upload(c, wdet);
+}
+
+// Tensor-line form of the gradient and divergence operators (quadrilaterals,
+// hexahedra; see the tensor-line kernels): the lines in the kernels'
+// numbering (direction i, then the other indices, xi fastest), each line's
+// two end flux points found by their reference coordinates (the xi_i = -1
+// one first), and n x (n+2) line matrices taken from the first line.  The
+// form is accepted only if it rebuilds every row of the dense operators to
+// 1e-12 of the row's largest entry (so no line or direction differs and no
+// entry is missed).
+struct LineForm {
+    int n = 0;
+    bool grad = false, div = false;
+    std::vector<double> A, B;
+    std::vector<int> fl;
+};
+
+static LineForm line_form(const fr::ElemType& el, int d) {
+    LineForm L;
+    if (el.etype != fr::ET_QUAD && el.etype != fr::ET_HEX) return L;
+    const int n = el.p + 1, nu = el.nupts, nf = el.nfpts;
+    int NU = 1;
+    for (int i = 0; i < d; ++i) NU *= n;
+    if (NU != nu || n < 2 || n > 6) return L;
+    const int NL = NU / n, NLT = d * NL;
+    const double tol = 1e-12;
+    for (int s = 0; s < nu; ++s) {                       // s = a + n b (+ n^2 c) at the GL nodes (a, b, c)
+        int r = s;
+        for (int j = 0; j < d; ++j) {
+            if (std::fabs(el.upts[(size_t)s * d + j] - el.gl[r % n]) > tol) return L;
+            r /= n;
+        }
+    }
+    std::vector<std::vector<int>> pts(NLT, std::vector<int>(n));
+    std::vector<int> dir(NLT), fl((size_t)NLT * 2, -1);
+    for (int l = 0; l < NLT; ++l) {
+        const int i = l / NL, m = l % NL;
+        int base, stride;
+        if (d == 2) {
+            base = i == 0 ? m * n : m;
+            stride = i == 0 ? 1 : n;
+        } else {
+            base = i == 0 ? m * n : (i == 1 ? m % n + n * n * (m / n) : m);
+            stride = i == 0 ? 1 : (i == 1 ? n : n * n);
+        }
+        dir[l] = i;
+        for (int q = 0; q < n; ++q) pts[l][q] = base + q * stride;
+        for (int f = 0; f < nf; ++f) {
+            bool on = true;
+            for (int j = 0; j < d && on; ++j)
+                if (j != i && std::fabs(el.fpts[(size_t)f * d + j] - el.upts[(size_t)pts[l][0] * d + j]) > tol) on = false;
+            if (!on) continue;
+            const double x = el.fpts[(size_t)f * d + i];
+            const int e = std::fabs(x + 1) < tol ? 0 : (std::fabs(x - 1) < tol ? 1 : -1);
+            if (e < 0 || fl[2 * l + e] >= 0) return L;
+            fl[2 * l + e] = f;
+        }
+        if (fl[2 * l] < 0 || fl[2 * l + 1] < 0) return L;
+    }
+    const int w = n + 2;
+    auto close = [&](const std::vector<double>& rec, const double* row, size_t len) {
+        double mx = 0, df = 0;
+        for (size_t k = 0; k < len; ++k) {
+            mx = std::max(mx, std::fabs(row[k]));
+            df = std::max(df, std::fabs(row[k] - rec[k]));
+        }
+        return df <= tol * mx;
+    };
+    // gradient: row (i, s) of [M6 | M4 - M6 M0] from line l through s along i
+    {
+        std::vector<double> A((size_t)n * w);
+        for (int q = 0; q < n; ++q) {
+            const size_t r = (size_t)dir[0] * nu + pts[0][q];
+            for (int k = 0; k < n; ++k) A[(size_t)q * w + k] = el.M46[r * nu + pts[0][k]];
+            for (int e = 0; e < 2; ++e) A[(size_t)q * w + n + e] = el.M6[r * nf + fl[e]];
+        }
+        bool ok = true;
+        std::vector<double> rec(nf + nu);
+        for (int l = 0; l < NLT && ok; ++l)
+            for (int q = 0; q < n && ok; ++q) {
+                const size_t r = (size_t)dir[l] * nu + pts[l][q];
+                std::fill(rec.begin(), rec.end(), 0.0);
+                for (int k = 0; k < n; ++k) rec[nf + pts[l][k]] = A[(size_t)q * w + k];
+                for (int e = 0; e < 2; ++e) rec[fl[2 * l + e]] = A[(size_t)q * w + n + e];
+                std::vector<double> row(nf + nu);
+                for (int f = 0; f < nf; ++f) row[f] = el.M6[r * nf + f];
+                for (int k = 0; k < nu; ++k) row[nf + k] = el.M46[r * nu + k];
+                ok = close(rec, row.data(), row.size());
+            }
+        L.grad = ok;
+        L.A = A;
+    }
+    // divergence: row s of [M3 | M1 - M3 M2], one line per direction through s
+    {
+        std::vector<double> B((size_t)n * w);
+        for (int q = 0; q < n; ++q) {
+            const size_t s = pts[0][q];
+            for (int k = 0; k < n; ++k) B[(size_t)q * w + k] = el.M132[s * d * nu + (size_t)dir[0] * nu + pts[0][k]];
+            for (int e = 0; e < 2; ++e) B[(size_t)q * w + n + e] = el.M3[s * nf + fl[e]];
+        }
+        std::vector<std::vector<double>> rec(nu, std::vector<double>(nf + (size_t)d * nu, 0.0));
+        for (int l = 0; l < NLT; ++l)
+            for (int q = 0; q < n; ++q) {
+                std::vector<double>& rr = rec[pts[l][q]];
+                for (int k = 0; k < n; ++k) rr[nf + (size_t)dir[l] * nu + pts[l][k]] += B[(size_t)q * w + k];
+                for (int e = 0; e < 2; ++e) rr[fl[2 * l + e]] += B[(size_t)q * w + n + e];
+            }
+        bool ok = true;
+        for (int s = 0; s < nu && ok; ++s) {
+            std::vector<double> row(nf + (size_t)d * nu);
+            for (int f = 0; f < nf; ++f) row[f] = el.M3[(size_t)s * nf + f];
+            for (int k = 0; k < d * nu; ++k) row[nf + k] = el.M132[(size_t)s * d * nu + k];
+            ok = close(rec[s], row.data(), row.size());
+        }
+        L.div = ok;
+        L.B = B;
+    }
+    L.n = n;
+    L.fl = fl;
+    return L;
 }
 
 void upload_device(fr_ctx* c) {
@@ -202,6 +336,67 @@ void upload_device(fr_ctx* c) {
             (void)cudaGetLastError();
         }
         B.opQ = upload_real(c, hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu), fp64);
+        {
+            const LineForm lf = line_form(el, d);
+            if (lf.n > 0) {
+                B.ln_grad = ns && lf.grad && fr::line_prepare(0, d, lf.n, (int)nf, fp64) == cudaSuccess;
+                B.ln_div = lf.div && fr::line_prepare(1, d, lf.n, (int)nf, fp64) == cudaSuccess;
+                (void)cudaGetLastError();
+                if (B.ln_grad || B.ln_div) {
+                    B.ln_n = lf.n;
+                    std::copy(lf.A.begin(), lf.A.end(), B.ln_A);
+                    std::copy(lf.B.begin(), lf.B.end(), B.ln_B);
+                    B.ln_fl = (int*)upload(c, lf.fl);
+                }
+            }
+        }
+        {
+            // structured form of the divergence operator [M3 | M1 - M3 M2] (same
+            // rule): on tensor elements row s holds, per direction, the p+1
+            // points of the line through s and the two flux points at its ends
+            const std::vector<double> G = hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu);
+            const int64_t rows = nu, K = nf + d * nu;
+            std::vector<std::vector<std::pair<int, double>>> nzr((size_t)rows);
+            int nnz = 0;
+            for (int64_t r = 0; r < rows; ++r) {
+                double mx = 0;
+                for (int64_t k = 0; k < K; ++k) mx = std::max(mx, std::fabs(G[(size_t)(r * K + k)]));
+                for (int64_t k = 0; k < K; ++k) {
+                    const double v = G[(size_t)(r * K + k)];
+                    if (std::fabs(v) > 1e-15 * mx) nzr[r].push_back({(int)k, v});
+                }
+                nnz = std::max(nnz, (int)nzr[r].size());
+            }
+            if (nnz > 0 && nnz <= 24 && fr::div_prepare((int)nu, (int)nf, d, nnz, fp64) == cudaSuccess) {
+                B.ds_nnz = nnz;
+                B.ds_ent = upload_pairs(c, nzr, nnz, fp64);
+            }
+            (void)cudaGetLastError();
+        }
+        if (ns) {
+            // structured form of the corrected-gradient operator [M6 | M4 - M6 M0]
+            // (same rule as M0's): on tensor elements row (i, s) holds the p+1
+            // solution points on the line through s in direction i and the two
+            // flux points at its ends
+            const std::vector<double> G = hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu);
+            const int64_t rows = d * nu, K = nf + nu;
+            std::vector<std::vector<std::pair<int, double>>> nzr((size_t)rows);
+            int nnz = 0;
+            for (int64_t r = 0; r < rows; ++r) {
+                double mx = 0;
+                for (int64_t k = 0; k < K; ++k) mx = std::max(mx, std::fabs(G[(size_t)(r * K + k)]));
+                for (int64_t k = 0; k < K; ++k) {
+                    const double v = G[(size_t)(r * K + k)];
+                    if (std::fabs(v) > 1e-15 * mx) nzr[r].push_back({(int)k, v});
+                }
+                nnz = std::max(nnz, (int)nzr[r].size());
+            }
+            if (nnz > 0 && nnz <= 8 && fr::grad_prepare((int)nu, (int)nf, d, nnz, fp64) == cudaSuccess) {
+                B.gs_nnz = nnz;
+                B.gs_ent = upload_pairs(c, nzr, nnz, fp64);
+            }
+            (void)cudaGetLastError();
+        }
         B.opR = upload_real(c, hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu), fp64);
         {
             // transposed operators of the discrete adjoint
@@ -998,6 +1193,20 @@ fr_status fr_autotune(fr_ctx* ctx, void* const* u, int reps, void* stream) {
                         for (const auto& B2 : D.blocks) dense = dense || B2.sp_nnz <= 0;
                     if (!dense) continue;
                 }
+                if (slot == fr::TUNE_TGRADU && D.structured_grad) {
+                    auto st_ = [&](const fr::DevBlock& X) { return (D.structured_grad == 1 && X.ln_grad) || X.gs_nnz > 0; };
+                    bool dense = !st_(B);
+                    if (grouped)
+                        for (const auto& B2 : D.blocks) dense = dense || !st_(B2);
+                    if (!dense) continue;
+                }
+                if (slot == fr::TUNE_TDIVF && D.structured_div) {
+                    auto st_ = [&](const fr::DevBlock& X) { return (D.structured_div == 1 && X.ln_div) || X.ds_nnz > 0; };
+                    bool dense = !st_(B);
+                    if (grouped)
+                        for (const auto& B2 : D.blocks) dense = dense || !st_(B2);
+                    if (!dense) continue;
+                }
                 int cand[8];
                 int nc = fr::tune_candidates(D, B, slot, cand);
                 if (grouped) {
@@ -1145,6 +1354,18 @@ fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value) {
     }
     if (std::string(name) == "structured_interp") {
         ctx->dev.structured_interp = value != 0;
+        drop_graph(ctx);
+        return FR_OK;
+    }
+    if (std::string(name) == "structured_grad") {
+        if (value < 0 || value > 2) return set_err(ctx, FR_ERR_ARG, "structured_grad must be 0, 1 or 2");
+        ctx->dev.structured_grad = (int)value;
+        drop_graph(ctx);
+        return FR_OK;
+    }
+    if (std::string(name) == "structured_div") {
+        if (value < 0 || value > 2) return set_err(ctx, FR_ERR_ARG, "structured_div must be 0, 1 or 2");
+        ctx->dev.structured_div = (int)value;
         drop_graph(ctx);
         return FR_OK;
     }

@@ -59,6 +59,30 @@ struct DevBlock {
     int sp_nnz = 0;
     int* sp_idx = nullptr;
     void* sp_val = nullptr;
+    // the corrected-gradient operator [M6 | M4 - M6 M0] in structured form
+    // (NS; rows (i, s), [ndims*nupts][gs_nnz] SpPair<T> entries over the columns
+    // [nfpts + nupts], zero-padded; 0: dense)
+    int gs_nnz = 0;
+    void* gs_ent = nullptr;
+    // the divergence operator [M3 | M1 - M3 M2] in the same form (rows s,
+    // [nupts][ds_nnz] over the columns [nfpts + ndims*nupts]; at most 24)
+    int ds_nnz = 0;
+    void* ds_ent = nullptr;
+    // tensor-line form (quadrilaterals, hexahedra): n = p+1 points per line (0:
+    // none), whether the gradient / divergence operators take it, their n x (n+2)
+    // line matrices, and the two flux points ending each line, [ndims n^(ndims-1)][2]
+    int ln_n = 0;
+    bool ln_grad = false, ln_div = false;
+    double ln_A[48] = {}, ln_B[48] = {};
+    int* ln_fl = nullptr;
+};
+
+// one nonzero of a structured operator row: value and column, packed so that
+// one 8-byte (FP32) or 16-byte (FP64) load fetches both
+template <typename T>
+struct alignas(sizeof(T) == 8 ? 16 : 8) SpPair {
+    T v;
+    int k;
 };
 
 // operator products whose kernel variant can be chosen (DevBlock::tune)
@@ -137,6 +161,11 @@ struct DevCtx {
     long long tc_wait_limit = 0;   // tensor-core GEMM wait limit in SM cycles (0: about two seconds)
     bool group_blocks = true;      // tensor-core products of all element blocks in one launch per stage
     bool structured_interp = true; // M0 products through the structured kernel where M0 allows
+    // corrected gradient / divergence through a structured kernel where the
+    // operator allows: 0 never (dense products), 1 the tensor-line kernel, else
+    // the row-wise one, 2 the row-wise kernel
+    int structured_grad = 1;
+    int structured_div = 1;
     double* partial = nullptr;     // reduction scratch
     int64_t npartial = 0;
 };
@@ -185,6 +214,11 @@ cudaError_t measure_fma(double* fp32_tflops, double* fp64_tflops);
 // raise the structured interpolation kernel's shared-memory limit for an
 // element type (nupts solution, nfpts flux points, nnz nonzeros per row)
 cudaError_t interp_prepare(int nupts, int nfpts, int nnz, bool fp64);
+// the same for the structured corrected-gradient kernel
+cudaError_t grad_prepare(int nupts, int nfpts, int ndims, int nnz, bool fp64);
+cudaError_t div_prepare(int nupts, int nfpts, int ndims, int nnz, bool fp64);
+// the tensor-line kernels: kind 0 gradient, 1 divergence; n = p+1
+cudaError_t line_prepare(int kind, int ndims, int n, int nfpts, bool fp64);
 // look up the allocation-free RK4's fixed device array on `device` (current),
 // reserving it there; failures are left for fr_rk4_noalloc to report
 void noalloc_prepare(int device);

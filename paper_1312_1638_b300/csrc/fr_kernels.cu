@@ -364,6 +364,740 @@ cudaError_t interp_prepare(int nupts, int nfpts, int nnz, bool fp64) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
 }
 
+// ============================================================ structured corrected gradient
+// Q = J^{-T} [M6 C + (M4 - M6 M0)(U - u_ref)] (Eq. tquptsm, then the
+// transform of Eq. gradufpts) for an element type whose gradient operator
+// rows have at most GS_NNZ nonzeros.  On quadrilaterals and hexahedra with
+// tensor Gauss-Legendre points, row (i, s) involves only the p+1 solution
+// points on the line through s in direction i and the two flux points at
+// that line's ends (7 of 275 entries for hexahedra at p = 4), so the product
+// is bound by HBM, not by arithmetic.  A CTA of 256 threads owns TN = 32 VW
+// columns of one variable: it stages the K = N^(f) + N^(u) rows of C and U
+// for them in shared memory (16-byte asynchronous copies; the reference
+// state is subtracted from the U rows by the thread that copied them), and
+// warp w then takes the points s = w, w + 8, ...: per point the D rows of
+// Q~ (each lane a VW-vector of columns, the row's entries read as
+// broadcasts), then the transform with the metric terms of those columns,
+// written as D rows of Q.  Sums run over a row's nonzeros in increasing k,
+// the order of the dense CUDA-core product, and the transform is the
+// arithmetic of grad_transform_kernel.
+constexpr int GS_NNZ = 8;
+constexpr int GS_THREADS = 256;
+template <typename T> struct GsCfg;
+// VW columns per lane, PC points per prefetch chunk, MINB CTAs per SM (the
+// shared-memory limit for hexahedra at p = 4), so registers stay within 64K / SM
+template <> struct GsCfg<float> { static constexpr int VW = 1, PC = 3, MINB = 4; };
+template <> struct GsCfg<double> { static constexpr int VW = 1, PC = 2, MINB = 2; };
+
+template <typename T, int VW>
+__device__ __forceinline__ void ld_vec(const T* p, T* x) {
+    if constexpr (VW == 2 && sizeof(T) == 4) {
+        const float2 v = *(const float2*)p;
+        x[0] = v.x; x[1] = v.y;
+    } else if constexpr (VW == 4 && sizeof(T) == 4) {
+        const float4 v = *(const float4*)p;
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else if constexpr (VW == 2 && sizeof(T) == 8) {
+        const double2 v = *(const double2*)p;
+        x[0] = v.x; x[1] = v.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < VW; ++j) x[j] = p[j];
+    }
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void ldg_vec(const T* p, T* x) {
+    if constexpr (VW == 2 && sizeof(T) == 4) {
+        const float2 v = __ldg((const float2*)p);
+        x[0] = v.x; x[1] = v.y;
+    } else if constexpr (VW == 4 && sizeof(T) == 4) {
+        const float4 v = __ldg((const float4*)p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else if constexpr (VW == 2 && sizeof(T) == 8) {
+        const double2 v = __ldg((const double2*)p);
+        x[0] = v.x; x[1] = v.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < VW; ++j) x[j] = __ldg(p + j);
+    }
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void st_vec(T* p, const T* x) {
+    if constexpr (VW == 2 && sizeof(T) == 4) {
+        *(float2*)p = make_float2(x[0], x[1]);
+    } else if constexpr (VW == 4 && sizeof(T) == 4) {
+        *(float4*)p = make_float4(x[0], x[1], x[2], x[3]);
+    } else if constexpr (VW == 2 && sizeof(T) == 8) {
+        *(double2*)p = make_double2(x[0], x[1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < VW; ++j) p[j] = x[j];
+    }
+}
+
+// one nonzero of a structured operator row, packed so that one load fetches both
+template <typename T>
+__device__ __forceinline__ SpPair<T> ld_pair(const SpPair<T>* p) {
+    if constexpr (sizeof(T) == 4) {
+        const int2 v = __ldg((const int2*)p);
+        return SpPair<T>{__int_as_float(v.x), v.y};
+    } else {
+        const int4 v = __ldg((const int4*)p);
+        return SpPair<T>{__hiloint2double(v.y, v.x), v.z};
+    }
+}
+
+
+// column tile t of a persistent structured kernel: the variables of one
+// element range are consecutive tiles, so CTAs working at the same time share
+// that range's metric terms in L2
+__device__ __forceinline__ int64_t tile_col0(int t, int nvars, int64_t ld, int TN) {
+    return (int64_t)(t % nvars) * ld + (int64_t)(t / nvars) * TN;
+}
+
+// The metric terms of the PC points of a warp's next chunk are loaded while
+// the current chunk is formed, so their HBM latency is paid once per chunk.
+template <typename T, int D>
+__global__ void __launch_bounds__(GS_THREADS, GsCfg<T>::MINB)
+grad_sparse_kernel(int nupts, int nfpts, int nnz, int nvars, const SpPair<T>* __restrict__ ent,
+                   const T* __restrict__ Cf, const T* __restrict__ U, int64_t N, T* __restrict__ Q,
+                   const T* __restrict__ smat, const T* __restrict__ rcp, int64_t ld, Sub<T> sub) {
+    constexpr int VW = GsCfg<T>::VW, TN = 32 * VW, NW = GS_THREADS / 32, GS_PC = GsCfg<T>::PC;
+    constexpr int EPC = 16 / sizeof(T), CPR = TN / EPC;          // values per copy, copies per row
+    extern __shared__ __align__(16) unsigned char gs_smem[];
+    const int K = nfpts + nupts, M = D * nupts;
+    SpPair<T>* et = (SpPair<T>*)gs_smem;                          // [M][nnz] operator entries
+    T* tile = (T*)(gs_smem + (((size_t)M * nnz * sizeof(SpPair<T>) + 15) & ~(size_t)15));   // [K][TN]
+    const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+    for (int e = tid; e < M * nnz; e += GS_THREADS) et[e] = ent[e];
+    const int ntiles = (int)(N / TN);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t col0 = tile_col0(t, nvars, ld, TN);
+        const int a = t % nvars;
+        __syncthreads();                                          // the previous tile is consumed
+        for (int e = tid; e < K * CPR; e += GS_THREADS) {
+            const int k = e / CPR, q = e % CPR;
+            const T* src = k < nfpts ? Cf + (int64_t)k * N : U + (int64_t)(k - nfpts) * N;
+            cp_async16(tile + (size_t)k * TN + q * EPC, src + col0 + q * EPC);
+        }
+        const int64_t n0 = col0 - (int64_t)a * ld + lane * VW;    // element of this lane's first column
+        // the first chunk's metric terms travel with the tile
+        T adj[GS_PC][D][D][VW], r[GS_PC][VW];
+        auto fetch = [&](int s0) {
+#pragma unroll
+            for (int c = 0; c < GS_PC; ++c) {
+                const int s = min(s0 + c * NW, nupts - 1);
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j)
+                        ldg_vec<T, VW>(smat + ((int64_t)(i * D + j) * nupts + s) * ld + n0, adj[c][i][j]);
+                ldg_vec<T, VW>(rcp + (int64_t)s * ld + n0, r[c]);
+            }
+        };
+        fetch(w);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        const T sv = sub.v[a];
+        if (sv != T(0))
+            for (int e = tid; e < K * CPR; e += GS_THREADS) {
+                const int k = e / CPR, q = e % CPR;
+                if (k < nfpts) continue;
+                T* tt = tile + (size_t)k * TN + q * EPC;
+#pragma unroll
+                for (int j = 0; j < EPC; ++j) tt[j] -= sv;
+            }
+        __syncthreads();
+        for (int s0 = w; s0 < nupts; s0 += GS_PC * NW) {
+            T g[GS_PC][D][VW];
+#pragma unroll
+            for (int c = 0; c < GS_PC; ++c) {
+                const int s = min(s0 + c * NW, nupts - 1);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+#pragma unroll
+                    for (int v = 0; v < VW; ++v) g[c][i][v] = T(0);
+                    const SpPair<T>* er = et + (size_t)(i * nupts + s) * nnz;
+#pragma unroll
+                    for (int j = 0; j < GS_NNZ; ++j) {
+                        if (j < nnz) {
+                            const SpPair<T> en = er[j];
+                            T x[VW];
+                            ld_vec<T, VW>(tile + (size_t)en.k * TN + lane * VW, x);
+#pragma unroll
+                            for (int v = 0; v < VW; ++v) g[c][i][v] = fma(en.v, x[v], g[c][i][v]);
+                        }
+                    }
+                }
+            }
+            // this chunk's transform; the next chunk's metric terms are fetched after
+            // it, so that their latency overlaps the next chunk's sums
+#pragma unroll
+            for (int c = 0; c < GS_PC; ++c) {
+                const int s = s0 + c * NW;
+                if (s >= nupts) break;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    T out[VW];
+#pragma unroll
+                    for (int v = 0; v < VW; ++v) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int i = 0; i < D; ++i) acc += adj[c][i][j][v] * g[c][i][v];
+                        out[v] = acc * r[c][v];
+                    }
+                    st_vec<T, VW>(Q + (int64_t)(j * nupts + s) * N + col0 + lane * VW, out);
+                }
+            }
+            if (s0 + GS_PC * NW < nupts) fetch(s0 + GS_PC * NW);
+        }
+    }
+}
+
+template <typename T>
+static size_t grad_smem(int nupts, int nfpts, int ndims, int nnz) {
+    return (((size_t)ndims * nupts * nnz * sizeof(SpPair<T>) + 15) & ~(size_t)15) +
+           (size_t)(nfpts + nupts) * 32 * GsCfg<T>::VW * sizeof(T);
+}
+
+template <typename T, int D>
+static const void* grad_fn() { return (const void*)grad_sparse_kernel<T, D>; }
+
+// persistent grid: as many CTAs as fit on the device at once (capped by the tiles)
+static int persistent_grid(const void* fn, int threads, size_t smem, int ntiles) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return std::max(1, std::min(ntiles, nsm * per));
+}
+
+// Q = J^{-T} Q~ through the structured kernel (B.gs_nnz > 0); Cf is the common
+// solution (the first N^(f) rows of the Q^(f) storage)
+template <typename T, int D>
+static cudaError_t grad_sparse(const DevBlock& Bk, const void* U, cudaStream_t st, Sub<T> sub) {
+    constexpr int TN = 32 * GsCfg<T>::VW;
+    const int64_t N = (int64_t)Bk.nvars * Bk.ld;
+    if (N % TN != 0 || Bk.ld % 128 != 0 || ((uintptr_t)U | (uintptr_t)Bk.Qf | (uintptr_t)Bk.Q) % 16 != 0)
+        return cudaErrorInvalidValue;
+    const size_t sm = grad_smem<T>(Bk.nupts, Bk.nfpts, D, Bk.gs_nnz);
+    const int grid = persistent_grid(grad_fn<T, D>(), GS_THREADS, sm, (int)(N / TN));
+    grad_sparse_kernel<T, D><<<(unsigned)grid, GS_THREADS, sm, st>>>(
+        Bk.nupts, Bk.nfpts, Bk.gs_nnz, Bk.nvars, (const SpPair<T>*)Bk.gs_ent, (const T*)Bk.Qf, (const T*)U, N,
+        (T*)Bk.Q, (const T*)Bk.smat, (const T*)Bk.rcpdjac, Bk.ld, sub);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_prepare(int nupts, int nfpts, int ndims, int nnz, bool fp64) {
+    // as interp_prepare: the kernel's limit is raised to the most a CTA may hold
+    constexpr int kMax = 227 * 1024;
+    const size_t sm = fp64 ? grad_smem<double>(nupts, nfpts, ndims, nnz) : grad_smem<float>(nupts, nfpts, ndims, nnz);
+    if (sm > (size_t)kMax) return cudaErrorInvalidValue;
+    const void* f = fp64 ? (ndims == 2 ? grad_fn<double, 2>() : grad_fn<double, 3>())
+                         : (ndims == 2 ? grad_fn<float, 2>() : grad_fn<float, 3>());
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
+}
+
+// ============================================================ structured divergence
+// R = -J^{-1} [M3 D~ + (M1 - M3 M2) F~] (Eq. tdivflux, negdivconf) for an
+// element type whose divergence operator rows have at most DS_NNZ nonzeros.
+// On tensor elements row s involves, per direction i, the p+1 flux values
+// F~_i on the line through s in direction i and the two common fluxes D~ at
+// that line's ends (21 of 525 entries for hexahedra at p = 4).  A CTA of 256
+// threads owns 32 columns of one variable: it stages the K = N^(f) + D N^(u)
+// rows of D~ and F~ for them in shared memory and warp w forms the rows
+// s = w, w + 8, ... (one column per lane).  The sums run over a row's
+// nonzeros in increasing k, the order of the dense CUDA-core product, and the
+// -1/J scaling is that product's epilogue.  With an RK stage (rk.mode >= 0)
+// the result k is not stored; the stage combination of rk_point_kernel is
+// applied at once (real elements only): mode 0: acc = u + a k, tmp = u + b k;
+// mode 1: acc += a k, tmp = u + b k; mode 2: u = acc + a k.
+constexpr int DS_NNZ = 24;
+constexpr int DS_THREADS = 512;
+template <typename T>
+struct RkArgs {
+    int mode;                  // -1: store R
+    T a, b;
+    T *u, *acc, *tmp;
+    int64_t nelem;
+};
+
+// rows per prefetch chunk of a warp: their 1/J (and RK registers) are loaded
+// while the previous chunk's sums run, and their sums are interleaved
+constexpr int DS_RC = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(DS_THREADS, 2)
+div_sparse_kernel(int nupts, int K, int nnz, int nvars, const SpPair<T>* __restrict__ ent,
+                  const T* __restrict__ Df, const T* __restrict__ F, int nf, int64_t N, T* __restrict__ R,
+                  const T* __restrict__ rcp, int64_t ld, RkArgs<T> rk) {
+    constexpr int TN = 32, NW = DS_THREADS / 32;
+    constexpr int EPC = 16 / sizeof(T), CPR = TN / EPC;
+    extern __shared__ __align__(16) unsigned char ds_smem[];
+    SpPair<T>* et = (SpPair<T>*)ds_smem;                          // [nupts][nnz] operator entries
+    T* tile = (T*)(ds_smem + (((size_t)nupts * nnz * sizeof(SpPair<T>) + 15) & ~(size_t)15));   // [K][TN]
+    const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+    for (int e = tid; e < nupts * nnz; e += DS_THREADS) et[e] = ent[e];
+    const int ntiles = (int)(N / TN);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t col0 = tile_col0(t, nvars, ld, TN);
+        const int64_t col = col0 + lane;
+        const int64_t n = col % ld;
+        __syncthreads();                                          // the previous tile is consumed
+        for (int e = tid; e < K * CPR; e += DS_THREADS) {
+            const int k = e / CPR, q = e % CPR;
+            const T* src = k < nf ? Df + (int64_t)k * N : F + (int64_t)(k - nf) * N;
+            cp_async16(tile + (size_t)k * TN + q * EPC, src + col0 + q * EPC);
+        }
+        T r[DS_RC], ua[DS_RC], aa[DS_RC];
+        auto fetch = [&](int s0) {
+#pragma unroll
+            for (int c = 0; c < DS_RC; ++c) {
+                const int s = min(s0 + c * NW, nupts - 1);
+                const int64_t i = (int64_t)s * N + col;
+                r[c] = __ldg(rcp + (int64_t)s * ld + n);
+                if (rk.mode == 0 || rk.mode == 1) ua[c] = rk.u[i];
+                if (rk.mode == 1 || rk.mode == 2) aa[c] = rk.acc[i];
+            }
+        };
+        fetch(w);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+        for (int s0 = w; s0 < nupts; s0 += DS_RC * NW) {
+            T acc[DS_RC];
+            const SpPair<T>* er[DS_RC];
+#pragma unroll
+            for (int c = 0; c < DS_RC; ++c) {
+                acc[c] = T(0);
+                er[c] = et + (size_t)min(s0 + c * NW, nupts - 1) * nnz;
+            }
+#pragma unroll 4
+            for (int j = 0; j < nnz; ++j)
+#pragma unroll
+                for (int c = 0; c < DS_RC; ++c) {
+                    const SpPair<T> en = er[c][j];
+                    acc[c] = fma(en.v, tile[(size_t)en.k * TN + lane], acc[c]);
+                }
+#pragma unroll
+            for (int c = 0; c < DS_RC; ++c) {
+                const int s = s0 + c * NW;
+                if (s >= nupts) break;
+                const T v = -acc[c] * r[c];
+                const int64_t i = (int64_t)s * N + col;
+                if (rk.mode < 0) {
+                    R[i] = v;
+                } else if (n < rk.nelem) {
+                    if (rk.mode == 2) {
+                        rk.u[i] = aa[c] + rk.a * v;
+                    } else {
+                        rk.acc[i] = (rk.mode == 0 ? ua[c] : aa[c]) + rk.a * v;
+                        rk.tmp[i] = ua[c] + rk.b * v;
+                    }
+                }
+            }
+            if (s0 + DS_RC * NW < nupts) fetch(s0 + DS_RC * NW);
+        }
+    }
+}
+
+template <typename T>
+static size_t div_smem(int nupts, int nfpts, int ndims, int nnz) {
+    return (((size_t)nupts * nnz * sizeof(SpPair<T>) + 15) & ~(size_t)15) +
+           (size_t)(nfpts + ndims * nupts) * 32 * sizeof(T);
+}
+
+// R (or an RK stage, rk.mode >= 0) through the structured kernel (B.ds_nnz > 0)
+template <typename T>
+static cudaError_t div_sparse(const DevBlock& Bk, int ndims, void* R, RkArgs<T> rk, cudaStream_t st) {
+    const int64_t N = (int64_t)Bk.nvars * Bk.ld;
+    if (N % 32 != 0 || Bk.ld % 128 != 0 || ((uintptr_t)Bk.Uf | (uintptr_t)Bk.Q) % 16 != 0)
+        return cudaErrorInvalidValue;
+    if (rk.mode < 0 && !R) return cudaErrorInvalidValue;
+    const int K = Bk.nfpts + ndims * Bk.nupts;
+    const size_t sm = div_smem<T>(Bk.nupts, Bk.nfpts, ndims, Bk.ds_nnz);
+    const int grid = persistent_grid((const void*)div_sparse_kernel<T>, DS_THREADS, sm, (int)(N / 32));
+    div_sparse_kernel<T><<<(unsigned)grid, DS_THREADS, sm, st>>>(
+        Bk.nupts, K, Bk.ds_nnz, Bk.nvars, (const SpPair<T>*)Bk.ds_ent, (const T*)Bk.Uf, (const T*)Bk.Q, Bk.nfpts, N,
+        (T*)R, (const T*)Bk.rcpdjac, Bk.ld, rk);
+    return cudaGetLastError();
+}
+
+cudaError_t div_prepare(int nupts, int nfpts, int ndims, int nnz, bool fp64) {
+    constexpr int kMax = 227 * 1024;
+    const size_t sm = fp64 ? div_smem<double>(nupts, nfpts, ndims, nnz) : div_smem<float>(nupts, nfpts, ndims, nnz);
+    if (sm > (size_t)kMax) return cudaErrorInvalidValue;
+    return fp64 ? cudaFuncSetAttribute((const void*)div_sparse_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMax)
+                : cudaFuncSetAttribute((const void*)div_sparse_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
+}
+
+// ============================================================ tensor-line operators
+// On quadrilaterals and hexahedra with tensor Gauss-Legendre solution points
+// (xi fastest) and Gauss-Legendre face points, the corrected gradient
+// (Eq. tquptsm) and the divergence (Eq. tdivflux) act along lines: with x the
+// n = p+1 values on a line in direction i followed by the two values at the
+// flux points that end it (the xi_i = -1 face, then +1),
+//     Q~_i(line point q) = sum_r A[q][r] x_r   (x: U - u_ref, then C)
+//     R~(s) = sum_i sum_r B[q_i(s)][r] x_r     (x: F~_i, then D~)
+// where A (rows of [M6 | M4 - M6 M0]) and B (rows of [M3 | M1 - M3 M2]) are
+// n x (n+2) matrices that the set-up checks to be the same for every line
+// and direction (sum factorisation).  A line's n+2 values are read once for
+// n outputs, and the matrix lives in the constant bank (a kernel argument),
+// so a tile column costs D n^(D-1) (n+2) shared reads instead of the
+// D n^D (n+2) of the row-wise form.  A CTA owns 32 columns of one variable
+// (persistent, tiles in variable-fastest order): it stages the tile, forms
+// the lines (warp w: lines w, w + NW, ...), and
+//  - gradient: writes Q~ to shared memory, then transforms it point by point
+//    with the metric terms (prefetched a chunk ahead) into Q;
+//  - divergence: accumulates the directions in shared memory and, on the
+//    last one, applies -1/J and, inside RK4, the stage combination.
+constexpr int LN_MAX = 6;                          // n = p + 1
+template <typename T>
+struct LineMat {
+    T a[LN_MAX * (LN_MAX + 2)];                    // [n][n+2]
+};
+// threads per CTA and the CTAs per SM that registers must allow (shared memory
+// allows two hexahedral FP32 tiles at p = 4, one FP64 tile, and many
+// quadrilateral ones)
+template <int D> struct LnCfg;
+template <> struct LnCfg<2> { static constexpr int THREADS = 256; };
+template <> struct LnCfg<3> { static constexpr int THREADS = 512; };
+template <typename T, int D> struct LnMinB { static constexpr int V = D == 3 ? (sizeof(T) == 4 ? 2 : 1) : (sizeof(T) == 4 ? 3 : 2); };
+__host__ __device__ constexpr int ln_pow(int n, int d) { return d == 0 ? 1 : n * ln_pow(n, d - 1); }
+
+// line m of direction I: its first point (the stride is ln_stride<I>)
+template <int D, int n, int I>
+__device__ __forceinline__ int line_base(int m) {
+    if constexpr (D == 2) return I == 0 ? m * n : m;             // s = a + n b
+    else return I == 0 ? m * n : (I == 1 ? m % n + n * n * (m / n) : m);   // s = a + n b + n^2 c
+}
+template <int n, int I>
+__host__ __device__ constexpr int ln_stride() { return I == 0 ? 1 : (I == 1 ? n : n * n); }
+
+// one line of direction I through a [rows][32] tile: x = the n line values
+// (rows row0 + base + q stride) and the two end values (rows fa, fb); out[q] =
+// sum_r M[q][r] x_r, summed in that order
+template <typename T, int n, int I>
+__device__ __forceinline__ void line_apply(const T* __restrict__ tl, int row0, int base, int fa, int fb,
+                                           const LineMat<T>& M, int lane, T* out) {
+    constexpr int TN = 32, S = ln_stride<n, I>();
+    T x[n + 2];
+    const T* p = tl + (size_t)(row0 + base) * TN + lane;
+#pragma unroll
+    for (int q = 0; q < n; ++q) x[q] = p[q * S * TN];
+    x[n] = tl[(size_t)fa * TN + lane];
+    x[n + 1] = tl[(size_t)fb * TN + lane];
+#pragma unroll
+    for (int q = 0; q < n; ++q) {
+        T y = T(0);
+#pragma unroll
+        for (int r = 0; r < n + 2; ++r) y = fma(M.a[q * (n + 2) + r], x[r], y);
+        out[q] = y;
+    }
+}
+
+// Gradient: a CTA owns 32 elements and walks their variables in turn (the
+// next variable's tile is copied while the current one is formed); each warp
+// keeps the metric terms of its points in registers for all variables.
+template <typename T, int D, int n>
+__global__ void __launch_bounds__(LnCfg<D>::THREADS, D == 3 ? 1 : 2)
+grad_line_kernel(int nfpts, const int* __restrict__ fl, const LineMat<T> A, const T* __restrict__ Cf,
+                 const T* __restrict__ U, int64_t ld, T* __restrict__ Q, const T* __restrict__ smat,
+                 const T* __restrict__ rcp, Sub<T> sub) {
+    constexpr int NV = D + 2, NU = ln_pow(n, D), NL = ln_pow(n, D - 1), NLT = D * NL, TN = 32;
+    constexpr int NT = LnCfg<D>::THREADS, NW = NT / 32, PW = (NU + NW - 1) / NW, LW = (NLT + NW - 1) / NW;
+    constexpr int EPC = 16 / sizeof(T), CPR = TN / EPC;
+    extern __shared__ __align__(16) unsigned char ln_smem[];
+    int* fls = (int*)ln_smem;                                     // [NLT][2] flux points ending each line
+    const int K = nfpts + NU;
+    T* tile0 = (T*)(ln_smem + ((NLT * 2 * sizeof(int) + 15) & ~15));   // 2 x [K][TN]: C, then U - u_ref
+    T* qt = tile0 + (size_t)2 * K * TN;                           // [D NU][TN]: Q~
+    const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+    const int64_t N = (int64_t)NV * ld;
+    for (int e = tid; e < NLT * 2; e += NT) fls[e] = fl[e];
+    const int ntiles = (int)(ld / TN);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t e0 = (int64_t)t * TN;
+        auto copy = [&](int a, T* tl) {
+            const T* c0 = Cf + (int64_t)a * ld + e0;
+            const T* u0 = U + (int64_t)a * ld + e0;
+            for (int e = tid; e < K * CPR; e += NT) {
+                const int k = e / CPR, q = e % CPR;
+                const T* src = k < nfpts ? c0 + (int64_t)k * N : u0 + (int64_t)(k - nfpts) * N;
+                cp_async16(tl + (size_t)k * TN + q * EPC, src + q * EPC);
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        };
+        copy(0, tile0);
+        // metric terms of this warp's points (s = w + k NW), kept for every variable
+        T adj[PW][D][D], rr[PW];
+        {
+            const T* mp = smat + e0 + lane;
+            const int64_t ps = (int64_t)NU * ld;
+#pragma unroll
+            for (int k = 0; k < PW; ++k) {
+                const int s = min(w + k * NW, NU - 1);
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) adj[k][i][j] = __ldg(mp + (i * D + j) * ps + (int64_t)s * ld);
+                rr[k] = __ldg(rcp + (int64_t)s * ld + e0 + lane);
+            }
+        }
+#pragma unroll 1
+        for (int a = 0; a < NV; ++a) {
+            T* tl = tile0 + (size_t)(a & 1) * K * TN;
+            if (a + 1 < NV) {
+                copy(a + 1, tile0 + (size_t)((a + 1) & 1) * K * TN);
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            }
+            const T sv = sub.v[a];
+            if (sv != T(0))
+                for (int e = tid; e < K * CPR; e += NT) {
+                    const int k = e / CPR, q = e % CPR;
+                    if (k < nfpts) continue;
+                    T* tt = tl + (size_t)k * TN + q * EPC;
+#pragma unroll
+                    for (int j = 0; j < EPC; ++j) tt[j] -= sv;
+                }
+            __syncthreads();
+            // the lines: Q~_i at their points
+#pragma unroll
+            for (int k = 0; k < LW; ++k) {
+                const int l = w + k * NW;
+                if (l >= NLT) break;
+                const int i = l / NL, m = l % NL;
+                T y[n];
+                int base, S;
+                if (i == 0) {
+                    base = line_base<D, n, 0>(m); S = ln_stride<n, 0>();
+                    line_apply<T, n, 0>(tl, nfpts, base, fls[2 * l], fls[2 * l + 1], A, lane, y);
+                } else if (i == 1) {
+                    base = line_base<D, n, 1>(m); S = ln_stride<n, 1>();
+                    line_apply<T, n, 1>(tl, nfpts, base, fls[2 * l], fls[2 * l + 1], A, lane, y);
+                } else {
+                    base = line_base<D, n, D - 1>(m); S = ln_stride<n, D - 1>();
+                    line_apply<T, n, D - 1>(tl, nfpts, base, fls[2 * l], fls[2 * l + 1], A, lane, y);
+                }
+                T* qp = qt + (size_t)(i * NU + base) * TN + lane;
+#pragma unroll
+                for (int q = 0; q < n; ++q) qp[(size_t)q * S * TN] = y[q];
+            }
+            __syncthreads();
+            // the transform of this warp's points: Q = J^{-T} Q~
+            T* qo = Q + (int64_t)a * ld + e0 + lane;
+#pragma unroll
+            for (int k = 0; k < PW; ++k) {
+                const int s = w + k * NW;
+                if (s >= NU) break;
+                T g[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) g[i] = qt[(size_t)(i * NU + s) * TN + lane];
+                T* qs = qo + (int64_t)s * N;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) acc += adj[k][i][j] * g[i];
+                    qs[(int64_t)j * NU * N] = acc * rr[k];
+                }
+            }
+        }
+    }
+}
+
+// Divergence: a CTA owns 32 columns of one variable (persistent, tiles in
+// variable-fastest order); the directions are summed in shared memory and
+// the last one applies -1/J and the RK stage.
+template <typename T, int D, int n>
+__global__ void __launch_bounds__(LnCfg<D>::THREADS, LnMinB<T, D>::V)
+div_line_kernel(int nfpts, int nvars, const int* __restrict__ fl, const LineMat<T> B, const T* __restrict__ Df,
+                const T* __restrict__ F, int64_t N, T* __restrict__ R, const T* __restrict__ rcp, int64_t ld,
+                RkArgs<T> rk) {
+    constexpr int NU = ln_pow(n, D), NL = ln_pow(n, D - 1), NLT = D * NL, TN = 32, NT = LnCfg<D>::THREADS;
+    constexpr int NW = NT / 32, KL = (NL + NW - 1) / NW;          // lines per warp and direction
+    constexpr int EPC = 16 / sizeof(T), CPR = TN / EPC;
+    extern __shared__ __align__(16) unsigned char ln_smem[];
+    int* fls = (int*)ln_smem;
+    T* tile = (T*)(ln_smem + ((NLT * 2 * sizeof(int) + 15) & ~15));   // [nfpts + D NU][TN]: D~, then F~
+    T* racc = tile + (size_t)(nfpts + D * NU) * TN;               // [NU][TN]: directions summed so far
+    const int K = nfpts + D * NU;
+    const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+    for (int e = tid; e < NLT * 2; e += NT) fls[e] = fl[e];
+    const int ntiles = (int)(N / TN);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t col0 = tile_col0(t, nvars, ld, TN);
+        const int64_t col = col0 + lane;
+        const int64_t nn = col % ld;
+        __syncthreads();
+        for (int e = tid; e < K * CPR; e += NT) {
+            const int k = e / CPR, q = e % CPR;
+            const T* src = k < nfpts ? Df + (int64_t)k * N : F + (int64_t)(k - nfpts) * N;
+            cp_async16(tile + (size_t)k * TN + q * EPC, src + col0 + q * EPC);
+        }
+        // the last direction's lines of this warp finish their points: their 1/J
+        // (and RK registers) are loaded while the tile arrives
+        T pr[KL][n], pu[KL][n], pa[KL][n];
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+            const int base = line_base<D, n, D - 1>(min(w + k * NW, NL - 1));
+#pragma unroll
+            for (int q = 0; q < n; ++q) {
+                const int s = base + q * ln_stride<n, D - 1>();
+                const int64_t ix = (int64_t)s * N + col;
+                pr[k][q] = __ldg(rcp + (int64_t)s * ld + nn);
+                if (rk.mode == 0 || rk.mode == 1) pu[k][q] = rk.u[ix];
+                if (rk.mode == 1 || rk.mode == 2) pa[k][q] = rk.acc[ix];
+            }
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+        // direction 0: the first partial sums
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+            const int m = w + k * NW;
+            if (m >= NL) break;
+            const int base = line_base<D, n, 0>(m);
+            T y[n];
+            line_apply<T, n, 0>(tile, nfpts, base, fls[2 * m], fls[2 * m + 1], B, lane, y);
+            T* rp = racc + (size_t)base * TN + lane;
+#pragma unroll
+            for (int q = 0; q < n; ++q) rp[(size_t)q * ln_stride<n, 0>() * TN] = y[q];
+        }
+        __syncthreads();
+        if constexpr (D == 3) {
+#pragma unroll
+            for (int k = 0; k < KL; ++k) {
+                const int m = w + k * NW;
+                if (m >= NL) break;
+                const int l = NL + m, base = line_base<D, n, 1>(m);
+                T y[n];
+                line_apply<T, n, 1>(tile, nfpts + NU, base, fls[2 * l], fls[2 * l + 1], B, lane, y);
+                T* rp = racc + (size_t)base * TN + lane;
+#pragma unroll
+                for (int q = 0; q < n; ++q) rp[(size_t)q * ln_stride<n, 1>() * TN] += y[q];
+            }
+            __syncthreads();
+        }
+        // the last direction, -1/J and the RK stage
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+            const int m = w + k * NW;
+            if (m >= NL) break;
+            constexpr int I = D - 1, S = ln_stride<n, D - 1>();
+            const int l = I * NL + m, base = line_base<D, n, I>(m);
+            T y[n];
+            line_apply<T, n, I>(tile, nfpts + I * NU, base, fls[2 * l], fls[2 * l + 1], B, lane, y);
+            const T* rp = racc + (size_t)base * TN + lane;
+#pragma unroll
+            for (int q = 0; q < n; ++q) {
+                const T v = -(rp[(size_t)q * S * TN] + y[q]) * pr[k][q];
+                const int64_t ix = (int64_t)(base + q * S) * N + col;
+                if (rk.mode < 0) {
+                    R[ix] = v;
+                } else if (nn < rk.nelem) {
+                    if (rk.mode == 2) {
+                        rk.u[ix] = pa[k][q] + rk.a * v;
+                    } else {
+                        rk.acc[ix] = (rk.mode == 0 ? pu[k][q] : pa[k][q]) + rk.a * v;
+                        rk.tmp[ix] = pu[k][q] + rk.b * v;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+static size_t line_smem(int kind, int ndims, int n, int nfpts) {
+    const int nu = ln_pow(n, ndims), nlt = ndims * ln_pow(n, ndims - 1);
+    // gradient: two variable tiles (C, U) and Q~; divergence: one tile (D~, F~) and the sums
+    const size_t rows = kind == 0 ? 2 * ((size_t)nfpts + nu) + (size_t)ndims * nu : (size_t)nfpts + ndims * nu + nu;
+    return (((size_t)nlt * 2 * sizeof(int) + 15) & ~(size_t)15) + rows * 32 * sizeof(T);
+}
+
+template <typename T, int D, int n>
+static const void* line_fn(int kind) {
+    return kind == 0 ? (const void*)grad_line_kernel<T, D, n> : (const void*)div_line_kernel<T, D, n>;
+}
+
+template <typename T, int D>
+static const void* line_fn_n(int kind, int n) {
+    switch (n) {
+        case 2: return line_fn<T, D, 2>(kind);
+        case 3: return line_fn<T, D, 3>(kind);
+        case 4: return line_fn<T, D, 4>(kind);
+        case 5: return line_fn<T, D, 5>(kind);
+        case 6: return line_fn<T, D, 6>(kind);
+        default: return nullptr;
+    }
+}
+
+template <typename T>
+static const void* line_kernel(int kind, int ndims, int n) {
+    return ndims == 2 ? line_fn_n<T, 2>(kind, n) : line_fn_n<T, 3>(kind, n);
+}
+
+cudaError_t line_prepare(int kind, int ndims, int n, int nfpts, bool fp64) {
+    constexpr int kMax = 227 * 1024;
+    if (n < 2 || n > LN_MAX || (ndims != 2 && ndims != 3)) return cudaErrorInvalidValue;
+    const size_t sm = fp64 ? line_smem<double>(kind, ndims, n, nfpts) : line_smem<float>(kind, ndims, n, nfpts);
+    if (sm > (size_t)kMax) return cudaErrorInvalidValue;
+    const void* f = fp64 ? line_kernel<double>(kind, ndims, n) : line_kernel<float>(kind, ndims, n);
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
+}
+
+template <typename T, int D, int n>
+static void launch_grad_line(const DevBlock& Bk, const void* U, int grid, size_t sm, Sub<T> sub, cudaStream_t st) {
+    LineMat<T> A{};
+    for (int e = 0; e < n * (n + 2); ++e) A.a[e] = (T)Bk.ln_A[e];
+    grad_line_kernel<T, D, n><<<(unsigned)grid, LnCfg<D>::THREADS, sm, st>>>(
+        Bk.nfpts, Bk.ln_fl, A, (const T*)Bk.Qf, (const T*)U, Bk.ld, (T*)Bk.Q, (const T*)Bk.smat,
+        (const T*)Bk.rcpdjac, sub);
+}
+
+template <typename T, int D, int n>
+static void launch_div_line(const DevBlock& Bk, void* R, RkArgs<T> rk, int grid, size_t sm, cudaStream_t st) {
+    LineMat<T> B{};
+    for (int e = 0; e < n * (n + 2); ++e) B.a[e] = (T)Bk.ln_B[e];
+    div_line_kernel<T, D, n><<<(unsigned)grid, LnCfg<D>::THREADS, sm, st>>>(
+        Bk.nfpts, Bk.nvars, Bk.ln_fl, B, (const T*)Bk.Uf, (const T*)Bk.Q, (int64_t)Bk.nvars * Bk.ld, (T*)R,
+        (const T*)Bk.rcpdjac, Bk.ld, rk);
+}
+
+// Q = J^{-T} Q~ (kind 0) or R / an RK stage (kind 1) through the tensor-line
+// kernels (B.ln_n > 0)
+template <typename T, int D>
+static cudaError_t line_op(const DevBlock& Bk, int kind, const void* U, void* R, Sub<T> sub, RkArgs<T> rk,
+                           cudaStream_t st) {
+    const int n = Bk.ln_n;
+    const int64_t N = (int64_t)Bk.nvars * Bk.ld;
+    if (N % 32 != 0 || Bk.ld % 128 != 0 || ((uintptr_t)Bk.Uf | (uintptr_t)Bk.Q | (uintptr_t)Bk.Qf) % 16 != 0 ||
+        (kind == 0 && (uintptr_t)U % 16 != 0) || (kind == 1 && rk.mode < 0 && !R))
+        return cudaErrorInvalidValue;
+    const size_t sm = line_smem<T>(kind, D, n, Bk.nfpts);
+    const void* fn = line_kernel<T>(kind, D, n);
+    if (!fn) return cudaErrorInvalidValue;
+    if (kind == 0 && Bk.nvars != D + 2) return cudaErrorInvalidValue;
+    // gradient: one tile per 32 elements (all variables); divergence: per variable
+    const int grid = persistent_grid(fn, LnCfg<D>::THREADS, sm, (int)((kind == 0 ? Bk.ld : N) / 32));
+    switch (n) {
+#define FR_LN_CASE(NN)                                                              \
+        case NN:                                                                    \
+            if (kind == 0) launch_grad_line<T, D, NN>(Bk, U, grid, sm, sub, st);   \
+            else launch_div_line<T, D, NN>(Bk, R, rk, grid, sm, st);               \
+            break;
+        FR_LN_CASE(2) FR_LN_CASE(3) FR_LN_CASE(4) FR_LN_CASE(5) FR_LN_CASE(6)
+#undef FR_LN_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // Operator product dispatch: CUDA-core GEMM for FP64 / FP32, tensor-core
 // split-precision GEMM (fr_tc.cu) for TF32x3 / BF16x3.
 template <typename T>
@@ -999,6 +1733,22 @@ static int dense_blocks(const DevCtx& c) {
     return n;
 }
 
+// whether block B's divergence / gradient takes a structured kernel: option
+// value 1 the tensor-line kernel where the block has the line form, else the
+// row-wise one; 2 the row-wise kernel only
+static bool div_structured(const DevCtx& c, const DevBlock& B) {
+    return (c.structured_div == 1 && B.ln_div) || (c.structured_div != 0 && B.ds_nnz > 0);
+}
+static bool grad_structured(const DevCtx& c, const DevBlock& B) {
+    return (c.structured_grad == 1 && B.ln_grad) || (c.structured_grad != 0 && B.gs_nnz > 0);
+}
+template <typename T, int D>
+static cudaError_t grad_struct(const DevCtx& c, const DevBlock& B, const void* u, cudaStream_t st, Sub<T> sub) {
+    if (c.structured_grad == 1 && B.ln_grad)
+        return line_op<T, D>(B, 0, u, nullptr, sub, RkArgs<T>{-1, T(0), T(0), nullptr, nullptr, nullptr, 0}, st);
+    return grad_sparse<T, D>(B, u, st, sub);
+}
+
 // Tensor-core products of every block in one launch (the blocks' problems
 // form one work list), when the context groups them.
 static bool grouped(const DevCtx& c) {
@@ -1116,25 +1866,34 @@ phase_b1:
         if (c.precision >= 2) {
             std::vector<tc::GradXform> gx(c.blocks.size());
             std::vector<tc::GemmProblem> PQ, PF;
+            std::vector<size_t> qb;              // block of each tensor-core gradient problem
             for (size_t b = 0; b < c.blocks.size(); ++b) {
                 DevBlock& B = c.blocks[b];
                 const int64_t N = (int64_t)NV * B.ld;
-                gx[b] = tc::GradXform{(const float*)B.smat, D, B.nupts, NV};
-                PQ.push_back({D * B.nupts, B.nfpts, B.nupts, B.tcQ, (const float*)B.Qf, (const float*)u[b], N,
-                              (float*)B.Q, (const float*)B.rcpdjac, B.ld, 2, &gx[b], nullptr});
+                if (grad_structured(c, B)) {
+                    // structured blocks: FP32 multiply-adds of the nonzeros, transform included
+                    prof_begin(c, K_TGRADU, st);
+                    FR_TRY((grad_struct<T, D>(c, B, u[b], st, sub)));
+                    prof_end(c, st);
+                } else {
+                    gx[b] = tc::GradXform{(const float*)B.smat, D, B.nupts, NV};
+                    PQ.push_back({D * B.nupts, B.nfpts, B.nupts, B.tcQ, (const float*)B.Qf, (const float*)u[b], N,
+                                  (float*)B.Q, (const float*)B.rcpdjac, B.ld, 2, &gx[b], nullptr});
+                    qb.push_back(b);
+                }
                 for (int i = 0; i < D; ++i)
                     PF.push_back({B.nfpts, B.nupts, 0, B.tcM0, (const float*)B.Q + (int64_t)i * B.nupts * N, nullptr,
                                   N, (float*)B.Qf + (int64_t)i * B.nfpts * N, nullptr, B.ld, 0, nullptr, nullptr});
             }
-            if (grouped(c)) {
+            if (grouped(c) && PQ.size() > 1) {
                 prof_begin(c, K_TGRADU, st);
                 FR_TRY(run_group(c, 0, PQ, sr, TUNE_TGRADU, st));
                 prof_end(c, st);
             } else {
-                for (size_t b = 0; b < c.blocks.size(); ++b) {
+                for (size_t i = 0; i < PQ.size(); ++i) {
                     prof_begin(c, K_TGRADU, st);
-                    FR_TRY(tc::gemm_group(c.precision == 3 ? 0 : 1, 0, &PQ[b], 1, sr, c.flags, st, c.tc_wait_limit,
-                                          c.blocks[b].tune[TUNE_TGRADU]));
+                    FR_TRY(tc::gemm_group(c.precision == 3 ? 0 : 1, 0, &PQ[i], 1, sr, c.flags, st, c.tc_wait_limit,
+                                          c.blocks[qb[i]].tune[TUNE_TGRADU]));
                     prof_end(c, st);
                 }
             }
@@ -1186,14 +1945,20 @@ phase_b1:
             for (size_t b = 0; b < c.blocks.size(); ++b) {
                 DevBlock& B = c.blocks[b];
                 int64_t N = (int64_t)NV * B.ld;
-                prof_begin(c, K_TGRADU, st);
-                FR_TRY(op_gemm<T>(c, B.opQ, B.tcQ, D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.Qf, u[b], N, B.Q, 0,
-                                  nullptr, B.ld, st, B.nfpts, B.nfpts + B.nupts, sub));
-                prof_end(c, st);
-                prof_begin(c, K_GRADCORU, st);
-                grad_transform_kernel<T, D><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
-                    B.nupts, B.nelem, B.ld, (const T*)B.smat, (const T*)B.rcpdjac, (T*)B.Q);
-                prof_end(c, st);
+                if (grad_structured(c, B)) {
+                    prof_begin(c, K_TGRADU, st);
+                    FR_TRY((grad_struct<T, D>(c, B, u[b], st, sub)));
+                    prof_end(c, st);
+                } else {
+                    prof_begin(c, K_TGRADU, st);
+                    FR_TRY(op_gemm<T>(c, B.opQ, B.tcQ, D * B.nupts, B.nfpts + B.nupts, B.nfpts, B.Qf, u[b], N, B.Q, 0,
+                                      nullptr, B.ld, st, B.nfpts, B.nfpts + B.nupts, sub));
+                    prof_end(c, st);
+                    prof_begin(c, K_GRADCORU, st);
+                    grad_transform_kernel<T, D><<<pw_grid(B.nelem, B.nupts), 128, 0, st>>>(
+                        B.nupts, B.nelem, B.ld, (const T*)B.smat, (const T*)B.rcpdjac, (T*)B.Q);
+                    prof_end(c, st);
+                }
                 for (int i = 0; i < D; ++i) {
                     prof_begin(c, K_GRADFPTS, st);
                     if (c.structured_interp && B.sp_nnz > 0)
@@ -1291,12 +2056,31 @@ phase_c2:
                 (const T*)g.magR, c.prm);
         prof_end(c, st);
     }
-    // 8. R = -J^{-1} [M3 D~ + (M1 - M3 M2) F~]  (tdivtpcorf + negdivconf)
-    if (grouped(c)) {
+    // 8. R = -J^{-1} [M3 D~ + (M1 - M3 M2) F~]  (tdivtpcorf + negdivconf); blocks
+    // whose divergence operator is structured (tensor elements) take the
+    // structured kernel (with the RK stage, if any), the others the operator GEMM
+    int ndense = 0;
+    for (size_t b = 0; b < c.blocks.size(); ++b) {
+        DevBlock& B = c.blocks[b];
+        if (!div_structured(c, B)) {
+            ++ndense;
+            continue;
+        }
+        RkArgs<T> ra{-1, T(0), T(0), nullptr, nullptr, nullptr, B.nelem};
+        if (rk) ra = RkArgs<T>{rk->mode, T(rk->a), T(rk->b), (T*)rk->u[b], (T*)B.rk_acc, (T*)B.rk_tmp, B.nelem};
+        prof_begin(c, K_TDIVF, st);
+        if (c.structured_div == 1 && B.ln_div)
+            FR_TRY((line_op<T, D>(B, 1, nullptr, rk ? nullptr : r[b], sub, ra, st)));
+        else
+            FR_TRY(div_sparse<T>(B, D, rk ? nullptr : r[b], ra, st));
+        prof_end(c, st);
+    }
+    if (grouped(c) && ndense > 1) {
         std::vector<tc::RkFuse> f(c.blocks.size());
         std::vector<tc::GemmProblem> P;
         for (size_t b = 0; b < c.blocks.size(); ++b) {
             DevBlock& B = c.blocks[b];
+            if (div_structured(c, B)) continue;
             if (rk) f[b] = tc::RkFuse{rk->mode, (float)rk->a, (float)rk->b, (float*)rk->u[b], (float*)B.rk_acc,
                                       (float*)B.rk_tmp, B.nelem};
             P.push_back({B.nupts, B.nfpts, D * B.nupts, B.tcR, (const float*)B.Uf, (const float*)B.Q,
@@ -1310,6 +2094,7 @@ phase_c2:
     }
     for (size_t b = 0; b < c.blocks.size(); ++b) {
         DevBlock& B = c.blocks[b];
+        if (div_structured(c, B)) continue;
         prof_begin(c, K_TDIVF, st);
         if (rk && c.precision >= 2) {
             const tc::RkFuse f{rk->mode, (float)rk->a, (float)rk->b, (float*)rk->u[b], (float*)B.rk_acc,
@@ -1363,15 +2148,17 @@ template <typename T>
 static cudaError_t rk4_impl(DevCtx& c, void* const* u, double dt, int nsteps, cudaStream_t st) {
     std::vector<void*> tmp(c.blocks.size());
     for (size_t b = 0; b < c.blocks.size(); ++b) tmp[b] = c.blocks[b].rk_tmp;
-    bool fuse = c.precision >= 2;
-    for (auto& B : c.blocks) fuse = fuse && tdivf_fused(c, B);
+    // the stage combination runs in the divergence kernel when every block's
+    // divergence can carry it (structured kernel, or the tensor-core GEMM)
+    bool fuse = true;
+    for (auto& B : c.blocks) fuse = fuse && (div_structured(c, B) || tdivf_fused(c, B));
     for (int step = 0; step < nsteps; ++step) {
         const double a_acc[4] = {dt / 6, dt / 3, dt / 3, dt / 6};
         const double a_tmp[3] = {dt / 2, dt / 2, dt};
         for (int s = 0; s < 4; ++s) {
             // stage 1 reads u directly; later stages read the stage state in tmp
             if (fuse) {
-                // tensor-core path: the stage combination runs in the divergence GEMM's epilogue
+                // the stage combination runs in the divergence kernel's epilogue
                 const RkStage rk{s == 0 ? 0 : (s == 3 ? 2 : 1), a_acc[s], s < 3 ? a_tmp[s] : 0.0, u};
                 cudaError_t e = c.ndims == 2 ? rhs_impl<T, 2>(c, s == 0 ? u : tmp.data(), tmp.data(), st, PH_ALL, &rk)
                                              : rhs_impl<T, 3>(c, s == 0 ? u : tmp.data(), tmp.data(), st, PH_ALL, &rk);

@@ -1,10 +1,11 @@
-"""RK4 on the tensor-core paths runs each stage combination inside the
-divergence GEMM's epilogue.  It must equal RK4 assembled from separate
-right-hand-side calls up to FP32 rounding, and leave the padding columns of
-the state untouched; and fr_rk4 in every single precision (the fused
-epilogue on TF32x3 / BF16x3, the stage kernel on FP32; CUDA-graph replay on
-and off) must match the FP64 oracle's RK4 (end of Sec. 2) from the same
-FP32-rounded state within the RHS bound integrated over the interval."""
+"""fr_rk4 runs each stage combination inside the divergence kernel: the
+structured kernel on tensor elements (every precision) or the tensor-core
+GEMM's epilogue (split precisions, dense operator).  It must equal RK4
+assembled from separate right-hand-side calls up to FP32 rounding, and leave
+the padding columns of the state untouched; and fr_rk4 in every single
+precision (CUDA-graph replay on and off) must match the FP64 oracle's RK4
+(end of Sec. 2) from the same FP32-rounded state within the RHS bound
+integrated over the interval."""
 
 import numpy as np
 import pytest
@@ -26,13 +27,16 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("graphs", [0, 1])
-def test_fused_rk4_equals_composed_rk4(torch, prec, graphs):
+@pytest.mark.parametrize("structured", [0, 1])
+def test_fused_rk4_equals_composed_rk4(torch, prec, graphs, structured):
     from paper_1312_1638_b300 import fr
     m = periodic_box("hex", 3, 0.0, 2 * np.pi, jitter=0.1, seed=5)       # 27 elements: ld = 128 > nelem
     s = fr.Solver(m, 3, "ns", prec, device=0, **NS_PRM)
     s.set_option("graphs", graphs)
+    s.set_option("structured_div", structured)
+    s.set_option("structured_grad", structured)
     X = s.solution_points(0)
     U = fields.taylor_green(X, M=0.3).transpose(1, 0, 2)
     ne = U.shape[2]
@@ -60,7 +64,7 @@ def test_fused_rk4_equals_composed_rk4(torch, prec, graphs):
     # componentwise bound tol * S.  Bound: tol * 2 S(u0) * T plus FP32 rounding.
     prm = {k: v for k, v in NS_PRM.items() if not k.startswith("ref_")}
     _, S = FRSystem(m, 3, "ns", **prm).rhs([U], scale=True)
-    tol = {"tf32x3": 4e-6, "bf16x3": 1e-4}[prec]
+    tol = {"fp32": 2e-6, "tf32x3": 4e-6, "bf16x3": 1e-4}[prec]
     bound = tol * 2 * S[0] * nsteps * dt + 16 * np.finfo(np.float32).eps * np.abs(B) * nsteps
     assert np.all(np.abs(A - B) <= bound), float(np.max(np.abs(A - B) / bound))
     assert torch.all(a[0][:, :, ne:] == 12345.0)                         # padding untouched
