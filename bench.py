@@ -252,7 +252,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline bookkeeping
-def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False, one_side=False):
+def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False, one_side=False, with_qf=False):
     """Algorithmic (bytes, flops) of one launch of each kernel on the whole block.
 
     Bytes count every value the kernel must read or write once (state, metric
@@ -265,10 +265,13 @@ def kernel_work(name, nu, nf, V, D, nelem, npairs, s, fused=False, one_side=Fals
     if name == "disu_gemm":
         return (nu + nf) * V * s * E, 2.0 * nf * nu * V * E
     if name == "tgradu_gemm":
-        # on the tensor-core path the gradient transform (gradcoru) runs in this
-        # kernel's epilogue: + metric terms adj(J) and 1/J, read once per element
+        # the gradient transform (gradcoru) runs in this kernel (tensor-core
+        # epilogue or structured kernel): + metric terms adj(J) and 1/J, read once
+        # per element; with_qf: the structured kernel also writes Q^(f) = M5 Q
+        # (gradfpts), which then reads nothing more
         extra = (D * D * nu + nu) * s * E if fused else 0
-        return (nf + nu + D * nu) * V * s * E + extra, 2.0 * D * nu * (nf + nu) * V * E
+        qf = (D * nf * V * s * E, 2.0 * D * nf * nu * V * E) if with_qf else (0, 0.0)
+        return (nf + nu + D * nu) * V * s * E + extra + qf[0], 2.0 * D * nu * (nf + nu) * V * E + qf[1]
     if name == "gradfpts_gemm":
         return (nu + nf) * V * s * E, 2.0 * nf * nu * V * E
     if name == "tdivf_gemm":
@@ -338,13 +341,17 @@ def replica_value(ms_local, units_per_rank, world, dist=None, device="cpu"):
     return units_per_rank * world / (ms / 1e3) / 1e9, ms
 
 
-def structured_nonzeros(nu, nf, D, order):
-    """Nonzeros per output column of the products that run on structured
+def structured_nonzeros(nu, nf, D, order, with_qf=False):
+    """Multiply-adds per output column of the products that run on structured
     kernels on a hexahedral (tensor) mesh: M0 (p+1 per flux-point row, for U^(f)
-    and the gradient at flux points) and the corrected gradient [M6 | M4 - M6 M0]
-    (p+1 solution points and 2 flux points per row, D nu rows)."""
+    and the gradient at flux points), the corrected gradient [M6 | M4 - M6 M0]
+    (p+1 solution points and 2 flux points per row, D nu rows; with_qf: plus the
+    D M0 products it then forms) and the divergence [M3 | M1 - M3 M2] (per
+    direction p+1 flux values and 2 common fluxes, nu rows)."""
     p1 = order + 1
-    return {"disu_gemm": nf * p1, "gradfpts_gemm": nf * p1, "tgradu_gemm": D * nu * (p1 + 2)}
+    return {"disu_gemm": nf * p1, "gradfpts_gemm": nf * p1,
+            "tgradu_gemm": D * nu * (p1 + 2) + (D * nf * p1 if with_qf else 0),
+            "tdivf_gemm": nu * D * (p1 + 2)}
 
 
 def operator_flops_per_rhs(nu, nf, V, D, nelem):
@@ -483,10 +490,13 @@ def main():
     # nonzeros they multiply per column (M0 rows: p+1; corrected-gradient rows:
     # p+1 solution points and 2 flux points), as FP32 (FP64) multiply-adds on
     # the CUDA cores whatever the precision
-    structured = structured_nonzeros(nu, nf, D, a.order)
+    with_qf = prof.get("gradfpts_gemm", (0, 0.0))[0] == 0      # Q^(f) formed by the gradient kernel
+    structured = structured_nonzeros(nu, nf, D, a.order, with_qf)
+    fused_of = {"tgradu_gemm": True, "tdivf_gemm": True}          # transform / RK stage in the kernel
 
     def roof_of(name, launches, tms):
-        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz, tc_path or name in structured, one_side)
+        kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz, fused_of.get(name, tc_path), one_side,
+                             with_qf and name == "tgradu_gemm")
         avg = tms / launches / 1e3
         t_hbm = kb / (hbm_peak * 1e9) if kb else 0.0
         t_alu = (kf * arith[1]) / (arith[0] * 1e12) if kf else 0.0
@@ -527,7 +537,8 @@ def main():
         if not v[0]:
             continue
         d = dict(launches=v[0], ms=round(v[1], 3), share=round(v[1] / max(total_ms, 1e-9), 4))
-        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz, tc_path or k in structured, one_side)
+        b, f = kernel_work(k, nu, nf, V, D, nelem, npairs, srz, fused_of.get(k, tc_path), one_side,
+                           with_qf and k == "tgradu_gemm")
         if b:
             d["GB_s"] = round(b / (d["ms"] / d["launches"] / 1e3) / 1e9, 1)
             d["hbm_frac"] = round(d["GB_s"] / hbm_peak, 3)

@@ -164,8 +164,8 @@ void fill_metrics(fr_ctx* c, const fr::HostBlock& hb, fr::DevBlock& B, int d) {
 // entry is missed).
 struct LineForm {
     int n = 0;
-    bool grad = false, div = false;
-    std::vector<double> A, B;
+    bool grad = false, div = false, interp = false;
+    std::vector<double> A, B, I0;
     std::vector<int> fl;
 };
 
@@ -269,6 +269,26 @@ static LineForm line_form(const fr::ElemType& el, int d) {
         L.div = ok;
         L.B = B;
     }
+    // interpolation: row f of M0 for the flux point ending line l, over the line's points
+    {
+        std::vector<double> I0((size_t)2 * n);
+        for (int e = 0; e < 2; ++e)
+            for (int q = 0; q < n; ++q) I0[(size_t)e * n + q] = el.M0[(size_t)fl[e] * nu + pts[0][q]];
+        bool ok = true;
+        std::vector<double> rec(nu);
+        for (int l = 0; l < NLT && ok; ++l)
+            for (int e = 0; e < 2 && ok; ++e) {
+                std::fill(rec.begin(), rec.end(), 0.0);
+                for (int q = 0; q < n; ++q) rec[pts[l][q]] = I0[(size_t)e * n + q];
+                ok = close(rec, &el.M0[(size_t)fl[2 * l + e] * nu], nu);
+            }
+        // every flux point ends exactly one line
+        std::vector<int> seen(nf, 0);
+        for (int f : fl) seen[f]++;
+        for (int f = 0; f < nf && ok; ++f) ok = seen[f] == 1;
+        L.interp = ok;
+        L.I0 = I0;
+    }
     L.n = n;
     L.fl = fl;
     return L;
@@ -347,6 +367,8 @@ void upload_device(fr_ctx* c) {
                     std::copy(lf.A.begin(), lf.A.end(), B.ln_A);
                     std::copy(lf.B.begin(), lf.B.end(), B.ln_B);
                     B.ln_fl = (int*)upload(c, lf.fl);
+                    B.ln_interp = lf.interp;
+                    std::copy(lf.I0.begin(), lf.I0.end(), B.ln_I0);
                 }
             }
         }

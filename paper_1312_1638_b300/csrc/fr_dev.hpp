@@ -75,6 +75,11 @@ struct DevBlock {
     bool ln_grad = false, ln_div = false;
     double ln_A[48] = {}, ln_B[48] = {};
     int* ln_fl = nullptr;
+    // M0 in line form: the rows of a line's two end flux points, each over the
+    // line's n points ([2][n]: the xi_i = -1 end, then +1); the gradient kernel
+    // then also forms Q^(f)
+    bool ln_interp = false;
+    double ln_I0[12] = {};
 };
 
 // one nonzero of a structured operator row: value and column, packed so that

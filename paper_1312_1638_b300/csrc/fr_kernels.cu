@@ -803,9 +803,9 @@ __device__ __forceinline__ void line_apply(const T* __restrict__ tl, int row0, i
 // keeps the metric terms of its points in registers for all variables.
 template <typename T, int D, int n>
 __global__ void __launch_bounds__(LnCfg<D>::THREADS, D == 3 ? 1 : 2)
-grad_line_kernel(int nfpts, const int* __restrict__ fl, const LineMat<T> A, const T* __restrict__ Cf,
-                 const T* __restrict__ U, int64_t ld, T* __restrict__ Q, const T* __restrict__ smat,
-                 const T* __restrict__ rcp, Sub<T> sub) {
+grad_line_kernel(int nfpts, const int* __restrict__ fl, const LineMat<T> A, const LineMat<T> I0,
+                 const T* __restrict__ Cf, const T* __restrict__ U, int64_t ld, T* __restrict__ Q,
+                 T* __restrict__ Qf, const T* __restrict__ smat, const T* __restrict__ rcp, Sub<T> sub) {
     constexpr int NV = D + 2, NU = ln_pow(n, D), NL = ln_pow(n, D - 1), NLT = D * NL, TN = 32;
     constexpr int NT = LnCfg<D>::THREADS, NW = NT / 32, PW = (NU + NW - 1) / NW, LW = (NLT + NW - 1) / NW;
     constexpr int EPC = 16 / sizeof(T), CPR = TN / EPC;
@@ -888,7 +888,8 @@ grad_line_kernel(int nfpts, const int* __restrict__ fl, const LineMat<T> A, cons
                 for (int q = 0; q < n; ++q) qp[(size_t)q * S * TN] = y[q];
             }
             __syncthreads();
-            // the transform of this warp's points: Q = J^{-T} Q~
+            // the transform of this warp's points: Q = J^{-T} Q~ (kept in place of Q~
+            // when the flux-point values follow)
             T* qo = Q + (int64_t)a * ld + e0 + lane;
 #pragma unroll
             for (int k = 0; k < PW; ++k) {
@@ -903,111 +904,165 @@ grad_line_kernel(int nfpts, const int* __restrict__ fl, const LineMat<T> A, cons
                     T acc = T(0);
 #pragma unroll
                     for (int i = 0; i < D; ++i) acc += adj[k][i][j] * g[i];
-                    qs[(int64_t)j * NU * N] = acc * rr[k];
+                    const T v = acc * rr[k];
+                    qs[(int64_t)j * NU * N] = v;
+                    if (Qf) qt[(size_t)(j * NU + s) * TN + lane] = v;
+                }
+            }
+            if (!Qf) continue;
+            __syncthreads();
+            // Q^(f) = M0 Q per component (Eq. gradufpts): the two flux points
+            // ending each line from its n points, summed in point order
+            T* fo = Qf + (int64_t)a * ld + e0 + lane;
+#pragma unroll
+            for (int k = 0; k < LW; ++k) {
+                const int l = w + k * NW;
+                if (l >= NLT) break;
+                const int i = l / NL, m = l % NL;
+                int base, S;
+                if (i == 0) { base = line_base<D, n, 0>(m); S = ln_stride<n, 0>(); }
+                else if (i == 1) { base = line_base<D, n, 1>(m); S = ln_stride<n, 1>(); }
+                else { base = line_base<D, n, D - 1>(m); S = ln_stride<n, D - 1>(); }
+                const int fa = fls[2 * l], fb = fls[2 * l + 1];
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const T* qp = qt + (size_t)(j * NU + base) * TN + lane;
+                    T va = T(0), vb = T(0);
+#pragma unroll
+                    for (int q = 0; q < n; ++q) {
+                        const T x = qp[(size_t)q * S * TN];
+                        va = fma(I0.a[q], x, va);
+                        vb = fma(I0.a[n + q], x, vb);
+                    }
+                    fo[((int64_t)j * nfpts + fa) * N] = va;
+                    fo[((int64_t)j * nfpts + fb) * N] = vb;
                 }
             }
         }
     }
 }
 
-// Divergence: a CTA owns 32 columns of one variable (persistent, tiles in
-// variable-fastest order); the directions are summed in shared memory and
-// the last one applies -1/J and the RK stage.
+// Divergence: a CTA owns 32 elements and walks their variables in turn (the
+// next variable's tile, and after the last variable the next element range's
+// first one, is copied while the current one is formed); the directions are
+// summed in shared memory and the last one applies -1/J (kept in registers
+// for every variable) and the RK stage.
 template <typename T, int D, int n>
-__global__ void __launch_bounds__(LnCfg<D>::THREADS, LnMinB<T, D>::V)
-div_line_kernel(int nfpts, int nvars, const int* __restrict__ fl, const LineMat<T> B, const T* __restrict__ Df,
-                const T* __restrict__ F, int64_t N, T* __restrict__ R, const T* __restrict__ rcp, int64_t ld,
-                RkArgs<T> rk) {
-    constexpr int NU = ln_pow(n, D), NL = ln_pow(n, D - 1), NLT = D * NL, TN = 32, NT = LnCfg<D>::THREADS;
-    constexpr int NW = NT / 32, KL = (NL + NW - 1) / NW;          // lines per warp and direction
-    constexpr int EPC = 16 / sizeof(T), CPR = TN / EPC;
+__global__ void __launch_bounds__(LnCfg<D>::THREADS, 1)
+div_line_kernel(int nfpts, const int* __restrict__ fl, const LineMat<T> B, const T* __restrict__ Df,
+                const T* __restrict__ F, int64_t ld, T* __restrict__ R, const T* __restrict__ rcp, RkArgs<T> rk) {
+    constexpr int NV = D + 2, NU = ln_pow(n, D), NL = ln_pow(n, D - 1), NLT = D * NL, TN = 32;
+    constexpr int NT = LnCfg<D>::THREADS, NW = NT / 32, KL = (NL + NW - 1) / NW;   // lines per warp and direction
+    constexpr int EPC = 16 / sizeof(T), CPR = TN / EPC, I = D - 1, SL = ln_stride<n, D - 1>();
     extern __shared__ __align__(16) unsigned char ln_smem[];
     int* fls = (int*)ln_smem;
-    T* tile = (T*)(ln_smem + ((NLT * 2 * sizeof(int) + 15) & ~15));   // [nfpts + D NU][TN]: D~, then F~
-    T* racc = tile + (size_t)(nfpts + D * NU) * TN;               // [NU][TN]: directions summed so far
     const int K = nfpts + D * NU;
+    T* tile0 = (T*)(ln_smem + ((NLT * 2 * sizeof(int) + 15) & ~15));   // 2 x [K][TN]: D~, then F~
+    T* racc = tile0 + (size_t)2 * K * TN;                         // [NU][TN]: directions summed so far
     const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+    const int64_t N = (int64_t)NV * ld;
     for (int e = tid; e < NLT * 2; e += NT) fls[e] = fl[e];
-    const int ntiles = (int)(N / TN);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t col0 = tile_col0(t, nvars, ld, TN);
-        const int64_t col = col0 + lane;
-        const int64_t nn = col % ld;
-        __syncthreads();
+    const int ntiles = (int)(ld / TN);
+    auto copy = [&](int t, int a, T* tl) {
+        const int64_t off = (int64_t)a * ld + (int64_t)t * TN;
         for (int e = tid; e < K * CPR; e += NT) {
             const int k = e / CPR, q = e % CPR;
-            const T* src = k < nfpts ? Df + (int64_t)k * N : F + (int64_t)(k - nfpts) * N;
-            cp_async16(tile + (size_t)k * TN + q * EPC, src + col0 + q * EPC);
+            const T* src = k < nfpts ? Df + off + (int64_t)k * N : F + off + (int64_t)(k - nfpts) * N;
+            cp_async16(tl + (size_t)k * TN + q * EPC, src + q * EPC);
         }
-        // the last direction's lines of this warp finish their points: their 1/J
-        // (and RK registers) are loaded while the tile arrives
-        T pr[KL][n], pu[KL][n], pa[KL][n];
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    int t = blockIdx.x, ph = 0;
+    if (t < ntiles) copy(t, 0, tile0);
+    for (; t < ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        const int64_t nn = (int64_t)t * TN + lane;
+        // 1/J at the points this warp finishes (its last-direction lines)
+        T pr[KL][n];
 #pragma unroll
         for (int k = 0; k < KL; ++k) {
-            const int base = line_base<D, n, D - 1>(min(w + k * NW, NL - 1));
+            const int base = line_base<D, n, I>(min(w + k * NW, NL - 1));
 #pragma unroll
-            for (int q = 0; q < n; ++q) {
-                const int s = base + q * ln_stride<n, D - 1>();
-                const int64_t ix = (int64_t)s * N + col;
-                pr[k][q] = __ldg(rcp + (int64_t)s * ld + nn);
-                if (rk.mode == 0 || rk.mode == 1) pu[k][q] = rk.u[ix];
-                if (rk.mode == 1 || rk.mode == 2) pa[k][q] = rk.acc[ix];
+            for (int q = 0; q < n; ++q) pr[k][q] = __ldg(rcp + (int64_t)(base + q * SL) * ld + nn);
+        }
+#pragma unroll 1
+        for (int a = 0; a < NV; ++a) {
+            const T* tl = tile0 + (size_t)ph * K * TN;
+            __syncthreads();                                      // the other buffer and the sums are free
+            // this variable's RK registers at those points
+            T pu[KL][n], pa[KL][n];
+            if (rk.mode >= 0) {
+#pragma unroll
+                for (int k = 0; k < KL; ++k) {
+                    const int base = line_base<D, n, I>(min(w + k * NW, NL - 1));
+#pragma unroll
+                    for (int q = 0; q < n; ++q) {
+                        const int64_t ix = (int64_t)(base + q * SL) * N + (int64_t)a * ld + nn;
+                        if (rk.mode == 0 || rk.mode == 1) pu[k][q] = rk.u[ix];
+                        if (rk.mode == 1 || rk.mode == 2) pa[k][q] = rk.acc[ix];
+                    }
+                }
             }
-        }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        __syncthreads();
-        // direction 0: the first partial sums
-#pragma unroll
-        for (int k = 0; k < KL; ++k) {
-            const int m = w + k * NW;
-            if (m >= NL) break;
-            const int base = line_base<D, n, 0>(m);
-            T y[n];
-            line_apply<T, n, 0>(tile, nfpts, base, fls[2 * m], fls[2 * m + 1], B, lane, y);
-            T* rp = racc + (size_t)base * TN + lane;
-#pragma unroll
-            for (int q = 0; q < n; ++q) rp[(size_t)q * ln_stride<n, 0>() * TN] = y[q];
-        }
-        __syncthreads();
-        if constexpr (D == 3) {
+            if (a + 1 < NV || tn < ntiles) {
+                copy(a + 1 < NV ? t : tn, a + 1 < NV ? a + 1 : 0, tile0 + (size_t)(ph ^ 1) * K * TN);
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            }
+            __syncthreads();
+            // direction 0: the first partial sums
 #pragma unroll
             for (int k = 0; k < KL; ++k) {
                 const int m = w + k * NW;
                 if (m >= NL) break;
-                const int l = NL + m, base = line_base<D, n, 1>(m);
+                const int base = line_base<D, n, 0>(m);
                 T y[n];
-                line_apply<T, n, 1>(tile, nfpts + NU, base, fls[2 * l], fls[2 * l + 1], B, lane, y);
+                line_apply<T, n, 0>(tl, nfpts, base, fls[2 * m], fls[2 * m + 1], B, lane, y);
                 T* rp = racc + (size_t)base * TN + lane;
 #pragma unroll
-                for (int q = 0; q < n; ++q) rp[(size_t)q * ln_stride<n, 1>() * TN] += y[q];
+                for (int q = 0; q < n; ++q) rp[(size_t)q * ln_stride<n, 0>() * TN] = y[q];
             }
             __syncthreads();
-        }
-        // the last direction, -1/J and the RK stage
+            if constexpr (D == 3) {
 #pragma unroll
-        for (int k = 0; k < KL; ++k) {
-            const int m = w + k * NW;
-            if (m >= NL) break;
-            constexpr int I = D - 1, S = ln_stride<n, D - 1>();
-            const int l = I * NL + m, base = line_base<D, n, I>(m);
-            T y[n];
-            line_apply<T, n, I>(tile, nfpts + I * NU, base, fls[2 * l], fls[2 * l + 1], B, lane, y);
-            const T* rp = racc + (size_t)base * TN + lane;
+                for (int k = 0; k < KL; ++k) {
+                    const int m = w + k * NW;
+                    if (m >= NL) break;
+                    const int l = NL + m, base = line_base<D, n, 1>(m);
+                    T y[n];
+                    line_apply<T, n, 1>(tl, nfpts + NU, base, fls[2 * l], fls[2 * l + 1], B, lane, y);
+                    T* rp = racc + (size_t)base * TN + lane;
 #pragma unroll
-            for (int q = 0; q < n; ++q) {
-                const T v = -(rp[(size_t)q * S * TN] + y[q]) * pr[k][q];
-                const int64_t ix = (int64_t)(base + q * S) * N + col;
-                if (rk.mode < 0) {
-                    R[ix] = v;
-                } else if (nn < rk.nelem) {
-                    if (rk.mode == 2) {
-                        rk.u[ix] = pa[k][q] + rk.a * v;
-                    } else {
-                        rk.acc[ix] = (rk.mode == 0 ? pu[k][q] : pa[k][q]) + rk.a * v;
-                        rk.tmp[ix] = pu[k][q] + rk.b * v;
+                    for (int q = 0; q < n; ++q) rp[(size_t)q * ln_stride<n, 1>() * TN] += y[q];
+                }
+                __syncthreads();
+            }
+            // the last direction, -1/J and the RK stage
+#pragma unroll
+            for (int k = 0; k < KL; ++k) {
+                const int m = w + k * NW;
+                if (m >= NL) break;
+                const int l = I * NL + m, base = line_base<D, n, I>(m);
+                T y[n];
+                line_apply<T, n, I>(tl, nfpts + I * NU, base, fls[2 * l], fls[2 * l + 1], B, lane, y);
+                const T* rp = racc + (size_t)base * TN + lane;
+#pragma unroll
+                for (int q = 0; q < n; ++q) {
+                    const T v = -(rp[(size_t)q * SL * TN] + y[q]) * pr[k][q];
+                    const int64_t ix = (int64_t)(base + q * SL) * N + (int64_t)a * ld + nn;
+                    if (rk.mode < 0) {
+                        R[ix] = v;
+                    } else if (nn < rk.nelem) {
+                        if (rk.mode == 2) {
+                            rk.u[ix] = pa[k][q] + rk.a * v;
+                        } else {
+                            rk.acc[ix] = (rk.mode == 0 ? pu[k][q] : pa[k][q]) + rk.a * v;
+                            rk.tmp[ix] = pu[k][q] + rk.b * v;
+                        }
                     }
                 }
             }
+            ph ^= 1;
         }
     }
 }
@@ -1015,8 +1070,9 @@ div_line_kernel(int nfpts, int nvars, const int* __restrict__ fl, const LineMat<
 template <typename T>
 static size_t line_smem(int kind, int ndims, int n, int nfpts) {
     const int nu = ln_pow(n, ndims), nlt = ndims * ln_pow(n, ndims - 1);
-    // gradient: two variable tiles (C, U) and Q~; divergence: one tile (D~, F~) and the sums
-    const size_t rows = kind == 0 ? 2 * ((size_t)nfpts + nu) + (size_t)ndims * nu : (size_t)nfpts + ndims * nu + nu;
+    // gradient: two variable tiles (C, U) and Q~; divergence: two tiles (D~, F~) and the sums
+    const size_t rows = kind == 0 ? 2 * ((size_t)nfpts + nu) + (size_t)ndims * nu
+                                  : 2 * ((size_t)nfpts + ndims * nu) + (size_t)nu;
     return (((size_t)nlt * 2 * sizeof(int) + 15) & ~(size_t)15) + rows * 32 * sizeof(T);
 }
 
@@ -1052,12 +1108,17 @@ cudaError_t line_prepare(int kind, int ndims, int n, int nfpts, bool fp64) {
 }
 
 template <typename T, int D, int n>
-static void launch_grad_line(const DevBlock& Bk, const void* U, int grid, size_t sm, Sub<T> sub, cudaStream_t st) {
-    LineMat<T> A{};
+static void launch_grad_line(const DevBlock& Bk, const void* U, bool interp, int grid, size_t sm, Sub<T> sub,
+                             cudaStream_t st) {
+    LineMat<T> A{}, I0{};
     for (int e = 0; e < n * (n + 2); ++e) A.a[e] = (T)Bk.ln_A[e];
+    for (int e = 0; e < 2 * n; ++e) I0.a[e] = (T)Bk.ln_I0[e];
+    // the common solution is read from the Q^(f) storage before any flux-point
+    // gradient is written there: a tile's reads precede its writes, and tiles
+    // own disjoint elements
     grad_line_kernel<T, D, n><<<(unsigned)grid, LnCfg<D>::THREADS, sm, st>>>(
-        Bk.nfpts, Bk.ln_fl, A, (const T*)Bk.Qf, (const T*)U, Bk.ld, (T*)Bk.Q, (const T*)Bk.smat,
-        (const T*)Bk.rcpdjac, sub);
+        Bk.nfpts, Bk.ln_fl, A, I0, (const T*)Bk.Qf, (const T*)U, Bk.ld, (T*)Bk.Q, interp ? (T*)Bk.Qf : nullptr,
+        (const T*)Bk.smat, (const T*)Bk.rcpdjac, sub);
 }
 
 template <typename T, int D, int n>
@@ -1065,15 +1126,14 @@ static void launch_div_line(const DevBlock& Bk, void* R, RkArgs<T> rk, int grid,
     LineMat<T> B{};
     for (int e = 0; e < n * (n + 2); ++e) B.a[e] = (T)Bk.ln_B[e];
     div_line_kernel<T, D, n><<<(unsigned)grid, LnCfg<D>::THREADS, sm, st>>>(
-        Bk.nfpts, Bk.nvars, Bk.ln_fl, B, (const T*)Bk.Uf, (const T*)Bk.Q, (int64_t)Bk.nvars * Bk.ld, (T*)R,
-        (const T*)Bk.rcpdjac, Bk.ld, rk);
+        Bk.nfpts, Bk.ln_fl, B, (const T*)Bk.Uf, (const T*)Bk.Q, Bk.ld, (T*)R, (const T*)Bk.rcpdjac, rk);
 }
 
 // Q = J^{-T} Q~ (kind 0) or R / an RK stage (kind 1) through the tensor-line
 // kernels (B.ln_n > 0)
 template <typename T, int D>
 static cudaError_t line_op(const DevBlock& Bk, int kind, const void* U, void* R, Sub<T> sub, RkArgs<T> rk,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool interp = false) {
     const int n = Bk.ln_n;
     const int64_t N = (int64_t)Bk.nvars * Bk.ld;
     if (N % 32 != 0 || Bk.ld % 128 != 0 || ((uintptr_t)Bk.Uf | (uintptr_t)Bk.Q | (uintptr_t)Bk.Qf) % 16 != 0 ||
@@ -1082,13 +1142,13 @@ static cudaError_t line_op(const DevBlock& Bk, int kind, const void* U, void* R,
     const size_t sm = line_smem<T>(kind, D, n, Bk.nfpts);
     const void* fn = line_kernel<T>(kind, D, n);
     if (!fn) return cudaErrorInvalidValue;
-    if (kind == 0 && Bk.nvars != D + 2) return cudaErrorInvalidValue;
-    // gradient: one tile per 32 elements (all variables); divergence: per variable
-    const int grid = persistent_grid(fn, LnCfg<D>::THREADS, sm, (int)((kind == 0 ? Bk.ld : N) / 32));
+    if (Bk.nvars != D + 2) return cudaErrorInvalidValue;
+    // one tile per 32 elements (all variables)
+    const int grid = persistent_grid(fn, LnCfg<D>::THREADS, sm, (int)(Bk.ld / 32));
     switch (n) {
 #define FR_LN_CASE(NN)                                                              \
         case NN:                                                                    \
-            if (kind == 0) launch_grad_line<T, D, NN>(Bk, U, grid, sm, sub, st);   \
+            if (kind == 0) launch_grad_line<T, D, NN>(Bk, U, interp, grid, sm, sub, st); \
             else launch_div_line<T, D, NN>(Bk, R, rk, grid, sm, st);               \
             break;
         FR_LN_CASE(2) FR_LN_CASE(3) FR_LN_CASE(4) FR_LN_CASE(5) FR_LN_CASE(6)
@@ -1742,10 +1802,16 @@ static bool div_structured(const DevCtx& c, const DevBlock& B) {
 static bool grad_structured(const DevCtx& c, const DevBlock& B) {
     return (c.structured_grad == 1 && B.ln_grad) || (c.structured_grad != 0 && B.gs_nnz > 0);
 }
+// whether block B's gradient kernel also forms Q^(f) (the tensor-line kernel
+// with M0 in line form and the structured interpolation on)
+static bool gradfpts_fused(const DevCtx& c, const DevBlock& B) {
+    return c.structured_grad == 1 && B.ln_grad && B.ln_interp && c.structured_interp;
+}
 template <typename T, int D>
 static cudaError_t grad_struct(const DevCtx& c, const DevBlock& B, const void* u, cudaStream_t st, Sub<T> sub) {
     if (c.structured_grad == 1 && B.ln_grad)
-        return line_op<T, D>(B, 0, u, nullptr, sub, RkArgs<T>{-1, T(0), T(0), nullptr, nullptr, nullptr, 0}, st);
+        return line_op<T, D>(B, 0, u, nullptr, sub, RkArgs<T>{-1, T(0), T(0), nullptr, nullptr, nullptr, 0}, st,
+                             gradfpts_fused(c, B));
     return grad_sparse<T, D>(B, u, st, sub);
 }
 
@@ -1907,6 +1973,7 @@ phase_b1:
                 for (size_t b = 0; b < c.blocks.size(); ++b) {
                     DevBlock& B = c.blocks[b];
                     const int64_t N = (int64_t)NV * B.ld;
+                    if (gradfpts_fused(c, B)) continue;             // formed by the gradient kernel
                     for (int i = 0; i < D; ++i) {
                         if (c.structured_interp && B.sp_nnz > 0) {
                             prof_begin(c, K_GRADFPTS, st);
@@ -1931,6 +1998,7 @@ phase_b1:
                     for (int i = 0; i < D; ++i) {
                         DevBlock& B = c.blocks[b];
                         const int64_t N = (int64_t)NV * B.ld;
+                        if (gradfpts_fused(c, B)) break;            // formed by the gradient kernel
                         prof_begin(c, K_GRADFPTS, st);
                         if (c.structured_interp && B.sp_nnz > 0)
                             FR_TRY(interp_sparse<T>(B, (const T*)B.Q + (int64_t)i * B.nupts * N, N,
@@ -1959,7 +2027,7 @@ phase_b1:
                         B.nupts, B.nelem, B.ld, (const T*)B.smat, (const T*)B.rcpdjac, (T*)B.Q);
                     prof_end(c, st);
                 }
-                for (int i = 0; i < D; ++i) {
+                for (int i = 0; i < D && !gradfpts_fused(c, B); ++i) {
                     prof_begin(c, K_GRADFPTS, st);
                     if (c.structured_interp && B.sp_nnz > 0)
                         FR_TRY(interp_sparse<T>(B, (const T*)B.Q + (int64_t)i * B.nupts * N, N,
