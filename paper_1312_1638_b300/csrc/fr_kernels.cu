@@ -804,8 +804,8 @@ __device__ __forceinline__ void line_apply(const T* __restrict__ tl, int row0, i
 template <typename T, int D, int n>
 __global__ void __launch_bounds__(LnCfg<D>::THREADS, D == 3 ? 1 : 2)
 grad_line_kernel(int nfpts, const int* __restrict__ fl, const LineMat<T> A, const LineMat<T> I0,
-                 const T* __restrict__ Cf, const T* __restrict__ U, int64_t ld, T* __restrict__ Q,
-                 T* __restrict__ Qf, const T* __restrict__ smat, const T* __restrict__ rcp, Sub<T> sub) {
+                 const T* Cf, const T* __restrict__ U, int64_t ld, T* __restrict__ Q,
+                 T* Qf, const T* __restrict__ smat, const T* __restrict__ rcp, Sub<T> sub) {
     constexpr int NV = D + 2, NU = ln_pow(n, D), NL = ln_pow(n, D - 1), NLT = D * NL, TN = 32;
     constexpr int NT = LnCfg<D>::THREADS, NW = NT / 32, PW = (NU + NW - 1) / NW, LW = (NLT + NW - 1) / NW;
     constexpr int EPC = 16 / sizeof(T), CPR = TN / EPC;

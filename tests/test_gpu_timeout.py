@@ -28,6 +28,10 @@ def test_forced_wait_timeout_is_reported_and_context_recovers(torch, prec):
     from paper_1312_1638_b300 import fr
     m = periodic_box("hex", 4, 0.0, 2 * np.pi, jitter=0.1, seed=3)
     s = fr.Solver(m, 3, "ns", prec, device=0, **NS_PRM, ref_rho=1.0, ref_p=1.0 / (1.4 * 0.09))
+    # every operator product on the tensor cores (on hexahedra the structured
+    # kernels would otherwise take them, and they have no waits to give up)
+    for opt in ("structured_interp", "structured_grad", "structured_div"):
+        s.set_option(opt, 0)
     U = fields.taylor_green(s.solution_points(0), M=0.3).transpose(1, 0, 2)
     u = torch.from_numpy(s.pack(0, U)).float().cuda()
     r = torch.empty_like(u)

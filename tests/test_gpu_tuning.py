@@ -35,9 +35,11 @@ def _solver(fr, case, prec):
         s = fr.Solver(m, 4, "ns", prec, device=0, gamma=1.4, mu=0.02, prandtl=0.72, ldg_beta=0.5, ldg_tau=0.1,
                       bc_rho=1.0, bc_v=(1.0, 0.0, 0.0), bc_p=p_inf, outflow_p=p_inf, wall_cpTw=1.4 / 0.4 * p_inf,
                       ref_rho=1.0, ref_p=p_inf)
-    # these tests are about the tensor-core products: the corrected gradient of
-    # the tensor elements runs there too (not on its structured kernel)
+    # these tests are about the tensor-core products: the corrected gradient and
+    # the divergence of the tensor elements run there too (not on their
+    # structured kernels)
     s.set_option("structured_grad", 0)
+    s.set_option("structured_div", 0)
     return m, s
 
 
