@@ -585,7 +585,7 @@ def main():
         sl.apply_tuning()
         sl.set_option("graphs", 1 if graphs else 0)
         dtp = torch.float64 if prec == "fp64" else torch.float32
-        ul = u_init.to(dtp)
+        ul = u_init.to(dtp, copy=True)                      # a copy: the leg's RK4 steps advance it
         rl = torch.empty_like(ul)
         sl.rhs([ul], [rl], stream)                          # loads every kernel
         if warm:
