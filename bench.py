@@ -62,6 +62,9 @@ def _args():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (16^3 hex box) leg")
     ap.add_argument("--autotune", action="store_true",
                     help="autotune kernel variants missing from the committed table (outside the timed region)")
+    ap.add_argument("--dense", action="store_true",
+                    help="run the headline context with the dense operator products (tensor cores on the split "
+                         "precisions) instead of the structured kernels: for profiling the dense path")
     ap.add_argument("--extra-legs", action="store_true",
                     help="also time the SD / HU correction functions and the Euler / DOPRI5 steppers (64^3 box)")
     return ap.parse_args()
@@ -426,6 +429,9 @@ def main():
     del U0
     u_init = u.clone()
     # kernel-variant choices measured on B300 (committed table; --autotune measures missing entries)
+    if a.dense:
+        for opt in ("structured_interp", "structured_grad", "structured_div"):
+            s.set_option(opt, 0)
     tune_src, tune_text = s.apply_tuning([u] if a.autotune else None)
     t_setup = time.perf_counter() - t_setup
     stream = torch.cuda.current_stream()
@@ -493,8 +499,10 @@ def main():
     # p+1 solution points and 2 flux points), as FP32 (FP64) multiply-adds on
     # the CUDA cores whatever the precision
     with_qf = prof.get("gradfpts_gemm", (0, 0.0))[0] == 0      # Q^(f) formed by the gradient kernel
-    structured = structured_nonzeros(nu, nf, D, a.order, with_qf)
-    fused_of = {"tgradu_gemm": True, "tdivf_gemm": True}          # transform / RK stage in the kernel
+    structured = {} if a.dense else structured_nonzeros(nu, nf, D, a.order, with_qf)
+    # transform / RK stage in the kernel (the structured kernels; the dense
+    # products fuse them on the tensor-core paths only)
+    fused_of = {} if a.dense else {"tgradu_gemm": True, "tdivf_gemm": True}
 
     def roof_of(name, launches, tms):
         kb, kf = kernel_work(name, nu, nf, V, D, nelem, npairs, srz, fused_of.get(name, tc_path), one_side,
@@ -801,7 +809,8 @@ def main():
         data="synthetic",
         config=dict(workload_config(a, world),
                     l2="inputs larger than L2 (state alone is %.1f GB)" % (u_init.numel() * u_init.element_size() / 1e9),
-                    setup_s=round(t_setup, 1), kernel_variants=dict(source=tune_src, choice=tune_text)),
+                    setup_s=round(t_setup, 1), kernel_variants=dict(source=tune_src, choice=tune_text),
+                    operator_products="dense (--dense)" if a.dense else "structured kernels on hexahedra"),
         roofline=roof, cpu_baseline=cpu_baseline, e2e=e2e, gpu_launches=launches,
         clocks=clk.summary(), per_kernel=per_kernel, kernel_pass_ms_per_step=ms_prof / a.steps,
         parity=parity, fp32_gpu=fp32, fp64_gpu=fp64, bf16x3_gpu=bf16, mixed_mesh=mixed, tgv32_p3=tgv32,

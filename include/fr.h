@@ -73,9 +73,12 @@ typedef enum {
 typedef enum { FR_EULER = 0, FR_NAVIER_STOKES = 1 } fr_system;
 /* FR_PREC_FP64: FP64 everywhere.  FR_PREC_FP32: FP32 everywhere (CUDA-core
  * operator products).  FR_PREC_TF32X3 / FR_PREC_BF16X3: FP32 state and
- * point-wise arithmetic; operator products on the tensor cores with both
- * factors split in two (TF32: 11+11 bits, BF16: 8+8 bits) and three products
- * accumulated in FP32. */
+ * point-wise arithmetic; dense operator products on the tensor cores with
+ * both factors split in two (TF32: 11+11 bits, BF16: 8+8 bits) and three
+ * products accumulated in FP32.  On quadrilaterals and hexahedra the operator
+ * products take structured kernels (the "structured_*" options of
+ * fr_set_option) that multiply the operators' nonzeros in FP32 in every
+ * single precision, so there these contexts compute what an FP32 one does. */
 typedef enum { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1, FR_PREC_BF16X3 = 2, FR_PREC_TF32X3 = 3 } fr_precision;
 typedef enum { FR_QUAD = 0, FR_TRI = 1, FR_HEX = 2 } fr_etype;
 /* boundary types (App. C): free-stream ("supersonic inflow") ghost, subsonic
@@ -294,17 +297,22 @@ fr_status fr_set_tuning(fr_ctx* ctx, const char* text);
  * FP32 / FP64 multiply-adds of those entries, in every precision (they need
  * no split: FP32 multiply-adds are as accurate as the split products); 0
  * uses the dense operator products.  "structured_grad" (default 1, Navier-Stokes):
- * where every row of the corrected-gradient operator [M6 | M4 - M6 M0]
- * (Eq. tquptsm) has at most 8 nonzeros (quadrilaterals and hexahedra: the
- * p+1 solution points on a line and the two flux points ending it), the
- * gradient Q = J^-T Q~ (Eq. gradufpts) runs as one structured kernel with
- * FP32 / FP64 multiply-adds of those entries and the transform in the same
- * pass, in every precision; 0 uses the dense operator product (tensor cores
- * on the split-precision paths).  "structured_div" (default 1): the same for
- * the divergence operator [M3 | M1 - M3 M2] (Eq. tdivflux; at most 24
- * nonzeros per row: per direction the p+1 flux values on the line through
- * the point and the two common fluxes ending it), -1/J (Eq. negdivconf) and, inside
- * fr_rk4, the RK4 stage combination applied in the same pass.  Changing
+ * where the corrected-gradient operator [M6 | M4 - M6 M0] (Eq. tquptsm) is
+ * structured (quadrilaterals and hexahedra: row (i, s) holds the p+1
+ * solution points on the line through s in direction i and the two flux
+ * points ending it), the gradient Q = J^-T Q~ (Eq. gradufpts) runs as one
+ * structured kernel with FP32 / FP64 multiply-adds of those entries and the
+ * transform in the same pass, in every precision.  1: the tensor-line form
+ * (set-up checks that one p+1 x p+3 line matrix rebuilds every row; this
+ * kernel also forms Q^(f) = M5 Q when "structured_interp" is on), falling
+ * back to 2 where a tile does not fit shared memory; 2: the row-wise form
+ * (each row's nonzeros, at most 8); 0: the dense operator product (tensor
+ * cores on the split-precision paths).  "structured_div" (default 1): the
+ * same choice for the divergence operator [M3 | M1 - M3 M2] (Eq. tdivflux;
+ * per direction the p+1 flux values on the line through the point and the
+ * two common fluxes ending it; row-wise form: at most 24 nonzeros per row),
+ * with -1/J (Eq. negdivconf) and, inside fr_rk4, the RK4 stage combination
+ * applied in the same pass.  Values outside 0..2 give FR_ERR_ARG.  Changing
  * either drops the captured RK4 step.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
  * operator GEMMs gives up: the kernel then drains its own copies and MMAs,
