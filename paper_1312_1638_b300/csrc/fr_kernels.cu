@@ -1485,27 +1485,59 @@ __global__ void comm_sol_bc_kernel(int64_t nb, int bctype, const uint32_t* __res
 // written with opposite signs to both sides, in place over U^(f).  SIDE = 1
 // (beta = +1/2) / 2 (beta = -1/2): the viscous flux of the side whose weight
 // is zero is neither read nor evaluated (SIDE = 0: any beta).
-template <typename T, int D, bool NS, int SIDE = 0>
-__global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ offL, const uint32_t* __restrict__ offR,
-                                 T* UfL, T* UfR, const T* __restrict__ QfL, const T* __restrict__ QfR,
-                                 int64_t ldL, int64_t ldR, int64_t qsL, int64_t qsR, const T* __restrict__ nrm,
-                                 const T* __restrict__ magL, const T* __restrict__ magR, DevParams P) {
+// The operands of one interior pair: both sides' U^(f), the unit normal,
+// J^(f) n^(f) of both sides and (NS) the flux-point gradient of the side(s)
+// whose viscous flux has weight (SIDE 1: L, SIDE 2: R, SIDE 0: both).
+template <typename T, int D, bool NS, int SIDE>
+struct PairIn {
+    static constexpr int NV = D + 2, NQ = NS ? (SIDE == 0 ? 2 : 1) : 1;
+    T uL[NV], uR[NV], n[D], mL, mR;
+    T q[NQ][D][NV];
+};
+
+template <typename T, int D, bool NS, int SIDE>
+__device__ __forceinline__ void pair_load(PairIn<T, D, NS, SIDE>& in, int64_t npairs, int64_t k, int64_t oL,
+                                          int64_t oR, const T* UfL, const T* UfR, const T* __restrict__ QfL,
+                                          const T* __restrict__ QfR, int64_t ldL, int64_t ldR, int64_t qsL,
+                                          int64_t qsR, const T* __restrict__ nrm, const T* __restrict__ magL,
+                                          const T* __restrict__ magR) {
     constexpr int NV = D + 2;
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= npairs) return;
-    int64_t oL = offL[k], oR = offR[k];
-    T uL[NV], uR[NV], n[D], F[NV];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) { uL[a] = UfL[oL + a * ldL]; uR[a] = UfR[oR + a * ldR]; }
+    for (int a = 0; a < NV; ++a) { in.uL[a] = UfL[oL + a * ldL]; in.uR[a] = UfR[oR + a * ldR]; }
 #pragma unroll
-    for (int i = 0; i < D; ++i) n[i] = nrm[i * npairs + k];
+    for (int i = 0; i < D; ++i) in.n[i] = nrm[i * npairs + k];
+    in.mL = magL[k];
+    in.mR = magR[k];
+    if constexpr (NS) {
+        if constexpr (SIDE != 2) {
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+#pragma unroll
+                for (int a = 0; a < NV; ++a) in.q[0][j][a] = QfL[j * qsL + oL + a * ldL];
+        }
+        if constexpr (SIDE != 1) {
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+#pragma unroll
+                for (int a = 0; a < NV; ++a) in.q[SIDE == 0 ? 1 : 0][j][a] = QfR[j * qsR + oR + a * ldR];
+        }
+    }
+}
+
+// Rusanov + LDG common normal flux of one pair (App. B, Sec. 4.3), stored as
+// J^(f) n^(f) F on the L side and its negative on the R side
+template <typename T, int D, bool NS, int SIDE>
+__device__ __forceinline__ void pair_flux_store(const PairIn<T, D, NS, SIDE>& in, int64_t oL, int64_t oR, T* UfL,
+                                                T* UfR, int64_t ldL, int64_t ldR, const DevParams& P) {
+    constexpr int NV = D + 2;
+    T F[NV];
     T gamma = T(P.gamma);
     const Ref<T> rf = make_ref<T>(P);
-    Gas<T, D>::rusanov(uL, uR, n, rf, gamma, F);
+    Gas<T, D>::rusanov(in.uL, in.uR, in.n, rf, gamma, F);
     // the energy split is undone on each part of the flux as it is formed
     // (h_ref times the mass component; see tflux_kernel)
     F[NV - 1] += rf.h * F[0];
-    if (NS) {
+    if constexpr (NS) {
         // LDG viscous part, one side at a time (the gradients and viscous flux
         // of only one side are live at once)
         T gm1 = gamma - T(1), mu = T(P.mu), kappa = T(P.mu * P.gamma / (P.prandtl * (P.gamma - 1.0)));
@@ -1514,47 +1546,85 @@ __global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ of
 #pragma unroll
         for (int a = 0; a < NV; ++a) fvn[a] = T(0);
         if constexpr (SIDE != 2) {
-            T q[D][NV], fv[D][NV];
-#pragma unroll
-            for (int j = 0; j < D; ++j)
-#pragma unroll
-                for (int a = 0; a < NV; ++a) q[j][a] = QfL[j * qsL + oL + a * ldL];
-            Gas<T, D>::vis_flux(uL, q, rf, gm1, mu, kappa, fv);
+            T fv[D][NV];
+            Gas<T, D>::vis_flux(in.uL, in.q[0], rf, gm1, mu, kappa, fv);
 #pragma unroll
             for (int a = 0; a < NV; ++a) {
                 T acc = T(0);
 #pragma unroll
-                for (int i = 0; i < D; ++i) acc += n[i] * fv[i][a];
+                for (int i = 0; i < D; ++i) acc += in.n[i] * fv[i][a];
                 fvn[a] = wl * acc;
             }
         }
         if constexpr (SIDE != 1) {
-            T q[D][NV], fv[D][NV];
-#pragma unroll
-            for (int j = 0; j < D; ++j)
-#pragma unroll
-                for (int a = 0; a < NV; ++a) q[j][a] = QfR[j * qsR + oR + a * ldR];
-            Gas<T, D>::vis_flux(uR, q, rf, gm1, mu, kappa, fv);
+            T fv[D][NV];
+            Gas<T, D>::vis_flux(in.uR, in.q[SIDE == 0 ? 1 : 0], rf, gm1, mu, kappa, fv);
 #pragma unroll
             for (int a = 0; a < NV; ++a) {
                 T acc = T(0);
 #pragma unroll
-                for (int i = 0; i < D; ++i) acc += n[i] * fv[i][a];
+                for (int i = 0; i < D; ++i) acc += in.n[i] * fv[i][a];
                 fvn[a] += wr * acc;
             }
         }
         T du[NV];
-        Gas<T, D>::jump(uL, uR, rf, du);
+        Gas<T, D>::jump(in.uL, in.uR, rf, du);
         fvn[NV - 1] += rf.h * fvn[0];
         du[NV - 1] += rf.h * du[0];
 #pragma unroll
         for (int a = 0; a < NV; ++a) F[a] = F[a] - fvn[a] + tau * du[a];
     }
-    T mL = magL[k], mR = magR[k];
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-        UfL[oL + a * ldL] = mL * F[a];
-        UfR[oR + a * ldR] = -mR * F[a];
+        UfL[oL + a * ldL] = in.mL * F[a];
+        UfR[oR + a * ldR] = -in.mR * F[a];
+    }
+}
+
+// common normal flux D~ (K7): one thread per pair, in place over U^(f)
+template <typename T, int D, bool NS, int SIDE = 0>
+__global__ void comm_flux_kernel(int64_t npairs, const uint32_t* __restrict__ offL, const uint32_t* __restrict__ offR,
+                                 T* UfL, T* UfR, const T* __restrict__ QfL, const T* __restrict__ QfR,
+                                 int64_t ldL, int64_t ldR, int64_t qsL, int64_t qsR, const T* __restrict__ nrm,
+                                 const T* __restrict__ magL, const T* __restrict__ magR, DevParams P) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    const int64_t oL = offL[k], oR = offR[k];
+    PairIn<T, D, NS, SIDE> in;
+    pair_load<T, D, NS, SIDE>(in, npairs, k, oL, oR, UfL, UfR, QfL, QfR, ldL, ldR, qsL, qsR, nrm, magL, magR);
+    pair_flux_store<T, D, NS, SIDE>(in, oL, oR, UfL, UfR, ldL, ldR, P);
+}
+
+// The same flux, software-pipelined for the latency of the gathers: a
+// persistent thread walks the pairs k, k + S, ... (S the grid's threads),
+// loading the offsets two pairs ahead and the operands one pair ahead while
+// it forms the current pair.  Pairs touch disjoint flux points, so the next
+// pair's loads never read what the current pair stores.
+template <typename T, int D, bool NS, int SIDE>
+__global__ void __launch_bounds__(128)
+comm_flux_pipe_kernel(int64_t npairs, const uint32_t* __restrict__ offL, const uint32_t* __restrict__ offR,
+                      T* UfL, T* UfR, const T* __restrict__ QfL, const T* __restrict__ QfR, int64_t ldL,
+                      int64_t ldR, int64_t qsL, int64_t qsR, const T* __restrict__ nrm,
+                      const T* __restrict__ magL, const T* __restrict__ magR, DevParams P) {
+    const int64_t S = (int64_t)gridDim.x * blockDim.x;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    int64_t oL0 = offL[k], oR0 = offR[k], oL1 = 0, oR1 = 0;
+    if (k + S < npairs) { oL1 = offL[k + S]; oR1 = offR[k + S]; }
+    PairIn<T, D, NS, SIDE> cur;
+    pair_load<T, D, NS, SIDE>(cur, npairs, k, oL0, oR0, UfL, UfR, QfL, QfR, ldL, ldR, qsL, qsR, nrm, magL, magR);
+#pragma unroll 1
+    for (; k < npairs; k += S) {
+        int64_t oL2 = 0, oR2 = 0;
+        if (k + 2 * S < npairs) { oL2 = offL[k + 2 * S]; oR2 = offR[k + 2 * S]; }
+        PairIn<T, D, NS, SIDE> nxt;
+        if (k + S < npairs)
+            pair_load<T, D, NS, SIDE>(nxt, npairs, k + S, oL1, oR1, UfL, UfR, QfL, QfR, ldL, ldR, qsL, qsR, nrm,
+                                      magL, magR);
+        pair_flux_store<T, D, NS, SIDE>(cur, oL0, oR0, UfL, UfR, ldL, ldR, P);
+        cur = nxt;
+        oL0 = oL1; oR0 = oR1;
+        oL1 = oL2; oR1 = oR2;
     }
 }
 
@@ -1765,12 +1835,15 @@ template <typename T, int D>
 static void launch_comm_flux_ns(int side, int64_t n, const uint32_t* oL, const uint32_t* oR, T* UL, T* UR,
                                 const T* QL, const T* QR, int64_t ldL, int64_t ldR, int64_t qsL, int64_t qsR,
                                 const T* nrm, const T* mL, const T* mR, const DevParams& P, cudaStream_t st) {
-    if (side == 1)
-        comm_flux_kernel<T, D, true, 1><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
-                                                                          qsR, nrm, mL, mR, P);
-    else if (side == 2)
-        comm_flux_kernel<T, D, true, 2><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
-                                                                          qsR, nrm, mL, mR, P);
+    if (side == 1) {
+        const int g = persistent_grid((const void*)comm_flux_pipe_kernel<T, D, true, 1>, 128, 0, (int)lin_grid(n, 128));
+        comm_flux_pipe_kernel<T, D, true, 1><<<(unsigned)g, 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
+                                                                         qsR, nrm, mL, mR, P);
+    } else if (side == 2) {
+        const int g = persistent_grid((const void*)comm_flux_pipe_kernel<T, D, true, 2>, 128, 0, (int)lin_grid(n, 128));
+        comm_flux_pipe_kernel<T, D, true, 2><<<(unsigned)g, 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
+                                                                         qsR, nrm, mL, mR, P);
+    }
     else
         comm_flux_kernel<T, D, true, 0><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
                                                                           qsR, nrm, mL, mR, P);
