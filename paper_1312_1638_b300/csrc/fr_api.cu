@@ -112,6 +112,25 @@ void* upload_pairs(fr_ctx* c, const std::vector<std::vector<std::pair<int, doubl
     return fp64 ? upload_pairs_t<double>(c, rows, nnz) : upload_pairs_t<float>(c, rows, nnz);
 }
 
+// the nonzeros (column, value) of every row of a rows x cols row-major
+// operator; entries below 1e-15 of their row's largest are the rounding of a
+// vanishing Lagrange factor and are dropped.  *nnz: the most in any row.
+static std::vector<std::vector<std::pair<int, double>>> nonzero_rows(const std::vector<double>& A, int64_t rows,
+                                                                      int64_t cols, int* nnz) {
+    std::vector<std::vector<std::pair<int, double>>> nz((size_t)rows);
+    *nnz = 0;
+    for (int64_t r = 0; r < rows; ++r) {
+        double mx = 0;
+        for (int64_t k = 0; k < cols; ++k) mx = std::max(mx, std::fabs(A[(size_t)(r * cols + k)]));
+        for (int64_t k = 0; k < cols; ++k) {
+            const double v = A[(size_t)(r * cols + k)];
+            if (std::fabs(v) > 1e-15 * mx) nz[r].push_back({(int)k, v});
+        }
+        *nnz = std::max(*nnz, (int)nz[r].size());
+    }
+    return nz;
+}
+
 fr_status set_err(fr_ctx* c, fr_status st, const std::string& m) {
     if (c) c->err = m;
     else g_setup_err = m;
@@ -440,6 +459,36 @@ void upload_device(fr_ctx* c) {
                 OutT = hcat(M0T, (int)nf, transpose(el.M46, d * (int)nu, (int)nu), d * (int)nu, (int)nu);
                 B.opM6T = upload_real(c, M6T, fp64);
                 B.opOutT = upload_real(c, OutT, fp64);
+            }
+            {
+                // the same operators in structured form where they allow (tensor
+                // elements: p+1 or 2 D nonzeros per row; [M0^T | (M4 - M6 M0)^T]:
+                // 2 D + D (p+1))
+                const std::vector<double>* ops[6] = {nullptr, &M3T, &M132T, &M0T, ns ? &M6T : nullptr,
+                                                     ns ? &OutT : nullptr};
+                const int rows[6] = {0, (int)nf, d * (int)nu, (int)nu, (int)nf, (int)nu};
+                const int cols[6] = {0, (int)nu, (int)nu, (int)nf, d * (int)nu, (int)(nf + d * nu)};
+                for (int w = 1; w < 6; ++w) {
+                    if (!ops[w]) continue;
+                    int nnz = 0;
+                    const auto nz = nonzero_rows(*ops[w], rows[w], cols[w], &nnz);
+                    if (w < 5 && fr::sparse_prepare(0, rows[w], cols[w], nnz, fp64)) {
+                        std::vector<int> idx((size_t)rows[w] * nnz, 0);
+                        std::vector<double> val((size_t)rows[w] * nnz, 0.0);
+                        for (int r = 0; r < rows[w]; ++r)
+                            for (size_t j = 0; j < nz[r].size(); ++j) {
+                                idx[(size_t)r * nnz + j] = nz[r][j].first;
+                                val[(size_t)r * nnz + j] = nz[r][j].second;
+                            }
+                        B.adj_nnz[w] = nnz;
+                        B.adj_idx[w] = (int*)upload(c, idx);
+                        B.adj_val[w] = upload_real(c, val, fp64);
+                    } else if (w == 5 && fr::sparse_prepare(1, rows[w], cols[w], nnz, fp64)) {
+                        B.adj_nnz[5] = nnz;
+                        B.adj_ent = upload_pairs(c, nz, nnz, fp64);
+                    }
+                    (void)cudaGetLastError();
+                }
             }
             if (c->prm.precision == FR_PREC_BF16X3 || c->prm.precision == FR_PREC_TF32X3) {
                 const int kind = c->prm.precision == FR_PREC_TF32X3 ? 0 : 1;
@@ -1389,6 +1438,10 @@ fr_status fr_set_option(fr_ctx* ctx, const char* name, int64_t value) {
         if (value < 0 || value > 2) return set_err(ctx, FR_ERR_ARG, "structured_div must be 0, 1 or 2");
         ctx->dev.structured_div = (int)value;
         drop_graph(ctx);
+        return FR_OK;
+    }
+    if (std::string(name) == "structured_adjoint") {
+        ctx->dev.structured_adjoint = value != 0;
         return FR_OK;
     }
     if (std::string(name) == "group_blocks") {

@@ -80,6 +80,14 @@ struct DevBlock {
     // then also forms Q^(f)
     bool ln_interp = false;
     double ln_I0[12] = {};
+    // the adjoint's operators (adjoint_gemm `which` 1..4: M3^T, (M1 - M3 M2)^T,
+    // M0^T, M6^T) in structured form: [rows][nnz] columns and values (at most
+    // 8 nonzeros per row); which 5, [M0^T | (M4 - M6 M0)^T]: packed SpPair<T>
+    // entries (at most 24); nnz 0: dense
+    int adj_nnz[6] = {};
+    int* adj_idx[6] = {};
+    void* adj_val[6] = {};
+    void* adj_ent = nullptr;
 };
 
 // one nonzero of a structured operator row: value and column, packed so that
@@ -171,6 +179,7 @@ struct DevCtx {
     // the row-wise one, 2 the row-wise kernel
     int structured_grad = 1;
     int structured_div = 1;
+    bool structured_adjoint = true; // the adjoint's operator products through the structured kernels where they allow
     double* partial = nullptr;     // reduction scratch
     int64_t npartial = 0;
 };
@@ -222,6 +231,10 @@ cudaError_t interp_prepare(int nupts, int nfpts, int nnz, bool fp64);
 // the same for the structured corrected-gradient kernel
 cudaError_t grad_prepare(int nupts, int nfpts, int ndims, int nnz, bool fp64);
 cudaError_t div_prepare(int nupts, int nfpts, int ndims, int nnz, bool fp64);
+// whether the structured product kernels take an M x K operator with nnz
+// nonzeros per row (kind 0: at most 8; kind 1: at most 24 over two stacked
+// sources), raising their shared-memory limits if so
+bool sparse_prepare(int kind, int M, int K, int nnz, bool fp64);
 // the tensor-line kernels: kind 0 gradient, 1 divergence; n = p+1
 cudaError_t line_prepare(int kind, int ndims, int n, int nfpts, bool fp64);
 // look up the allocation-free RK4's fixed device array on `device` (current),

@@ -349,6 +349,20 @@ static cudaError_t interp_sparse(const DevBlock& Bk, const void* B, int64_t N, v
     return cudaGetLastError();
 }
 
+// C[M][N] = A B for any operator A with at most SP_NNZ nonzeros per row held
+// as [M][nnz] columns / values (the adjoint's transposed operators)
+template <typename T>
+static cudaError_t sparse_product(int M, int K, int nnz, const int* idx, const void* val, const void* B, int64_t N,
+                                  void* C, int64_t ld, cudaStream_t st) {
+    constexpr int TN = 32 * SpCfg<T>::VW;
+    if (nnz < 1 || nnz > SP_NNZ || N % TN != 0 || ld % 128 != 0 || ((uintptr_t)B | (uintptr_t)C) % 16 != 0)
+        return cudaErrorInvalidValue;
+    const size_t sm = interp_smem<T>(M, K, nnz);
+    interp_sparse_kernel<T><<<(unsigned)(N / TN), SP_THREADS, sm, st>>>(M, K, nnz, idx, (const T*)val, (const T*)B, N,
+                                                                       (T*)C, ld, Sub<T>{}, 0);
+    return cudaGetLastError();
+}
+
 cudaError_t interp_prepare(int nupts, int nfpts, int nnz, bool fp64) {
     // shared memory above the default 48 KB for the staged state tile.  The
     // limit is a property of the kernel, shared by every block and context:
@@ -656,7 +670,7 @@ div_sparse_kernel(int nupts, int K, int nnz, int nvars, const SpPair<T>* __restr
             for (int c = 0; c < DS_RC; ++c) {
                 const int s = min(s0 + c * NW, nupts - 1);
                 const int64_t i = (int64_t)s * N + col;
-                r[c] = __ldg(rcp + (int64_t)s * ld + n);
+                r[c] = rcp ? __ldg(rcp + (int64_t)s * ld + n) : T(-1);
                 if (rk.mode == 0 || rk.mode == 1) ua[c] = rk.u[i];
                 if (rk.mode == 1 || rk.mode == 2) aa[c] = rk.acc[i];
             }
@@ -705,6 +719,47 @@ template <typename T>
 static size_t div_smem(int nupts, int nfpts, int ndims, int nnz) {
     return (((size_t)nupts * nnz * sizeof(SpPair<T>) + 15) & ~(size_t)15) +
            (size_t)(nfpts + ndims * nupts) * 32 * sizeof(T);
+}
+
+// C[M][N] = A [B1; B2] for an operator with at most DS_NNZ nonzeros per row
+// (packed entries over the K1 + K2 stacked rows), unscaled: the row-wise
+// divergence kernel with no 1/J (the adjoint's [M0^T | (M4 - M6 M0)^T])
+template <typename T>
+static size_t sparse2_smem(int M, int K, int nnz) {
+    return (((size_t)M * nnz * sizeof(SpPair<T>) + 15) & ~(size_t)15) + (size_t)K * 32 * sizeof(T);
+}
+
+template <typename T>
+static cudaError_t sparse2_product(int M, int K1, int K2, int nnz, const void* ent, const void* B1, const void* B2,
+                                   int nvars, int64_t ld, void* C, cudaStream_t st) {
+    const int64_t N = (int64_t)nvars * ld;
+    if (nnz < 1 || nnz > DS_NNZ || N % 32 != 0 || ld % 128 != 0 || ((uintptr_t)B1 | (uintptr_t)B2) % 16 != 0)
+        return cudaErrorInvalidValue;
+    const size_t sm = sparse2_smem<T>(M, K1 + K2, nnz);
+    const int grid = persistent_grid((const void*)div_sparse_kernel<T>, DS_THREADS, sm, (int)(N / 32));
+    div_sparse_kernel<T><<<(unsigned)grid, DS_THREADS, sm, st>>>(
+        M, K1 + K2, nnz, nvars, (const SpPair<T>*)ent, (const T*)B1, (const T*)B2, K1, N, (T*)C, nullptr, ld,
+        RkArgs<T>{-1, T(0), T(0), nullptr, nullptr, nullptr, 0});
+    return cudaGetLastError();
+}
+
+// whether the structured kernels can take an M x K operator with nnz nonzeros
+// per row (kind 0: at most 8, the interpolation kernel; kind 1: at most 24,
+// two stacked sources), and raise their shared-memory limits if so
+bool sparse_prepare(int kind, int M, int K, int nnz, bool fp64) {
+    constexpr size_t kMax = 227 * 1024;
+    if (kind == 0) {
+        if (nnz < 1 || nnz > SP_NNZ) return false;
+        const size_t sm = fp64 ? interp_smem<double>(M, K, nnz) : interp_smem<float>(M, K, nnz);
+        if (sm > kMax) return false;
+        const void* f = fp64 ? (const void*)interp_sparse_kernel<double> : (const void*)interp_sparse_kernel<float>;
+        return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax) == cudaSuccess;
+    }
+    if (nnz < 1 || nnz > DS_NNZ) return false;
+    const size_t sm = fp64 ? sparse2_smem<double>(M, K, nnz) : sparse2_smem<float>(M, K, nnz);
+    if (sm > kMax) return false;
+    const void* f = fp64 ? (const void*)div_sparse_kernel<double> : (const void*)div_sparse_kernel<float>;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax) == cudaSuccess;
 }
 
 // R (or an RK stage, rk.mode >= 0) through the structured kernel (B.ds_nnz > 0)
@@ -2256,6 +2311,23 @@ cudaError_t adjoint_gemm(DevCtx& c, int which, int b, const void* B, void* C, cu
     DevBlock& Bk = c.blocks[b];
     const int D = c.ndims, nu = Bk.nupts, nf = Bk.nfpts;
     const int64_t N = (int64_t)c.nvars * Bk.ld;
+    if (c.structured_adjoint) {
+        // structured products where the operator allows (tensor elements): the
+        // interpolation M0 and the transposed operators' nonzeros
+        const bool fp64 = c.precision == 0;
+        const int Ms[6] = {nf, nf, D * nu, nu, nf, nu}, Ks[6] = {nu, nu, nu, nf, D * nu, nf + D * nu};
+        if (which == 0 && c.structured_interp && Bk.sp_nnz > 0)
+            return fp64 ? sparse_product<double>(nf, nu, Bk.sp_nnz, Bk.sp_idx, Bk.sp_val, B, N, C, Bk.ld, st)
+                        : sparse_product<float>(nf, nu, Bk.sp_nnz, Bk.sp_idx, Bk.sp_val, B, N, C, Bk.ld, st);
+        if (which >= 1 && which <= 4 && Bk.adj_nnz[which] > 0)
+            return fp64 ? sparse_product<double>(Ms[which], Ks[which], Bk.adj_nnz[which], Bk.adj_idx[which],
+                                                 Bk.adj_val[which], B, N, C, Bk.ld, st)
+                        : sparse_product<float>(Ms[which], Ks[which], Bk.adj_nnz[which], Bk.adj_idx[which],
+                                                Bk.adj_val[which], B, N, C, Bk.ld, st);
+        if (which == 5 && Bk.adj_nnz[5] > 0 && B2)
+            return fp64 ? sparse2_product<double>(nu, nf, D * nu, Bk.adj_nnz[5], Bk.adj_ent, B, B2, c.nvars, Bk.ld, C, st)
+                        : sparse2_product<float>(nu, nf, D * nu, Bk.adj_nnz[5], Bk.adj_ent, B, B2, c.nvars, Bk.ld, C, st);
+    }
     const void *op = nullptr, *tcop = nullptr;
     int M = 0, K = 0, K1 = 0;
     switch (which) {

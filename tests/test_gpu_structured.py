@@ -141,3 +141,36 @@ def test_mixed_mesh_structured_gradient_grouped_and_per_block(torch, prec):
         ne = blk.nodes.shape[0]
         assert torch.equal(x[:, :, :ne], y[:, :, :ne])
     assert s.sync_status() == fr.OK and t.sync_status() == fr.OK
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("system", ["euler", "ns"])
+def test_structured_adjoint_matches_the_dense_products(torch, prec, system):
+    """The adjoint's transposed operators in structured form (M3^T,
+    (M1 - M3 M2)^T, M0^T, M6^T: p+1 or 2D nonzeros per row; [M0^T |
+    (M4 - M6 M0)^T] over two stacked sources) give the adjoint RHS of the
+    dense products to the precision's rounding (tests/test_gpu_adjoint.py
+    holds both against the oracle's transpose)."""
+    from paper_1312_1638_b300 import fr
+    m = periodic_box("hex", 4, 0.0, 2 * np.pi, jitter=0.1, seed=4)
+    s = fr.Solver(m, 3, system, prec, device=0, **PRM)
+    t = fr.Solver(m, 3, system, prec, device=0, **PRM)
+    t.set_option("structured_adjoint", 0)
+    U = fields.smooth_random(s.solution_points(0), seed=3, amp=0.1, vel0=(0.3, 0.1, 0.0),
+                             p0=1.0 / (1.4 * 0.09)).transpose(1, 0, 2).copy()
+    rng = np.random.default_rng(11)
+    L = rng.standard_normal(U.shape)
+    u = [torch.from_numpy(s.pack(0, U)).cuda()]
+    lam = [torch.from_numpy(s.pack(0, L)).cuda()]
+    a = [torch.zeros_like(u[0])]
+    b = [torch.zeros_like(u[0])]
+    s.adjoint_rhs(u, lam, a)
+    t.adjoint_rhs(u, lam, b)
+    torch.cuda.synchronize()
+    ne = m.blocks[0].nodes.shape[0]
+    ga, gb = (x[0][:, :, :ne].double().cpu().numpy() for x in (a, b))
+    rel = np.linalg.norm(ga - gb) / np.linalg.norm(gb)
+    bound = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 2e-5}[prec]
+    print(f"structured adjoint {system} {prec}: rel-L2 difference {rel:.2e}")
+    assert rel <= bound
+    assert s.sync_status() == fr.OK and t.sync_status() == fr.OK
