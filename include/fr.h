@@ -313,7 +313,12 @@ fr_status fr_set_tuning(fr_ctx* ctx, const char* text);
  * two common fluxes ending it; row-wise form: at most 24 nonzeros per row),
  * with -1/J (Eq. negdivconf) and, inside fr_rk4, the RK4 stage combination
  * applied in the same pass.  Values outside 0..2 give FR_ERR_ARG.  Changing
- * either drops the captured RK4 step.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
+ * either drops the captured RK4 step.  "structured_adjoint" (default 1): the
+ * adjoint's transposed products (M3^T, (M1 - M3 M2)^T, M0^T, M6^T and
+ * [M0^T | (M4 - M6 M0)^T], fr_adjoint_rhs and fr_rk4_adjoint) take the
+ * structured kernels where their rows allow (tensor elements; at most 8,
+ * resp. 24, nonzeros per row), with FP32 / FP64 multiply-adds; 0 uses the
+ * dense products.  "tc_wait_limit" (default 0 = about two seconds; value >= 0) sets
  * the SM clock cycles after which a bounded wait inside the tensor-core
  * operator GEMMs gives up: the kernel then drains its own copies and MMAs,
  * returns, and fr_sync_status reports FR_ERR_TIMEOUT; the context stays
