@@ -385,13 +385,17 @@ cudaError_t interp_prepare(int nupts, int nfpts, int nnz, bool fp64) {
 // tensor Gauss-Legendre points, row (i, s) involves only the p+1 solution
 // points on the line through s in direction i and the two flux points at
 // that line's ends (7 of 275 entries for hexahedra at p = 4), so the product
-// is bound by HBM, not by arithmetic.  A CTA of 256 threads owns TN = 32 VW
-// columns of one variable: it stages the K = N^(f) + N^(u) rows of C and U
-// for them in shared memory (16-byte asynchronous copies; the reference
-// state is subtracted from the U rows by the thread that copied them), and
-// warp w then takes the points s = w, w + 8, ...: per point the D rows of
-// Q~ (each lane a VW-vector of columns, the row's entries read as
-// broadcasts), then the transform with the metric terms of those columns,
+// is bound by HBM, not by arithmetic.  This is the row-wise form (the
+// tensor-line kernel below is the default where the line form exists): a
+// persistent CTA of 256 threads keeps the packed (value, column) entries in
+// shared memory and walks tiles of TN = 32 VW columns of one variable
+// (variables of an element range consecutive, so their CTAs share the metric
+// terms in L2): it stages the K = N^(f) + N^(u) rows of C and U for them
+// (16-byte asynchronous copies; the reference state is subtracted from the U
+// rows by the thread that copied them), and warp w then takes the points
+// s = w, w + 8, ...: per point the D rows of Q~ (each lane a VW-vector of
+// columns, the row's entries read as broadcasts), then the transform with
+// the metric terms of those columns (fetched a chunk of points ahead),
 // written as D rows of Q.  Sums run over a row's nonzeros in increasing k,
 // the order of the dense CUDA-core product, and the transform is the
 // arithmetic of grad_transform_kernel.
@@ -618,10 +622,14 @@ cudaError_t grad_prepare(int nupts, int nfpts, int ndims, int nnz, bool fp64) {
 // element type whose divergence operator rows have at most DS_NNZ nonzeros.
 // On tensor elements row s involves, per direction i, the p+1 flux values
 // F~_i on the line through s in direction i and the two common fluxes D~ at
-// that line's ends (21 of 525 entries for hexahedra at p = 4).  A CTA of 256
-// threads owns 32 columns of one variable: it stages the K = N^(f) + D N^(u)
-// rows of D~ and F~ for them in shared memory and warp w forms the rows
-// s = w, w + 8, ... (one column per lane).  The sums run over a row's
+// that line's ends (21 of 525 entries for hexahedra at p = 4).  This is the
+// row-wise form (the tensor-line kernel is the default where the line form
+// exists): a persistent CTA of 512 threads keeps the packed entries in
+// shared memory and walks tiles of 32 columns of one variable: it stages the
+// K = N^(f) + D N^(u) rows of D~ and F~ for them and warp w forms the rows
+// s = w, w + 16, ... (one column per lane, four rows interleaved).  With
+// rcp = nullptr the kernel stores the plain product (the adjoint's stacked
+// transposed operators).  The sums run over a row's
 // nonzeros in increasing k, the order of the dense CUDA-core product, and the
 // -1/J scaling is that product's epilogue.  With an RK stage (rk.mode >= 0)
 // the result k is not stored; the stage combination of rk_point_kernel is
