@@ -131,6 +131,21 @@ static std::vector<std::vector<std::pair<int, double>>> nonzero_rows(const std::
     return nz;
 }
 
+// the same rows as [rows][nnz] column indices and values (compute type),
+// zero-padded
+static void upload_idx_val(fr_ctx* c, const std::vector<std::vector<std::pair<int, double>>>& nz, int nnz, bool fp64,
+                           int** idx_out, void** val_out) {
+    std::vector<int> idx(nz.size() * (size_t)nnz, 0);
+    std::vector<double> val(nz.size() * (size_t)nnz, 0.0);
+    for (size_t r = 0; r < nz.size(); ++r)
+        for (size_t j = 0; j < nz[r].size(); ++j) {
+            idx[r * nnz + j] = nz[r][j].first;
+            val[r * nnz + j] = nz[r][j].second;
+        }
+    *idx_out = (int*)upload(c, idx);
+    *val_out = upload_real(c, val, fp64);
+}
+
 fr_status set_err(fr_ctx* c, fr_status st, const std::string& m) {
     if (c) c->err = m;
     else g_setup_err = m;
@@ -346,31 +361,12 @@ void upload_device(fr_ctx* c) {
         }
         B.opM0 = upload_real(c, el.M0, fp64);
         {
-            // structured form of M0: the nonzeros of every row, if no row has more
-            // than 8 (entries below 1e-15 of their row's largest are rounding of a
-            // vanishing Lagrange factor and are dropped)
-            std::vector<std::vector<std::pair<int, double>>> rows((size_t)nf);
+            // structured form of M0: the nonzeros of every row, if no row has more than 8
             int nnz = 0;
-            for (int64_t r = 0; r < nf; ++r) {
-                double mx = 0;
-                for (int64_t k = 0; k < nu; ++k) mx = std::max(mx, std::fabs(el.M0[(size_t)r * nu + k]));
-                for (int64_t k = 0; k < nu; ++k) {
-                    const double v = el.M0[(size_t)r * nu + k];
-                    if (std::fabs(v) > 1e-15 * mx) rows[r].push_back({(int)k, v});
-                }
-                nnz = std::max(nnz, (int)rows[r].size());
-            }
+            const auto nz = nonzero_rows(el.M0, nf, nu, &nnz);
             if (nnz > 0 && nnz <= 8 && fr::interp_prepare((int)nu, (int)nf, nnz, fp64) == cudaSuccess) {
-                std::vector<int> idx((size_t)nf * nnz, 0);
-                std::vector<double> val((size_t)nf * nnz, 0.0);
-                for (int64_t r = 0; r < nf; ++r)
-                    for (size_t j = 0; j < rows[r].size(); ++j) {
-                        idx[(size_t)r * nnz + j] = rows[r][j].first;
-                        val[(size_t)r * nnz + j] = rows[r][j].second;
-                    }
                 B.sp_nnz = nnz;
-                B.sp_idx = (int*)upload(c, idx);
-                B.sp_val = upload_real(c, val, fp64);
+                upload_idx_val(c, nz, nnz, fp64, &B.sp_idx, &B.sp_val);
             }
             (void)cudaGetLastError();
         }
@@ -395,19 +391,8 @@ void upload_device(fr_ctx* c) {
             // structured form of the divergence operator [M3 | M1 - M3 M2] (same
             // rule): on tensor elements row s holds, per direction, the p+1
             // points of the line through s and the two flux points at its ends
-            const std::vector<double> G = hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu);
-            const int64_t rows = nu, K = nf + d * nu;
-            std::vector<std::vector<std::pair<int, double>>> nzr((size_t)rows);
             int nnz = 0;
-            for (int64_t r = 0; r < rows; ++r) {
-                double mx = 0;
-                for (int64_t k = 0; k < K; ++k) mx = std::max(mx, std::fabs(G[(size_t)(r * K + k)]));
-                for (int64_t k = 0; k < K; ++k) {
-                    const double v = G[(size_t)(r * K + k)];
-                    if (std::fabs(v) > 1e-15 * mx) nzr[r].push_back({(int)k, v});
-                }
-                nnz = std::max(nnz, (int)nzr[r].size());
-            }
+            const auto nzr = nonzero_rows(hcat(el.M3, (int)nf, el.M132, d * (int)nu, (int)nu), nu, nf + d * nu, &nnz);
             if (nnz > 0 && nnz <= 24 && fr::div_prepare((int)nu, (int)nf, d, nnz, fp64) == cudaSuccess) {
                 B.ds_nnz = nnz;
                 B.ds_ent = upload_pairs(c, nzr, nnz, fp64);
@@ -419,19 +404,8 @@ void upload_device(fr_ctx* c) {
             // (same rule as M0's): on tensor elements row (i, s) holds the p+1
             // solution points on the line through s in direction i and the two
             // flux points at its ends
-            const std::vector<double> G = hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu);
-            const int64_t rows = d * nu, K = nf + nu;
-            std::vector<std::vector<std::pair<int, double>>> nzr((size_t)rows);
             int nnz = 0;
-            for (int64_t r = 0; r < rows; ++r) {
-                double mx = 0;
-                for (int64_t k = 0; k < K; ++k) mx = std::max(mx, std::fabs(G[(size_t)(r * K + k)]));
-                for (int64_t k = 0; k < K; ++k) {
-                    const double v = G[(size_t)(r * K + k)];
-                    if (std::fabs(v) > 1e-15 * mx) nzr[r].push_back({(int)k, v});
-                }
-                nnz = std::max(nnz, (int)nzr[r].size());
-            }
+            const auto nzr = nonzero_rows(hcat(el.M6, (int)nf, el.M46, (int)nu, d * (int)nu), d * nu, nf + nu, &nnz);
             if (nnz > 0 && nnz <= 8 && fr::grad_prepare((int)nu, (int)nf, d, nnz, fp64) == cudaSuccess) {
                 B.gs_nnz = nnz;
                 B.gs_ent = upload_pairs(c, nzr, nnz, fp64);
@@ -473,16 +447,8 @@ void upload_device(fr_ctx* c) {
                     int nnz = 0;
                     const auto nz = nonzero_rows(*ops[w], rows[w], cols[w], &nnz);
                     if (w < 5 && fr::sparse_prepare(0, rows[w], cols[w], nnz, fp64)) {
-                        std::vector<int> idx((size_t)rows[w] * nnz, 0);
-                        std::vector<double> val((size_t)rows[w] * nnz, 0.0);
-                        for (int r = 0; r < rows[w]; ++r)
-                            for (size_t j = 0; j < nz[r].size(); ++j) {
-                                idx[(size_t)r * nnz + j] = nz[r][j].first;
-                                val[(size_t)r * nnz + j] = nz[r][j].second;
-                            }
                         B.adj_nnz[w] = nnz;
-                        B.adj_idx[w] = (int*)upload(c, idx);
-                        B.adj_val[w] = upload_real(c, val, fp64);
+                        upload_idx_val(c, nz, nnz, fp64, &B.adj_idx[w], &B.adj_val[w]);
                     } else if (w == 5 && fr::sparse_prepare(1, rows[w], cols[w], nnz, fp64)) {
                         B.adj_nnz[5] = nnz;
                         B.adj_ent = upload_pairs(c, nz, nnz, fp64);
