@@ -1898,22 +1898,16 @@ template <typename T, int D>
 static void launch_comm_flux_ns(int side, int64_t n, const uint32_t* oL, const uint32_t* oR, T* UL, T* UR,
                                 const T* QL, const T* QR, int64_t ldL, int64_t ldR, int64_t qsL, int64_t qsR,
                                 const T* nrm, const T* mL, const T* mR, const DevParams& P, cudaStream_t st) {
-    // the software-pipelined form where it was measured faster (3D: 2.80 -> 2.00 ms
-    // at 96^3); the 2D kernel keeps one pair per thread
-    if (side == 1 && D == 3) {
+    // beta = +-1/2: the software-pipelined form (measured faster in 3D, 2.80 ->
+    // 2.00 ms at 96^3, and in 2D, 0.65 -> 0.55 ms per RK4 step on the mixed annulus)
+    if (side == 1) {
         const int g = persistent_grid((const void*)comm_flux_pipe_kernel<T, D, true, 1>, 128, 0, (int)lin_grid(n, 128));
         comm_flux_pipe_kernel<T, D, true, 1><<<(unsigned)g, 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
                                                                          qsR, nrm, mL, mR, P);
-    } else if (side == 2 && D == 3) {
+    } else if (side == 2) {
         const int g = persistent_grid((const void*)comm_flux_pipe_kernel<T, D, true, 2>, 128, 0, (int)lin_grid(n, 128));
         comm_flux_pipe_kernel<T, D, true, 2><<<(unsigned)g, 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
                                                                          qsR, nrm, mL, mR, P);
-    } else if (side == 1) {
-        comm_flux_kernel<T, D, true, 1><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
-                                                                          qsR, nrm, mL, mR, P);
-    } else if (side == 2) {
-        comm_flux_kernel<T, D, true, 2><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
-                                                                          qsR, nrm, mL, mR, P);
     } else {
         comm_flux_kernel<T, D, true, 0><<<lin_grid(n, 128), 128, 0, st>>>(n, oL, oR, UL, UR, QL, QR, ldL, ldR, qsL,
                                                                           qsR, nrm, mL, mR, P);
